@@ -1,0 +1,337 @@
+"""Benchmark: label fusion fuse + render-back on the paper-shaped workload.
+
+Workload: procedural 6 x 5 x 3 m room with 20 boxes (~500k triangles),
+1,000 frames of 640 x 480 along a smooth random-walk trajectory, c = 40
+softmax predictions (FP32, pixel-major), log-sum fusion (f_mul) with
+w^(P), arg-max render-back of every frame.  One step = sm_reset +
+sm_fuse_frames(all frames, keeping the row maps) + sm_normalise +
+sm_render_idmap(all frames).  The 49 GB of predictions are resident in HBM
+before timing and are larger than L2, so no L2 flush is needed.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenegen as sg  # noqa: E402
+
+METRIC = "frames/s fuse+render (640x480, c=40) & HBM roofline %, plain vs BF16/FP8"
+WORKLOAD = "paper-shaped room: 500k triangles, 1000 frames 640x480, c=40"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rule", default="logsum", choices=["sum", "logsum", "maxsum", "vote"])
+    ap.add_argument("--weight", default="pixel", choices=["pixel", "image"])
+    ap.add_argument("--frames", type=int, default=1000)
+    ap.add_argument("--faces", type=int, default=500_000)
+    ap.add_argument("--cpu-frames", type=int, default=128, help="oracle sample size (frames)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- helpers
+class ClockSampler:
+    """Samples nvidia-smi clocks/throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(args, dev):
+    scene = sg.paper_room(target_faces=args.faces)
+    cams = sg.random_walk_poses(args.frames)
+    N, H, W, c = args.frames, cams.H, cams.W, scene.n_classes
+    probs = torch.empty((N, H, W, c), dtype=torch.float32, device=dev)
+    for a in range(0, N, 25):
+        b = min(N, a + 25)
+        sg.predictions(scene, cams, "paper", frames=range(a, b), device=dev, out=probs[a:b])
+    torch.cuda.synchronize(dev)
+    return scene, cams, probs
+
+
+def cpu_baseline(scene, cams, probs, args, n_frames):
+    """The oracle, as it stands, on the first n_frames of the workload, on all
+    host cores (frames dealt to threads)."""
+    import oracle
+    mesh = oracle.Mesh(scene.vertices, scene.faces)
+    p = probs[:n_frames].cpu().numpy()
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.fuse_sequence(mesh, cams.K[:n_frames], cams.cam_to_world[:n_frames], p, args.rule, args.weight,
+                         nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n_frames / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {n_frames} of the {args.frames} frames (render + fuse, {args.rule}, w^({args.weight[0].upper()})), "
+                      f"{dt:.1f} s wall"}
+
+
+# --------------------------------------------------------------------------- arms
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    scene = sg.paper_room(target_faces=args.faces)
+    cams = sg.random_walk_poses(args.frames)
+    n = min(args.cpu_frames, args.frames)
+    probs = sg.predictions(scene, cams, "paper", frames=range(n), device="cuda" if torch.cuda.is_available() else "cpu")
+    p = probs.cpu().numpy()
+    mesh = oracle.Mesh(scene.vertices, scene.faces)
+    cores = os.cpu_count() or 1
+    per = max(1, n // max(1, args.steps))
+    for _ in range(args.warmup):
+        oracle.fuse_sequence(mesh, cams.K[:1], cams.cam_to_world[:1], p[:1], args.rule, args.weight, nthreads=1)
+    times = []
+    for s in range(args.steps):
+        a = (s * per) % n
+        b = min(n, a + per)
+        t0 = time.perf_counter()
+        oracle.fuse_sequence(mesh, cams.K[a:b], cams.cam_to_world[a:b], p[a:b], args.rule, args.weight,
+                             nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    frames = per * args.steps
+    value = frames / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rule": args.rule, "weight": args.weight},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per} frames per step from the first {n} frames"},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    ws, rank, local = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if ws > 1:
+        torch.distributed.init_process_group("nccl", device_id=dev)
+    from paper_2111_11103_gb300 import labelfuse as lf
+    lf.lib()
+
+    scene, cams, probs = make_workload(args, dev)
+    N, H, W, c = probs.shape
+    K = torch.as_tensor(cams.K, device=dev)
+    T = torch.as_tensor(cams.cam_to_world.reshape(N, 16), device=dev)
+    V = torch.as_tensor(scene.vertices, device=dev)
+    Fc = torch.as_tensor(scene.faces, device=dev)
+    m = lf.sm_mesh_upload(V, Fc, None, c, args.rule, args.weight)
+    idmaps = torch.empty((N, H, W), dtype=torch.int32, device=dev)
+    images = torch.empty((N, H, W), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        lf.sm_reset(m, stream)
+        lf.sm_fuse_frames(m, probs, "f32", None, K, T, N, H, W, idmaps, stream)
+        lf.sm_normalise(m, None, None, stream)
+        lf.sm_render_idmap(m, idmaps, N * H * W, images, stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    lf.sm_check(m, stream)
+    for k in lf.SM_KERNEL:
+        lf.sm_profile_read(m, k)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    lf.sm_profile_enable(m, True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        barrier()
+    lf.sm_profile_enable(m, False)
+    ms_total = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    lf.sm_check(m, stream)
+    prof = {k: lf.sm_profile_read(m, k) for k in lf.SM_KERNEL}
+    launches = sum(n for n, _ in prof.values())
+    ms_step = ms_total / args.steps
+    value = ws * N / (ms_step / 1e3)
+
+    # roofline of the dominant kernel (the scatter): algorithmic bytes per
+    # launch = predictions + row-map read of the frames it processes
+    n_sc, ms_sc = prof["scatter"]
+    bytes_per_frame_scatter = H * W * c * 4 + H * W * 4
+    frames_per_launch = N * args.steps / max(n_sc, 1)
+    achieved = bytes_per_frame_scatter * frames_per_launch / (ms_sc / max(n_sc, 1) / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    kernels = {k: {"launches": n, "ms_per_step": t / args.steps} for k, (n, t) in prof.items() if n}
+
+    line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "faces": int(scene.faces.shape[0]), "frames": N, "H": H, "W": W,
+                       "classes": c, "rule": args.rule, "weight": args.weight, "probs": "f32 HWC",
+                       "l2": "inputs (49 GB) larger than L2, no flush", "parallelism": f"replicas{ws}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "scatter",
+                         "peak_kind": peak_kind},
+            "kernels": kernels,
+            "gpu_launches": launches,
+            "clocks": clk.summary()}
+    # step-level HBM fraction on the algorithmic bytes of the whole path
+    algo_step = N * (H * W * c * 4 + 2 * H * W * 4 + H * W) + 2 * sg_rows(m, lf) * c * 4
+    line["step_hbm_frac"] = algo_step / (ms_step / 1e3) / 1e9 / peak
+
+    if not args.no_e2e and rank == 0:
+        try:
+            line["e2e"] = e2e(args, lf, m, probs, K, T, dev, stream)
+        except (RuntimeError, MemoryError) as exc:  # e.g. pinned host memory unavailable
+            line["e2e"] = {"value": None, "unit": "frames/s", "error": str(exc)[:200]}
+    if not args.no_cpu and rank == 0:
+        line["cpu_baseline"] = cpu_baseline(scene, cams, probs, args, min(args.cpu_frames, N))
+    lf.sm_mesh_free(m)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def sg_rows(m, lf):
+    return lf.sm_num_rows(m)
+
+
+def e2e(args, lf, m, probs, K, T, dev, stream):
+    """Same metric end to end: per step the predictions and cameras are copied
+    host -> device (pinned memory) inside the timed region, fused and rendered
+    through the C ABI, and the label images copied back."""
+    N, H, W, c = probs.shape
+    h_probs = torch.empty(probs.shape, dtype=probs.dtype, pin_memory=True)
+    h_probs.copy_(probs)
+    h_K, h_T = K.cpu().pin_memory(), T.cpu().pin_memory()
+    h_img = torch.empty((N, H, W), dtype=torch.uint8, pin_memory=True)
+    d_probs = probs  # device staging reuses the resident buffer
+    d_K, d_T = torch.empty_like(K), torch.empty_like(T)
+    idmaps = torch.empty((N, H, W), dtype=torch.int32, device=dev)
+    images = torch.empty((N, H, W), dtype=torch.uint8, device=dev)
+
+    def step():
+        d_probs.copy_(h_probs, non_blocking=True)
+        d_K.copy_(h_K, non_blocking=True)
+        d_T.copy_(h_T, non_blocking=True)
+        lf.sm_reset(m, stream)
+        lf.sm_fuse_frames(m, d_probs, "f32", None, d_K, d_T, N, H, W, idmaps, stream)
+        lf.sm_normalise(m, None, None, stream)
+        lf.sm_render_idmap(m, idmaps, N * H * W, images, stream)
+        h_img.copy_(images, non_blocking=True)
+
+    step()
+    torch.cuda.synchronize(dev)
+    steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize(dev)
+    dt = (time.perf_counter() - t0) / steps
+    hb = probs.numel() * 4 + K.numel() * 8 + T.numel() * 8
+    return {"value": N / dt, "unit": "frames/s", "h2d_bytes_per_step": hb, "d2h_bytes_per_step": N * H * W,
+            "steps": steps}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,222 @@
+/*
+ * labelfuse.h -- C ABI of the GB300 label-fusion library (liblabelfuse.so).
+ *
+ * Method: "Improving Semantic Image Segmentation via Label Fusion in
+ * Semantically Textured Meshes" (arXiv 2111.11103).  For every camera frame
+ * the triangle mesh is rendered with that frame's intrinsics and extrinsics
+ * into a per-pixel row map (Sec. 3.3.1); every pixel's c-class probability
+ * vector is added into the row of the texel it sees (Sec. 3.3.2,
+ * Eq. texel-in-array) under one of the fusion rules (Eqs. sum, mul, maxsum
+ * and their weighted forms, Sec. 3.2); the accumulators are normalised and
+ * their arg max is the texel class (Sec. 3.2.1); finally the fused mesh is
+ * rendered back into every view as a label image (Sec. 3.2.1, last paragraph).
+ *
+ * Conventions for every call:
+ *   - Pointers named d_* are DEVICE pointers (cudaMalloc / PyTorch tensors on
+ *     the current CUDA device), owned by the caller.  They are read-only
+ *     unless the name ends in _out, and must stay valid until the work
+ *     enqueued on `stream` has finished.  Pointers named h_* are host pointers.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  All device work is enqueued on it, asynchronously, unless the
+ *     call's comment says it synchronises.  One sm_mesh must be used from one
+ *     stream at a time (calls on one mesh are not thread-safe).
+ *   - Arguments are validated before anything is enqueued; an invalid call
+ *     returns SM_ERR_INVALID_ARG and changes nothing.  No call aborts the
+ *     process or throws.  sm_last_error() gives a one-line reason for the
+ *     calling thread's most recent failure.
+ *   - Errors found by kernels (an out-of-range vertex index, a texel row past
+ *     n_x) are latched in the mesh and returned by sm_check().
+ *   - Layouts are C order (row-major).  Image coordinates: pixel (x, y) is
+ *     sampled at image point (x, y), x to the right, y down; camera axes x
+ *     right, y down, z forward.
+ */
+#ifndef LABELFUSE_H
+#define LABELFUSE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SM_API_VERSION 1
+#define SM_MAX_CLASSES 254 /* label 255 is reserved for "no label" */
+#define SM_MAX_IMAGE_DIM 16384
+#define SM_MAX_TEXEL_RES 2048
+
+typedef enum sm_status {
+    SM_OK = 0,
+    SM_ERR_INVALID_ARG = 1, /* bad size, null pointer, enum out of range */
+    SM_ERR_OOM = 2,         /* a device allocation failed */
+    SM_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    SM_ERR_STATE = 4,       /* call not allowed in the mesh's current state */
+    SM_ERR_TIMEOUT = 5,     /* a bounded wait gave up */
+    SM_ERR_INTERNAL = 6     /* a kernel latched an error (see sm_last_error) */
+} sm_status;
+
+/* Fusion rule, fixed per mesh at upload (the accumulators' meaning depends on it). */
+typedef enum sm_rule {
+    SM_RULE_SUM = 0,    /* f_sum, Eq. (sum) / (w-sum): A += w p                       */
+    SM_RULE_LOGSUM = 1, /* f_mul, Eq. (mul) / (w-mul): A += w log(max(p, 2^-30))      */
+    SM_RULE_MAXSUM = 2, /* f_maxsum, Eq. (maxsum) / (w-maxsum): A += w g(p), g keeps  */
+                        /* the entries equal to max p and zeroes the others           */
+    SM_RULE_VOTE = 3    /* one-hot vote: A += w onehot(first arg max p)               */
+} sm_rule;
+
+/* Pixel weights w_k (Sec. 3.2.2). */
+typedef enum sm_weight {
+    SM_WEIGHT_PIXEL = 0, /* w^(P) = 1: pixels are i.i.d. observations             */
+    SM_WEIGHT_IMAGE = 1  /* w^(I) = 1 / |K_i ∩ K_x|: each image adds weight 1 to  */
+                         /* every texel it sees                                    */
+} sm_weight;
+
+/* Storage type of the probability images. */
+typedef enum sm_dtype {
+    SM_F32 = 0,     /* float32, value = p                                  */
+    SM_BF16 = 1,    /* bfloat16 q with a float32 scale per pixel, p = q*s  */
+    SM_FP8_E4M3 = 2 /* fp8 e4m3 q with a float32 scale per pixel, p = q*s  */
+} sm_dtype;
+
+/* Pinhole intrinsics in pixels. */
+typedef struct sm_intrinsics {
+    double fx, fy, cx, cy;
+} sm_intrinsics;
+
+/* Opaque mesh + accumulator state, owned by the library. */
+typedef struct sm_mesh sm_mesh;
+
+/* ------------------------------------------------------------------------ */
+
+/* Uploads a triangle mesh and allocates its accumulators (Sec. 3.1, 3.3.2).
+ *
+ *   d_vertices  V x 3 float32 world coordinates (metres), device.
+ *   d_faces     F x 3 int32 vertex indices, device.  Indices outside [0, V)
+ *               are latched as SM_ERR_INTERNAL (sm_check) and the face is
+ *               never drawn.
+ *   d_texel_res F int32 texel steps s_t >= 1 (|X_t| = (s^2+s)/2 texels,
+ *               Sec. 3.1), device; NULL means s = 1 for every triangle
+ *               (gamma = 0, one row per triangle).  For s > 1 the uv origin is
+ *               the vertex with the interior angle closest to 90 degrees.
+ *               s outside [1, SM_MAX_TEXEL_RES] -> SM_ERR_INVALID_ARG.
+ *   n_classes   c in [1, SM_MAX_CLASSES].
+ *   rule, weight  fusion rule and pixel weight used by every later fusion.
+ *   *out        receives the mesh; free it with sm_mesh_free.
+ *
+ * The library copies the geometry, so the caller may free its buffers once
+ * the call returns.  Rows are stacked triangle by triangle: the row of texel
+ * x on triangle t is l = id_t + id_x (Eq. texel-in-array), id_t the prefix sum
+ * of the texel counts.  n_x must stay below 2^31.  The accumulators start at
+ * zero.  Synchronises `stream` (it reads n_x back).
+ * Errors: SM_ERR_INVALID_ARG, SM_ERR_OOM, SM_ERR_CUDA. */
+sm_status sm_mesh_upload(const float *d_vertices, int64_t V, const int32_t *d_faces, int64_t F,
+                         const int32_t *d_texel_res, int32_t n_classes, sm_rule rule, sm_weight weight,
+                         void *stream, sm_mesh **out);
+
+/* Renders and fuses N frames into the mesh's accumulators (Sec. 3.3.1-3.3.2).
+ *
+ *   d_probs   N x H x W x c probabilities, pixel-major (the c values of a pixel
+ *             are contiguous), device, in `dtype`.  16-byte aligned.
+ *   d_scale   N x H x W float32 per-pixel scales for BF16/FP8, NULL for F32.
+ *   d_K       N intrinsics, device.
+ *   d_cam_to_world  N x 16 float64 row-major camera-to-world poses, device
+ *             (rigid: the world-to-camera rotation is the transpose).
+ *   N, H, W   frame count (0 is a no-op) and image size, 1..SM_MAX_IMAGE_DIM.
+ *   d_idmap_out  N x H x W int32 row map of every frame (-1 = no triangle), or
+ *             NULL.  Row maps are deterministic (see below).
+ *
+ * Renderer: vertices are projected in binary32 and snapped to 1/256 pixel; a
+ * triangle with any vertex at depth <= 0.05 is dropped; coverage is decided
+ * by exact integer edge functions with a top-left fill rule; the nearest
+ * surface wins by 1/z interpolated in binary32, an exact tie going to the
+ * lower triangle index.  Accumulation is float32 with atomics, so results
+ * agree with an exact sum up to rounding.  The rows' observation counts are
+ * kept alongside the accumulators.
+ * Errors: SM_ERR_INVALID_ARG, SM_ERR_OOM, SM_ERR_CUDA, SM_ERR_STATE (mesh
+ * freed). */
+sm_status sm_fuse_frames(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
+                         const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N, int32_t H, int32_t W,
+                         int32_t *d_idmap_out, void *stream);
+
+/* Normalises the accumulators and takes the arg max (Sec. 3.2.1).
+ *
+ *   d_dist    n_x x c float32 fused distributions (L1-normalised; for the
+ *             log-sum rule exp(L - max L) / sum exp(L - max L)), or NULL.
+ *   d_labels  n_x int32 arg max per row (lowest class on ties), -1 for rows
+ *             never observed, or NULL.
+ * Also stores the labels inside the mesh for sm_render_*.  Rows never
+ * observed get an all-zero distribution.
+ * Errors: SM_ERR_CUDA. */
+sm_status sm_normalise(sm_mesh *m, float *d_dist, int32_t *d_labels, void *stream);
+
+/* Renders the fused labels into N views given by their poses (the fused mesh
+ * rendered from the original poses, Sec. 3.2.1).
+ *
+ *   d_labels_out  N x H x W uint8 class per pixel; 255 where no triangle is
+ *                 seen or the row was never observed.
+ *   d_idmap_out   N x H x W int32 row maps, or NULL.
+ * Requires an earlier sm_normalise (else SM_ERR_STATE). */
+sm_status sm_render_labels(sm_mesh *m, const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N,
+                           int32_t H, int32_t W, uint8_t *d_labels_out, int32_t *d_idmap_out, void *stream);
+
+/* Render-back from row maps kept from sm_fuse_frames (no second raster):
+ * d_labels_out[k] = label of row d_idmap[k], 255 for -1 or unobserved rows.
+ * Requires an earlier sm_normalise (else SM_ERR_STATE). */
+sm_status sm_render_idmap(sm_mesh *m, const int32_t *d_idmap, int64_t n_pixels, uint8_t *d_labels_out,
+                          void *stream);
+
+/* Zeroes the accumulators and observation counts. */
+sm_status sm_reset(sm_mesh *m, void *stream);
+
+/* Copies the accumulators (n_x x c float32) and observation counts (n_x
+ * uint32) to device buffers; either may be NULL.  With sm_load_state this
+ * is the checkpoint / resume path: fusion is a sum over frames (Sec. 3.3.2),
+ * so states of disjoint frame sets can be added. */
+sm_status sm_read_state(sm_mesh *m, float *d_acc_out, uint32_t *d_cnt_out, void *stream);
+
+/* Overwrites the accumulators and counts from device buffers (both required). */
+sm_status sm_load_state(sm_mesh *m, const float *d_acc, const uint32_t *d_cnt, void *stream);
+
+/* Synchronises `stream` and returns the first error a kernel latched since
+ * the last sm_check (SM_ERR_INTERNAL), or SM_ERR_CUDA, or SM_OK.  Clears the
+ * latch. */
+sm_status sm_check(sm_mesh *m, void *stream);
+
+/* Number of accumulator rows n_x (texels), or -1 for NULL. */
+int64_t sm_num_rows(const sm_mesh *m);
+
+/* Number of classes c, or -1 for NULL. */
+int32_t sm_num_classes(const sm_mesh *m);
+
+/* Releases the mesh and all library-owned device memory.  Synchronises the
+ * device first.  NULL is a no-op. */
+sm_status sm_mesh_free(sm_mesh *m);
+
+/* Static description of a status code. */
+const char *sm_status_string(sm_status s);
+
+/* One-line detail of the calling thread's last failed call ("" if none). */
+const char *sm_last_error(void);
+
+/* Kernel timing: when enabled, every launch of the kernels below is bracketed
+ * by CUDA events on the launching stream.  sm_profile_read synchronises those
+ * events and returns the launch count and total device time since the last
+ * read (then clears them). */
+typedef enum sm_kernel {
+    SM_K_PROJECT = 0,   /* per-frame camera set-up (binary64)                  */
+    SM_K_RASTER = 1,    /* triangle set-up, coverage and depth test            */
+    SM_K_RESOLVE = 2,   /* z-buffer -> row map                                 */
+    SM_K_COUNT = 3,     /* per-frame row histogram for w^(I)                   */
+    SM_K_SCATTER = 4,   /* probability stream -> accumulator rows              */
+    SM_K_NORMALISE = 5, /* rows -> distributions and labels                    */
+    SM_K_RENDER = 6,    /* row maps -> label images                            */
+    SM_K_COUNT_KINDS = 7
+} sm_kernel;
+
+sm_status sm_profile_enable(sm_mesh *m, int32_t on);
+sm_status sm_profile_read(sm_mesh *m, sm_kernel kernel, int64_t *launches, double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LABELFUSE_H */

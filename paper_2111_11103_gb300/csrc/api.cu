@@ -1,0 +1,485 @@
+// C ABI of the label-fusion library: argument validation, library-owned
+// buffers, batching of frames and the launch sequence of the hot path
+// (camera set-up -> raster -> resolve -> [row histogram] -> scatter), plus
+// normalisation, render-back, state import/export and kernel timing.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "lf_internal.cuh"
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+sm_status fail(sm_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof g_last_error, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+sm_status cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation) return fail(SM_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(SM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define LF_CUDA(expr, what)                           \
+    do {                                              \
+        cudaError_t e_ = (expr);                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+#define LF_LAUNCHED(what)                                   \
+    do {                                                    \
+        cudaError_t e_ = cudaGetLastError();                \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);  \
+    } while (0)
+
+// Makes the mesh's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = cudaSetDevice(dev) == cudaSuccess;
+        }
+    }
+    ~DeviceGuard()
+    {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+// CUDA-event bracket of one launch when kernel timing is enabled.
+struct ProfScope {
+    sm_mesh *m;
+    int k;
+    cudaStream_t s;
+    sm_mesh::EvPair *ev = nullptr;
+    ProfScope(sm_mesh *m_, sm_kernel k_, cudaStream_t s_) : m(m_), k((int)k_), s(s_)
+    {
+        if (!m->prof) return;
+        if (m->ev_used[k] == m->ev[k].size()) {
+            sm_mesh::EvPair p;
+            if (cudaEventCreate(&p.a) != cudaSuccess) return;
+            if (cudaEventCreate(&p.b) != cudaSuccess) {
+                cudaEventDestroy(p.a);
+                return;
+            }
+            m->ev[k].push_back(p);
+        }
+        ev = &m->ev[k][m->ev_used[k]++];
+        cudaEventRecord(ev->a, s);
+    }
+    ~ProfScope()
+    {
+        if (ev) cudaEventRecord(ev->b, s);
+    }
+};
+
+template <class T>
+sm_status grow(T **buf, int64_t *cap, int64_t need, cudaStream_t s, int fill, const char *what)
+{
+    if (*cap >= need) return SM_OK;
+    if (*buf) LF_CUDA(cudaFreeAsync(*buf, s), what);
+    *buf = nullptr;
+    *cap = 0;
+    void *p = nullptr;
+    LF_CUDA(cudaMallocAsync(&p, (size_t)need * sizeof(T), s), what);
+    if (fill >= 0) LF_CUDA(cudaMemsetAsync(p, fill, (size_t)need * sizeof(T), s), what);
+    *buf = static_cast<T *>(p);
+    *cap = need;
+    return SM_OK;
+}
+
+size_t dtype_size(sm_dtype d) { return d == SM_F32 ? 4 : (d == SM_BF16 ? 2 : 1); }
+
+// Frames per batch: the batch's 64-bit z-buffers stay within ~24 MB (they are
+// hammered by atomics and should live in L2); the per-frame row histograms of
+// the image weights within ~512 MB.
+int batch_frames(const sm_mesh *m, int64_t npix, int N)
+{
+    int64_t B = (int64_t)(24u << 20) / (npix * 8);
+    if (m->weight == SM_WEIGHT_IMAGE && m->n_x > 0) {
+        const int64_t Bi = (int64_t)(512u << 20) / (m->n_x * 4);
+        if (Bi < B) B = Bi;
+    }
+    if (B < 1) B = 1;
+    if (B > 64) B = 64;
+    if (B > N) B = N;
+    return (int)B;
+}
+
+sm_status check_image(int32_t N, int32_t H, int32_t W)
+{
+    if (N < 0) return fail(SM_ERR_INVALID_ARG, "N = %d < 0", N);
+    if (H < 1 || H > SM_MAX_IMAGE_DIM || W < 1 || W > SM_MAX_IMAGE_DIM)
+        return fail(SM_ERR_INVALID_ARG, "image size %d x %d outside [1, %d]", H, W, SM_MAX_IMAGE_DIM);
+    return SM_OK;
+}
+
+// Raster + resolve of frames [f0, f0 + nb) into idm (nb x H x W).
+sm_status raster_batch(sm_mesh *m, int f0, int nb, int H, int W, int32_t *idm, cudaStream_t s)
+{
+    {
+        ProfScope p(m, SM_K_RASTER, s);
+        lf::launch_raster(m->verts, m->faces, m->F, m->cams, f0, nb, H, W, m->keys, s);
+    }
+    LF_LAUNCHED("raster");
+    {
+        ProfScope p(m, SM_K_RESOLVE, s);
+        lf::launch_resolve(m->keys, nb, H, W, m->texel_mode ? m->row0 : nullptr, m->texinfo, m->verts, m->faces,
+                           m->cams, f0, idm, s);
+    }
+    LF_LAUNCHED("resolve");
+    return SM_OK;
+}
+
+sm_status prepare_frames(sm_mesh *m, const sm_intrinsics *d_K, const double *d_T, int N, int64_t npix, int B,
+                         bool need_idbuf, cudaStream_t s)
+{
+    sm_status st;
+    if ((st = grow(&m->cams, &m->cams_cap, N, s, -1, "camera buffer")) != SM_OK) return st;
+    if ((st = grow(&m->keys, &m->keys_cap, (int64_t)B * npix, s, 0xFF, "z-buffer")) != SM_OK) return st;
+    if (need_idbuf && (st = grow(&m->idbuf, &m->idbuf_cap, (int64_t)B * npix, s, -1, "row-map buffer")) != SM_OK)
+        return st;
+    {
+        ProfScope p(m, SM_K_PROJECT, s);
+        lf::launch_project(d_K, d_T, N, m->cams, s);
+    }
+    LF_LAUNCHED("camera set-up");
+    return SM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sm_status_string(sm_status s)
+{
+    switch (s) {
+    case SM_OK: return "ok";
+    case SM_ERR_INVALID_ARG: return "invalid argument";
+    case SM_ERR_OOM: return "out of device memory";
+    case SM_ERR_CUDA: return "CUDA error";
+    case SM_ERR_STATE: return "invalid state";
+    case SM_ERR_TIMEOUT: return "timeout";
+    case SM_ERR_INTERNAL: return "error latched by a kernel";
+    }
+    return "unknown status";
+}
+
+const char *sm_last_error(void) { return g_last_error; }
+
+sm_status sm_mesh_upload(const float *d_vertices, int64_t V, const int32_t *d_faces, int64_t F,
+                         const int32_t *d_texel_res, int32_t n_classes, sm_rule rule, sm_weight weight,
+                         void *stream, sm_mesh **out)
+{
+    if (!out) return fail(SM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (V < 0 || F < 0) return fail(SM_ERR_INVALID_ARG, "negative V or F");
+    if (F > 0 && (!d_vertices || !d_faces)) return fail(SM_ERR_INVALID_ARG, "vertices/faces NULL");
+    if (V >= (1LL << 31) || F >= (1LL << 31)) return fail(SM_ERR_INVALID_ARG, "V or F >= 2^31");
+    if (n_classes < 1 || n_classes > SM_MAX_CLASSES)
+        return fail(SM_ERR_INVALID_ARG, "n_classes = %d outside [1, %d]", n_classes, SM_MAX_CLASSES);
+    if ((int)rule < 0 || (int)rule > 3) return fail(SM_ERR_INVALID_ARG, "unknown rule %d", (int)rule);
+    if ((int)weight < 0 || (int)weight > 1) return fail(SM_ERR_INVALID_ARG, "unknown weight %d", (int)weight);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    sm_mesh *m = new (std::nothrow) sm_mesh();
+    if (!m) return fail(SM_ERR_OOM, "host allocation");
+    auto bail = [&](sm_status st) {
+        sm_mesh_free(m);
+        return st;
+    };
+    if (cudaGetDevice(&m->device) != cudaSuccess) return bail(fail(SM_ERR_CUDA, "no current CUDA device"));
+    m->V = V;
+    m->F = F;
+    m->c = n_classes;
+    m->rule = rule;
+    m->weight = weight;
+    m->texel_mode = d_texel_res != nullptr;
+
+    cudaError_t e;
+    if ((e = cudaMalloc(&m->err, 2 * sizeof(int32_t))) != cudaSuccess) return bail(cuda_fail(e, "error latch"));
+    if ((e = cudaMemsetAsync(m->err, 0, 2 * sizeof(int32_t), s)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
+    if ((e = cudaMalloc(&m->verts, (size_t)(V > 0 ? V : 1) * sizeof(float4))) != cudaSuccess)
+        return bail(cuda_fail(e, "vertex buffer"));
+    if ((e = cudaMalloc(&m->faces, (size_t)(F > 0 ? F : 1) * sizeof(int4))) != cudaSuccess)
+        return bail(cuda_fail(e, "face buffer"));
+    lf::launch_pack_mesh(d_vertices, V, d_faces, F, m->verts, m->faces, m->err, s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(e, "pack mesh"));
+
+    int64_t n_x = F;
+    if (m->texel_mode) {
+        if ((e = cudaMalloc(&m->row0, (size_t)(F > 0 ? F : 1) * sizeof(int32_t))) != cudaSuccess)
+            return bail(cuda_fail(e, "row offsets"));
+        if ((e = cudaMalloc(&m->texinfo, (size_t)(F > 0 ? F : 1) * sizeof(int32_t))) != cudaSuccess)
+            return bail(cuda_fail(e, "texel info"));
+        void *scratch = nullptr;
+        int64_t *d_nx = nullptr;
+        if ((e = cudaMalloc(&scratch, lf::texel_scan_scratch_bytes(F))) != cudaSuccess)
+            return bail(cuda_fail(e, "scan scratch"));
+        if ((e = cudaMalloc(&d_nx, sizeof(int64_t))) != cudaSuccess) {
+            cudaFree(scratch);
+            return bail(cuda_fail(e, "scan scratch"));
+        }
+        lf::launch_texel_layout(d_texel_res, m->verts, m->faces, F, m->texinfo, m->row0, d_nx, scratch, m->err, s);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&n_x, d_nx, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(scratch);
+        cudaFree(d_nx);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "texel layout"));
+    }
+    int32_t latched = 0;
+    if ((e = cudaMemcpyAsync(&latched, m->err, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return bail(cuda_fail(e, "read error latch"));
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(cuda_fail(e, "upload"));
+    if (latched == lf::kErrTexelRes)
+        return bail(fail(SM_ERR_INVALID_ARG, "texel steps outside [1, %d]", SM_MAX_TEXEL_RES));
+    if (latched == lf::kErrRowOverflow || n_x >= (1LL << 31))
+        return bail(fail(SM_ERR_INVALID_ARG, "n_x = %lld texel rows >= 2^31", (long long)n_x));
+    m->n_x = n_x;
+
+    const size_t acc_bytes = (size_t)(n_x > 0 ? n_x : 1) * n_classes * sizeof(float);
+    if ((e = cudaMalloc(&m->acc, acc_bytes)) != cudaSuccess) return bail(cuda_fail(e, "accumulators"));
+    if ((e = cudaMalloc(&m->cnt, (size_t)(n_x > 0 ? n_x : 1) * sizeof(uint32_t))) != cudaSuccess)
+        return bail(cuda_fail(e, "counts"));
+    if ((e = cudaMalloc(&m->labels8, (size_t)(n_x > 0 ? n_x : 1))) != cudaSuccess)
+        return bail(cuda_fail(e, "labels"));
+    if ((e = cudaMemsetAsync(m->acc, 0, acc_bytes, s)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
+    if ((e = cudaMemsetAsync(m->cnt, 0, (size_t)(n_x > 0 ? n_x : 1) * sizeof(uint32_t), s)) != cudaSuccess)
+        return bail(cuda_fail(e, "memset"));
+    if ((e = cudaMemsetAsync(m->labels8, 0xFF, (size_t)(n_x > 0 ? n_x : 1), s)) != cudaSuccess)
+        return bail(cuda_fail(e, "memset"));
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(cuda_fail(e, "upload"));
+    *out = m;
+    return SM_OK;
+}
+
+sm_status sm_fuse_frames(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
+                         const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N, int32_t H, int32_t W,
+                         int32_t *d_idmap_out, void *stream)
+{
+    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
+    sm_status st = check_image(N, H, W);
+    if (st != SM_OK) return st;
+    if ((int)dtype < 0 || (int)dtype > 2) return fail(SM_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
+    if (dtype == SM_F32 && d_scale) return fail(SM_ERR_INVALID_ARG, "F32 probabilities take no scale");
+    if (dtype != SM_F32 && !d_scale && N > 0) return fail(SM_ERR_INVALID_ARG, "BF16/FP8 need a per-pixel scale");
+    if (N == 0) return SM_OK;
+    if (!d_probs || !d_K || !d_cam_to_world) return fail(SM_ERR_INVALID_ARG, "NULL input pointer");
+    if (((uintptr_t)d_probs & 15) != 0) return fail(SM_ERR_INVALID_ARG, "probabilities not 16-byte aligned");
+    DeviceGuard g(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t npix = (int64_t)H * W;
+    const int B = batch_frames(m, npix, N);
+    if ((st = prepare_frames(m, d_K, d_cam_to_world, N, npix, B, d_idmap_out == nullptr, s)) != SM_OK) return st;
+    const bool image_w = m->weight == SM_WEIGHT_IMAGE;
+    if (image_w && (st = grow(&m->fcnt, &m->fcnt_cap, (int64_t)B * m->n_x, s, 0, "row histograms")) != SM_OK)
+        return st;
+    const size_t esz = dtype_size(dtype);
+    for (int f0 = 0; f0 < N; f0 += B) {
+        const int nb = (N - f0 < B) ? N - f0 : B;
+        int32_t *idm = d_idmap_out ? d_idmap_out + (int64_t)f0 * npix : m->idbuf;
+        if ((st = raster_batch(m, f0, nb, H, W, idm, s)) != SM_OK) return st;
+        if (image_w) {
+            ProfScope p(m, SM_K_COUNT, s);
+            lf::launch_count(idm, npix, nb, m->fcnt, m->n_x, s);
+        }
+        {
+            ProfScope p(m, SM_K_SCATTER, s);
+            const char *probs = static_cast<const char *>(d_probs) + (size_t)f0 * npix * m->c * esz;
+            lf::launch_scatter(m->rule, dtype, probs, d_scale ? d_scale + (size_t)f0 * npix : nullptr, idm, npix,
+                               nb, m->c, image_w ? m->fcnt : nullptr, m->n_x, m->acc, m->cnt, m->err, s);
+        }
+        LF_LAUNCHED("scatter");
+        if (image_w) {
+            lf::launch_count_reset(idm, npix, nb, m->fcnt, m->n_x, s);
+            LF_LAUNCHED("histogram reset");
+        }
+    }
+    m->normalised = false;
+    return SM_OK;
+}
+
+sm_status sm_normalise(sm_mesh *m, float *d_dist, int32_t *d_labels, void *stream)
+{
+    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
+    DeviceGuard g(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    {
+        ProfScope p(m, SM_K_NORMALISE, s);
+        lf::launch_normalise(m->rule, m->acc, m->cnt, m->n_x, m->c, d_dist, d_labels, m->labels8, s);
+    }
+    LF_LAUNCHED("normalise");
+    m->normalised = true;
+    return SM_OK;
+}
+
+sm_status sm_render_labels(sm_mesh *m, const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N,
+                           int32_t H, int32_t W, uint8_t *d_labels_out, int32_t *d_idmap_out, void *stream)
+{
+    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
+    sm_status st = check_image(N, H, W);
+    if (st != SM_OK) return st;
+    if (!m->normalised) return fail(SM_ERR_STATE, "sm_render_labels before sm_normalise");
+    if (N == 0) return SM_OK;
+    if (!d_K || !d_cam_to_world || !d_labels_out) return fail(SM_ERR_INVALID_ARG, "NULL pointer");
+    DeviceGuard g(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t npix = (int64_t)H * W;
+    const int B = batch_frames(m, npix, N);
+    if ((st = prepare_frames(m, d_K, d_cam_to_world, N, npix, B, d_idmap_out == nullptr, s)) != SM_OK) return st;
+    for (int f0 = 0; f0 < N; f0 += B) {
+        const int nb = (N - f0 < B) ? N - f0 : B;
+        int32_t *idm = d_idmap_out ? d_idmap_out + (int64_t)f0 * npix : m->idbuf;
+        if ((st = raster_batch(m, f0, nb, H, W, idm, s)) != SM_OK) return st;
+        {
+            ProfScope p(m, SM_K_RENDER, s);
+            lf::launch_render(idm, npix * nb, m->labels8, m->n_x, d_labels_out + (int64_t)f0 * npix, s);
+        }
+        LF_LAUNCHED("render");
+    }
+    return SM_OK;
+}
+
+sm_status sm_render_idmap(sm_mesh *m, const int32_t *d_idmap, int64_t n_pixels, uint8_t *d_labels_out,
+                          void *stream)
+{
+    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
+    if (n_pixels < 0) return fail(SM_ERR_INVALID_ARG, "n_pixels < 0");
+    if (!m->normalised) return fail(SM_ERR_STATE, "sm_render_idmap before sm_normalise");
+    if (n_pixels == 0) return SM_OK;
+    if (!d_idmap || !d_labels_out) return fail(SM_ERR_INVALID_ARG, "NULL pointer");
+    DeviceGuard g(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    {
+        ProfScope p(m, SM_K_RENDER, s);
+        lf::launch_render(d_idmap, n_pixels, m->labels8, m->n_x, d_labels_out, s);
+    }
+    LF_LAUNCHED("render");
+    return SM_OK;
+}
+
+sm_status sm_reset(sm_mesh *m, void *stream)
+{
+    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
+    DeviceGuard g(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t rows = m->n_x > 0 ? m->n_x : 1;
+    LF_CUDA(cudaMemsetAsync(m->acc, 0, (size_t)rows * m->c * sizeof(float), s), "reset");
+    LF_CUDA(cudaMemsetAsync(m->cnt, 0, (size_t)rows * sizeof(uint32_t), s), "reset");
+    m->normalised = false;
+    return SM_OK;
+}
+
+sm_status sm_read_state(sm_mesh *m, float *d_acc_out, uint32_t *d_cnt_out, void *stream)
+{
+    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
+    DeviceGuard g(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (d_acc_out && m->n_x > 0)
+        LF_CUDA(cudaMemcpyAsync(d_acc_out, m->acc, (size_t)m->n_x * m->c * sizeof(float), cudaMemcpyDeviceToDevice,
+                                s),
+                "read state");
+    if (d_cnt_out && m->n_x > 0)
+        LF_CUDA(cudaMemcpyAsync(d_cnt_out, m->cnt, (size_t)m->n_x * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s),
+                "read state");
+    return SM_OK;
+}
+
+sm_status sm_load_state(sm_mesh *m, const float *d_acc, const uint32_t *d_cnt, void *stream)
+{
+    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
+    if (m->n_x > 0 && (!d_acc || !d_cnt)) return fail(SM_ERR_INVALID_ARG, "NULL state pointer");
+    DeviceGuard g(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (m->n_x > 0) {
+        LF_CUDA(cudaMemcpyAsync(m->acc, d_acc, (size_t)m->n_x * m->c * sizeof(float), cudaMemcpyDeviceToDevice, s),
+                "load state");
+        LF_CUDA(cudaMemcpyAsync(m->cnt, d_cnt, (size_t)m->n_x * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s),
+                "load state");
+    }
+    m->normalised = false;
+    return SM_OK;
+}
+
+sm_status sm_check(sm_mesh *m, void *stream)
+{
+    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
+    DeviceGuard g(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int32_t latched = 0;
+    LF_CUDA(cudaMemcpyAsync(&latched, m->err, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read error latch");
+    LF_CUDA(cudaStreamSynchronize(s), "synchronise");
+    if (latched != lf::kErrNone) {
+        LF_CUDA(cudaMemsetAsync(m->err, 0, sizeof(int32_t), s), "clear error latch");
+        LF_CUDA(cudaStreamSynchronize(s), "synchronise");
+        const char *what = latched == lf::kErrFaceIndex   ? "a face references a vertex outside [0, V)"
+                           : latched == lf::kErrRowRange  ? "a row index outside [0, n_x) reached the scatter"
+                           : latched == lf::kErrTexelRes  ? "texel steps out of range"
+                                                          : "internal error";
+        return fail(SM_ERR_INTERNAL, "%s (code %d)", what, latched);
+    }
+    return SM_OK;
+}
+
+int64_t sm_num_rows(const sm_mesh *m) { return m ? m->n_x : -1; }
+
+int32_t sm_num_classes(const sm_mesh *m) { return m ? m->c : -1; }
+
+sm_status sm_mesh_free(sm_mesh *m)
+{
+    if (!m) return SM_OK;
+    {
+        DeviceGuard g(m->device);
+        cudaDeviceSynchronize();
+        void *bufs[] = {m->verts, m->faces, m->row0,  m->texinfo, m->acc,  m->cnt,
+                        m->labels8, m->err, m->cams, m->keys,    m->idbuf, m->fcnt};
+        for (void *b : bufs)
+            if (b) cudaFree(b);
+        for (int k = 0; k < SM_K_COUNT_KINDS; ++k)
+            for (auto &p : m->ev[k]) {
+                cudaEventDestroy(p.a);
+                cudaEventDestroy(p.b);
+            }
+    }
+    delete m;
+    return SM_OK;
+}
+
+sm_status sm_profile_enable(sm_mesh *m, int32_t on)
+{
+    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
+    m->prof = on != 0;
+    return SM_OK;
+}
+
+sm_status sm_profile_read(sm_mesh *m, sm_kernel kernel, int64_t *launches, double *total_ms)
+{
+    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
+    if ((int)kernel < 0 || (int)kernel >= SM_K_COUNT_KINDS) return fail(SM_ERR_INVALID_ARG, "unknown kernel");
+    DeviceGuard g(m->device);
+    const int k = (int)kernel;
+    double tot = 0.0;
+    for (size_t i = 0; i < m->ev_used[k]; ++i) {
+        LF_CUDA(cudaEventSynchronize(m->ev[k][i].b), "profile");
+        float ms = 0.0f;
+        LF_CUDA(cudaEventElapsedTime(&ms, m->ev[k][i].a, m->ev[k][i].b), "profile");
+        tot += ms;
+    }
+    if (launches) *launches = (int64_t)m->ev_used[k];
+    if (total_ms) *total_ms = tot;
+    m->ev_used[k] = 0;
+    return SM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "labelfuse.h"
+
+namespace lf {
+
+// Per-frame camera: rows 0/1 map a world point to (image x, image y) * Z in
+// 1/256-pixel units, row 2 to the camera depth Z (all binary32).
+struct Camera {
+    float a[12];
+};
+
+constexpr float kZNear = 0.05f;             // a vertex at depth <= this drops its triangle
+constexpr float kSnapLimit = 536870912.0f;  // |snapped coordinate| <= 2^29 (int64 edge products stay exact)
+constexpr float kPMin = 9.31322574615478515625e-10f;  // 2^-30, lower clamp before log
+constexpr unsigned long long kEmptyKey = ~0ull;
+
+// Error codes latched by kernels (first one wins).
+enum DeviceError : int32_t {
+    kErrNone = 0,
+    kErrFaceIndex = 1,    // a face references a vertex outside [0, V)
+    kErrTexelRes = 2,     // texel steps outside [1, SM_MAX_TEXEL_RES]
+    kErrRowRange = 3,     // a row index outside [0, n_x) reached the scatter
+    kErrRowOverflow = 4,  // n_x >= 2^31
+};
+
+// ---- kernels (raster.cu) ----
+void launch_project(const sm_intrinsics *K, const double *T, int N, Camera *out, cudaStream_t s);
+void launch_raster(const float4 *V, const int4 *faces, int64_t F, const Camera *cams, int frame0, int nb, int H,
+                   int W, unsigned long long *keys, cudaStream_t s);
+void launch_resolve(unsigned long long *keys, int nb, int H, int W, const int32_t *row0, const int32_t *texinfo,
+                    const float4 *V, const int4 *faces, const Camera *cams, int frame0, int32_t *idmap,
+                    cudaStream_t s);
+
+// ---- kernels (fuse.cu) ----
+void launch_count(const int32_t *idmap, int64_t npix, int nb, uint32_t *fcnt, int64_t n_x, cudaStream_t s);
+void launch_count_reset(const int32_t *idmap, int64_t npix, int nb, uint32_t *fcnt, int64_t n_x, cudaStream_t s);
+void launch_scatter(sm_rule rule, sm_dtype dtype, const void *probs, const float *scale, const int32_t *idmap,
+                    int64_t npix, int nb, int c, const uint32_t *fcnt, int64_t n_x, float *acc, uint32_t *cnt,
+                    int32_t *err, cudaStream_t s);
+void launch_normalise(sm_rule rule, const float *acc, const uint32_t *cnt, int64_t n_x, int c, float *dist,
+                      int32_t *labels, uint8_t *labels8, cudaStream_t s);
+void launch_render(const int32_t *idmap, int64_t npix, const uint8_t *labels8, int64_t n_x, uint8_t *out,
+                   cudaStream_t s);
+
+// ---- kernels (mesh.cu) ----
+void launch_pack_mesh(const float *verts, int64_t V, const int32_t *faces, int64_t F, float4 *verts4, int4 *faces4,
+                      int32_t *err, cudaStream_t s);
+// Texel layout: texinfo[f] = s | (uv origin << 16); row0 = exclusive prefix
+// sum of (s^2+s)/2; *n_x_out (device int64) = total.  scratch needs
+// texel_scan_scratch_bytes(F) bytes.
+size_t texel_scan_scratch_bytes(int64_t F);
+void launch_texel_layout(const int32_t *res, const float4 *verts4, const int4 *faces4, int64_t F, int32_t *texinfo,
+                         int32_t *row0, int64_t *n_x_out, void *scratch, int32_t *err, cudaStream_t s);
+
+}  // namespace lf
+
+// The opaque mesh object behind the C ABI.
+struct sm_mesh {
+    int device = 0;
+    int64_t V = 0, F = 0, n_x = 0;
+    int32_t c = 0;
+    sm_rule rule = SM_RULE_SUM;
+    sm_weight weight = SM_WEIGHT_PIXEL;
+    bool texel_mode = false;
+    bool normalised = false;
+
+    float4 *verts = nullptr;   // V: x, y, z, 0
+    int4 *faces = nullptr;     // F: i0, i1, i2, valid
+    int32_t *row0 = nullptr;   // F: id_t (texel mode only)
+    int32_t *texinfo = nullptr;  // F: s | origin << 16 (texel mode only)
+    float *acc = nullptr;      // n_x x c
+    uint32_t *cnt = nullptr;   // n_x observation counts
+    uint8_t *labels8 = nullptr;  // n_x labels after sm_normalise (255 = unseen)
+    int32_t *err = nullptr;    // device error latch
+
+    // scratch, grown on demand
+    lf::Camera *cams = nullptr;
+    int64_t cams_cap = 0;
+    unsigned long long *keys = nullptr;
+    int64_t keys_cap = 0;
+    int32_t *idbuf = nullptr;
+    int64_t idbuf_cap = 0;
+    uint32_t *fcnt = nullptr;
+    int64_t fcnt_cap = 0;
+
+    // kernel timing
+    bool prof = false;
+    struct EvPair {
+        cudaEvent_t a, b;
+    };
+    std::vector<EvPair> ev[SM_K_COUNT_KINDS];
+    size_t ev_used[SM_K_COUNT_KINDS] = {};
+};

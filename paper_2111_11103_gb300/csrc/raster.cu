@@ -1,0 +1,263 @@
+// Renderer kernels (Sec. 3.3.1): per-frame camera set-up, triangle raster with
+// a 64-bit z-buffer key, and the resolve of the z-buffer into row indices
+// l = id_t + id_x (Eq. texel-in-array).
+//
+// Determinism: every floating-point step uses explicit round-to-nearest
+// intrinsics (__fmul_rn, __fadd_rn, __fdiv_rn, __dmul_rn, __dadd_rn), which the
+// compiler never contracts into FMAs, so the integer decisions (snapped vertex
+// positions, coverage, the depth key) are the same on every run and match the
+// project's raster reading bit for bit.
+#include "lf_internal.cuh"
+
+namespace lf {
+namespace {
+
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float i2f(long long v) { return __ll2float_rn(v); }
+
+// Camera set-up in binary64 (the only binary64 work on the device): world to
+// camera R = Rcw^T, t = -R C; image rows scaled by 256 (exact) for the
+// 1/256-pixel snap grid; each entry rounded to binary32 once.
+__global__ void k_project(const sm_intrinsics *__restrict__ Ks, const double *__restrict__ Ts, int N,
+                          Camera *__restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double *T = Ts + 16 * (int64_t)i;
+    const sm_intrinsics K = Ks[i];
+    double R[3][3], C[3], t[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) R[r][c] = T[c * 4 + r];
+        C[r] = T[r * 4 + 3];
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        t[r] = -__dadd_rn(__dadd_rn(__dmul_rn(R[r][0], C[0]), __dmul_rn(R[r][1], C[1])), __dmul_rn(R[r][2], C[2]));
+    Camera cam;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        cam.a[c] = __double2float_rn(__dmul_rn(256.0, __dadd_rn(__dmul_rn(K.fx, R[0][c]), __dmul_rn(K.cx, R[2][c]))));
+        cam.a[4 + c] =
+            __double2float_rn(__dmul_rn(256.0, __dadd_rn(__dmul_rn(K.fy, R[1][c]), __dmul_rn(K.cy, R[2][c]))));
+        cam.a[8 + c] = __double2float_rn(R[2][c]);
+    }
+    cam.a[3] = __double2float_rn(__dmul_rn(256.0, __dadd_rn(__dmul_rn(K.fx, t[0]), __dmul_rn(K.cx, t[2]))));
+    cam.a[7] = __double2float_rn(__dmul_rn(256.0, __dadd_rn(__dmul_rn(K.fy, t[1]), __dmul_rn(K.cy, t[2]))));
+    cam.a[11] = __double2float_rn(t[2]);
+    out[i] = cam;
+}
+
+// Projects and snaps one vertex; false if it is at/behind the near plane or
+// outside the snap range (its triangle is then dropped).
+__device__ __forceinline__ bool project_vertex(const float *A, float4 p, int &xs, int &ys, float &iz)
+{
+    float X = fadd(fadd(fadd(fmul(A[0], p.x), fmul(A[1], p.y)), fmul(A[2], p.z)), A[3]);
+    float Y = fadd(fadd(fadd(fmul(A[4], p.x), fmul(A[5], p.y)), fmul(A[6], p.z)), A[7]);
+    float Z = fadd(fadd(fadd(fmul(A[8], p.x), fmul(A[9], p.y)), fmul(A[10], p.z)), A[11]);
+    if (!(Z > kZNear)) return false;
+    float xf = fdiv(X, Z);
+    float yf = fdiv(Y, Z);
+    if (!(fabsf(xf) <= kSnapLimit) || !(fabsf(yf) <= kSnapLimit)) return false;
+    xs = __float2int_rn(xf);
+    ys = __float2int_rn(yf);
+    iz = fdiv(1.0f, Z);
+    return true;
+}
+
+// Screen-space triangle after orientation fix-up: positive area, so each edge
+// function is >= 0 inside.  perm[k] = original local index of vertex k.
+struct Tri {
+    int x[3], y[3];
+    float iz[3];
+    long long area2;
+    bool swapped;
+};
+
+__device__ __forceinline__ bool setup_triangle(const float *A, const float4 *__restrict__ V, int4 f, Tri &t)
+{
+    if (!project_vertex(A, V[f.x], t.x[0], t.y[0], t.iz[0])) return false;
+    if (!project_vertex(A, V[f.y], t.x[1], t.y[1], t.iz[1])) return false;
+    if (!project_vertex(A, V[f.z], t.x[2], t.y[2], t.iz[2])) return false;
+    long long area2 = (long long)(t.x[1] - t.x[0]) * (t.y[2] - t.y[0]) - (long long)(t.y[1] - t.y[0]) * (t.x[2] - t.x[0]);
+    if (area2 == 0) return false;
+    t.swapped = area2 < 0;
+    if (t.swapped) {
+        int tx = t.x[1], ty = t.y[1];
+        float tz = t.iz[1];
+        t.x[1] = t.x[2];
+        t.y[1] = t.y[2];
+        t.iz[1] = t.iz[2];
+        t.x[2] = tx;
+        t.y[2] = ty;
+        t.iz[2] = tz;
+        area2 = -area2;
+    }
+    t.area2 = area2;
+    return true;
+}
+
+// Edge function of vertex k (edge b -> c opposite it) at sample (px, py).
+__device__ __forceinline__ long long edge_at(const Tri &t, int k, long long px, long long py)
+{
+    const int b = (k + 1) % 3, c = (k + 2) % 3;
+    long long dx = t.x[c] - t.x[b], dy = t.y[c] - t.y[b];
+    return dx * (py - t.y[b]) - dy * (px - t.x[b]);
+}
+
+// Top-left rule in y-down image coordinates: an edge direction with dy < 0
+// is a left edge, dy == 0 && dx > 0 a top edge; samples on them are inside.
+__device__ __forceinline__ int top_left(const Tri &t, int k)
+{
+    const int b = (k + 1) % 3, c = (k + 2) % 3;
+    int dx = t.x[c] - t.x[b], dy = t.y[c] - t.y[b];
+    return (dy < 0 || (dy == 0 && dx > 0)) ? 1 : 0;
+}
+
+__device__ __forceinline__ int floor256(int a) { return a >> 8; }        // arithmetic shift = floor
+__device__ __forceinline__ int ceil256(int a) { return -((-a) >> 8); }
+
+// One thread per (triangle, frame): set-up, then every pixel centre of the
+// clamped bounding box is tested with incrementally stepped int64 edge
+// functions; covered samples take a 64-bit atomicMin of
+// ((0xFFFFFFFF - bits(1/z)) << 32 | triangle) into the frame's z-buffer.
+__global__ void __launch_bounds__(256) k_raster(const float4 *__restrict__ V, const int4 *__restrict__ faces,
+                                                int64_t F, const Camera *__restrict__ cams, int frame0, int H, int W,
+                                                unsigned long long *__restrict__ keys)
+{
+    __shared__ float A[12];
+    const int b = blockIdx.y;
+    if (threadIdx.x < 12) A[threadIdx.x] = cams[frame0 + b].a[threadIdx.x];
+    __syncthreads();
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F) return;
+    const int4 fc = faces[f];
+    if (!fc.w) return;
+    Tri t;
+    if (!setup_triangle(A, V, fc, t)) return;
+    int minx = min(t.x[0], min(t.x[1], t.x[2])), maxx = max(t.x[0], max(t.x[1], t.x[2]));
+    int miny = min(t.y[0], min(t.y[1], t.y[2])), maxy = max(t.y[0], max(t.y[1], t.y[2]));
+    int x0 = max(ceil256(minx), 0), x1 = min(floor256(maxx), W - 1);
+    int y0 = max(ceil256(miny), 0), y1 = min(floor256(maxy), H - 1);
+    if (x0 > x1 || y0 > y1) return;
+
+    long long e_row[3], sx[3], sy[3];
+    int tl[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int bb = (k + 1) % 3, cc = (k + 2) % 3;
+        long long dx = t.x[cc] - t.x[bb], dy = t.y[cc] - t.y[bb];
+        e_row[k] = edge_at(t, k, 256LL * x0, 256LL * y0);
+        sx[k] = -256LL * dy;
+        sy[k] = 256LL * dx;
+        tl[k] = top_left(t, k);
+    }
+    const float farea = i2f(t.area2);
+    unsigned long long *frame_keys = keys + (int64_t)b * H * W;
+    for (int py = y0; py <= y1; ++py) {
+        long long e0 = e_row[0], e1 = e_row[1], e2 = e_row[2];
+        for (int px = x0; px <= x1; ++px) {
+            if (e0 + tl[0] > 0 && e1 + tl[1] > 0 && e2 + tl[2] > 0) {
+                float num = fadd(fadd(fmul(i2f(e0), t.iz[0]), fmul(i2f(e1), t.iz[1])), fmul(i2f(e2), t.iz[2]));
+                float inv_z = fdiv(num, farea);
+                unsigned long long key =
+                    ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(inv_z)) << 32) | (unsigned int)f;
+                atomicMin(frame_keys + (int64_t)py * W + px, key);
+            }
+            e0 += sx[0];
+            e1 += sx[1];
+            e2 += sx[2];
+        }
+        e_row[0] += sy[0];
+        e_row[1] += sy[1];
+        e_row[2] += sy[2];
+    }
+}
+
+// z-buffer -> row map, and re-arms the z-buffer for the next batch.  For a
+// subdivided triangle (s > 1) the winning triangle's perspective-correct
+// barycentrics are recomputed with the same operations as the raster:
+// beta_k = (float)E_k * iz_k / ((w0 + w1) + w2); u, v are the barycentrics of
+// the vertices after the uv origin; the texel cell (i, j) is
+// (floor(s u), floor(s v)) clamped into the triangle and id_x = T(i + j) + j.
+__global__ void __launch_bounds__(256) k_resolve(unsigned long long *__restrict__ keys, int64_t total, int H, int W,
+                                                 const int32_t *__restrict__ row0,
+                                                 const int32_t *__restrict__ texinfo,
+                                                 const float4 *__restrict__ V, const int4 *__restrict__ faces,
+                                                 const Camera *__restrict__ cams, int frame0,
+                                                 int32_t *__restrict__ idmap)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= total) return;
+    const unsigned long long key = keys[p];
+    keys[p] = kEmptyKey;
+    int32_t row = -1;
+    if (key != kEmptyKey) {
+        const int f = (int)(unsigned int)key;
+        if (!row0) {
+            row = f;
+        } else {
+            const int info = texinfo[f];
+            const int s = info & 0xFFFF;
+            const int o = info >> 16;
+            int idx = 0;
+            if (s > 1) {
+                const int64_t npix = (int64_t)H * W;
+                const int b = (int)(p / npix);
+                const int64_t q = p - (int64_t)b * npix;
+                const int py = (int)(q / W), px = (int)(q - (int64_t)py * W);
+                const float *A = cams[frame0 + b].a;
+                Tri t;
+                setup_triangle(A, V, faces[f], t);
+                float w[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) w[k] = fmul(i2f(edge_at(t, k, 256LL * px, 256LL * py)), t.iz[k]);
+                const float num = fadd(fadd(w[0], w[1]), w[2]);
+                float beta[3];
+                beta[0] = fdiv(w[0], num);
+                beta[t.swapped ? 2 : 1] = fdiv(w[1], num);
+                beta[t.swapped ? 1 : 2] = fdiv(w[2], num);
+                const float u = beta[(o + 1) % 3], v = beta[(o + 2) % 3];
+                const float fs = (float)s;
+                int i = (int)floorf(fmul(fs, u));
+                i = min(max(i, 0), s - 1);
+                int j = (int)floorf(fmul(fs, v));
+                j = min(max(j, 0), s - 1 - i);
+                idx = (i + j) * (i + j + 1) / 2 + j;
+            }
+            row = row0[f] + idx;
+        }
+    }
+    idmap[p] = row;
+}
+
+}  // namespace
+
+void launch_project(const sm_intrinsics *K, const double *T, int N, Camera *out, cudaStream_t s)
+{
+    if (N <= 0) return;
+    k_project<<<(N + 127) / 128, 128, 0, s>>>(K, T, N, out);
+}
+
+void launch_raster(const float4 *V, const int4 *faces, int64_t F, const Camera *cams, int frame0, int nb, int H,
+                   int W, unsigned long long *keys, cudaStream_t s)
+{
+    if (F <= 0 || nb <= 0) return;
+    dim3 grid((unsigned)((F + 255) / 256), (unsigned)nb);
+    k_raster<<<grid, 256, 0, s>>>(V, faces, F, cams, frame0, H, W, keys);
+}
+
+void launch_resolve(unsigned long long *keys, int nb, int H, int W, const int32_t *row0, const int32_t *texinfo,
+                    const float4 *V, const int4 *faces, const Camera *cams, int frame0, int32_t *idmap,
+                    cudaStream_t s)
+{
+    const int64_t total = (int64_t)nb * H * W;
+    if (total <= 0) return;
+    k_resolve<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(keys, total, H, W, row0, texinfo, V, faces, cams,
+                                                                frame0, idmap);
+}
+
+}  // namespace lf

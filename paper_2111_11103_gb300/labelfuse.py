@@ -1,0 +1,177 @@
+"""Thin ctypes binding of liblabelfuse.so (include/labelfuse.h).
+
+Every function here has the name of the C entry point it calls and only
+marshals arguments: device buffers are passed as PyTorch CUDA tensors (or raw
+integer addresses), the stream as a ``torch.cuda.Stream`` (default: the
+current stream).  A non-OK status raises :class:`LabelFuseError` carrying
+``sm_last_error()``.  There is no fallback: if the library is missing or was
+not built, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "liblabelfuse.so")
+
+SM_RULE = {"sum": 0, "logsum": 1, "maxsum": 2, "vote": 3}
+SM_WEIGHT = {"pixel": 0, "image": 1}
+SM_DTYPE = {"f32": 0, "bf16": 1, "fp8_e4m3": 2}
+SM_KERNEL = {"project": 0, "raster": 1, "resolve": 2, "count": 3, "scatter": 4, "normalise": 5, "render": 6}
+SM_OK = 0
+SM_MAX_CLASSES = 254
+SYMBOLS = ["sm_mesh_upload", "sm_fuse_frames", "sm_normalise", "sm_render_labels", "sm_render_idmap", "sm_reset",
+           "sm_read_state", "sm_load_state", "sm_check", "sm_num_rows", "sm_num_classes", "sm_mesh_free",
+           "sm_status_string", "sm_last_error", "sm_profile_enable", "sm_profile_read"]
+
+
+class LabelFuseError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads liblabelfuse.so (build it with ``paper_2111_11103_gb300._build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2111_11103_gb300._build`")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        sig = {
+            "sm_mesh_upload": [P, i64, P, i64, P, i32, i32, i32, P, ctypes.POINTER(P)],
+            "sm_fuse_frames": [P, P, i32, P, P, P, i32, i32, i32, P, P],
+            "sm_normalise": [P, P, P, P],
+            "sm_render_labels": [P, P, P, i32, i32, i32, P, P, P],
+            "sm_render_idmap": [P, P, i64, P, P],
+            "sm_reset": [P, P],
+            "sm_read_state": [P, P, P, P],
+            "sm_load_state": [P, P, P, P],
+            "sm_check": [P, P],
+            "sm_mesh_free": [P],
+            "sm_profile_enable": [P, i32],
+            "sm_profile_read": [P, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.sm_num_rows.argtypes = [P]
+        L.sm_num_rows.restype = i64
+        L.sm_num_classes.argtypes = [P]
+        L.sm_num_classes.restype = i32
+        L.sm_status_string.argtypes = [ctypes.c_int]
+        L.sm_status_string.restype = ctypes.c_char_p
+        L.sm_last_error.argtypes = []
+        L.sm_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != SM_OK:
+        raise LabelFuseError(status, lib().sm_last_error().decode() or lib().sm_status_string(status).decode())
+
+
+def _ptr(t):
+    """Device address of a tensor (or passes an int / None through)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _enum(table, v):
+    return table[v] if isinstance(v, str) else int(v)
+
+
+def sm_mesh_upload(vertices, faces, texel_res, n_classes: int, rule="sum", weight="pixel", stream=None) -> int:
+    """Uploads a mesh; returns the opaque handle (an int).  vertices: V x 3
+    float32 CUDA tensor; faces: F x 3 int32; texel_res: F int32 or None."""
+    h = ctypes.c_void_p()
+    V = int(vertices.shape[0]) if vertices is not None else 0
+    F = int(faces.shape[0]) if faces is not None else 0
+    _check(lib().sm_mesh_upload(_ptr(vertices), V, _ptr(faces), F, _ptr(texel_res), int(n_classes),
+                                _enum(SM_RULE, rule), _enum(SM_WEIGHT, weight), _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def sm_fuse_frames(mesh: int, probs, dtype, scale, K, cam_to_world, N: int, H: int, W: int, idmap_out=None,
+                   stream=None):
+    _check(lib().sm_fuse_frames(mesh, _ptr(probs), _enum(SM_DTYPE, dtype), _ptr(scale), _ptr(K), _ptr(cam_to_world),
+                                int(N), int(H), int(W), _ptr(idmap_out), _stream(stream)))
+
+
+def sm_normalise(mesh: int, dist_out=None, labels_out=None, stream=None):
+    _check(lib().sm_normalise(mesh, _ptr(dist_out), _ptr(labels_out), _stream(stream)))
+
+
+def sm_render_labels(mesh: int, K, cam_to_world, N: int, H: int, W: int, labels_out, idmap_out=None, stream=None):
+    _check(lib().sm_render_labels(mesh, _ptr(K), _ptr(cam_to_world), int(N), int(H), int(W), _ptr(labels_out),
+                                  _ptr(idmap_out), _stream(stream)))
+
+
+def sm_render_idmap(mesh: int, idmap, n_pixels: int, labels_out, stream=None):
+    _check(lib().sm_render_idmap(mesh, _ptr(idmap), int(n_pixels), _ptr(labels_out), _stream(stream)))
+
+
+def sm_reset(mesh: int, stream=None):
+    _check(lib().sm_reset(mesh, _stream(stream)))
+
+
+def sm_read_state(mesh: int, acc_out=None, cnt_out=None, stream=None):
+    _check(lib().sm_read_state(mesh, _ptr(acc_out), _ptr(cnt_out), _stream(stream)))
+
+
+def sm_load_state(mesh: int, acc, cnt, stream=None):
+    _check(lib().sm_load_state(mesh, _ptr(acc), _ptr(cnt), _stream(stream)))
+
+
+def sm_check(mesh: int, stream=None):
+    _check(lib().sm_check(mesh, _stream(stream)))
+
+
+def sm_num_rows(mesh: int) -> int:
+    return int(lib().sm_num_rows(mesh))
+
+
+def sm_num_classes(mesh: int) -> int:
+    return int(lib().sm_num_classes(mesh))
+
+
+def sm_mesh_free(mesh: int):
+    _check(lib().sm_mesh_free(mesh))
+
+
+def sm_status_string(status: int) -> str:
+    return lib().sm_status_string(int(status)).decode()
+
+
+def sm_last_error() -> str:
+    return lib().sm_last_error().decode()
+
+
+def sm_profile_enable(mesh: int, on: bool = True):
+    _check(lib().sm_profile_enable(mesh, 1 if on else 0))
+
+
+def sm_profile_read(mesh: int, kernel) -> tuple[int, float]:
+    n = ctypes.c_int64()
+    ms = ctypes.c_double()
+    _check(lib().sm_profile_read(mesh, _enum(SM_KERNEL, kernel), ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value

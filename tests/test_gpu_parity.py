@@ -1,0 +1,282 @@
+"""GPU parity: the CUDA library (through its C ABI) against the oracle on the
+same seeded inputs -- row maps and label images bit for bit, accumulators to
+1e-5 relative, labels identical except near-ties."""
+import numpy as np
+import pytest
+import torch
+
+import scenegen as sg
+from gpu_common import (assert_acc_close, check_against_oracle, check_distributions, run_gpu)
+
+pytestmark = pytest.mark.gpu
+
+RULES = ["sum", "logsum", "maxsum", "vote"]
+WEIGHTS = ["pixel", "image"]
+
+
+@pytest.fixture(scope="module")
+def dev():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2111_11103_gb300 import labelfuse as lf
+    lf.lib()  # fails loudly if the library was not built
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def tiny(dev):
+    scene, cams = sg.tiny_room(), sg.circle_poses()
+    probs = sg.predictions(scene, cams, "tiny", device=dev)
+    return scene, cams, probs
+
+
+@pytest.fixture(scope="module")
+def medium(dev):
+    """Paper-shaped room at reduced size: ~60k triangles, 24 frames of
+    203 x 151 pixels (ragged against any tile size), c = 40."""
+    scene = sg.paper_room(target_faces=60_000)
+    cams = sg.random_walk_poses(24, H=151, W=203, fx=183.0, fy=183.0, cx=101.0, cy=75.0)
+    probs = sg.predictions(scene, cams, "paper", device=dev)
+    return scene, cams, probs
+
+
+def test_tiny_config_logsum_pixel(ora, tiny):
+    """The tiny configuration exactly: 8 frames of 64 x 48, c = 4, log-sum
+    fusion with w^(P), then arg-max render-back."""
+    scene, cams, probs = tiny
+    res = run_gpu(scene, cams, probs, "logsum", "pixel")
+    check_against_oracle(ora, scene, cams, probs.cpu().numpy(), res, "logsum", "pixel")
+    assert np.all(res.idmaps >= 0)  # the walls fill every view
+    seen = res.cnt > 0
+    assert np.mean(res.labels[seen] == scene.face_gt[seen]) > 0.95
+
+
+@pytest.mark.parametrize("rule", RULES)
+@pytest.mark.parametrize("weight", WEIGHTS)
+def test_tiny_all_rules(ora, tiny, rule, weight):
+    scene, cams, probs = tiny
+    res = run_gpu(scene, cams, probs, rule, weight, reraster=False)
+    check_against_oracle(ora, scene, cams, probs.cpu().numpy(), res, rule, weight)
+
+
+@pytest.mark.parametrize("rule,weight", [("logsum", "image"), ("sum", "pixel"), ("maxsum", "image")])
+def test_tiny_texels(ora, tiny, rule, weight):
+    """Subdivided triangles (s in 1..5, random): texel rows bit for bit."""
+    scene, cams, probs = tiny
+    s = np.random.default_rng(7).integers(1, 6, size=len(scene.faces)).astype(np.int32)
+    res = run_gpu(scene, cams, probs, rule, weight, texel_res=s)
+    check_against_oracle(ora, scene, cams, probs.cpu().numpy(), res, rule, weight, texel_res=s)
+    assert res.n_x == int(((s * s + s) // 2).sum())
+
+
+@pytest.mark.parametrize("rule,weight", [("logsum", "pixel"), ("sum", "pixel"), ("logsum", "image"),
+                                         ("vote", "pixel")])
+def test_medium_paper_room(ora, medium, rule, weight):
+    scene, cams, probs = medium
+    res = run_gpu(scene, cams, probs, rule, weight, reraster=(rule == "logsum" and weight == "pixel"))
+    check_against_oracle(ora, scene, cams, probs.cpu().numpy(), res, rule, weight, nthreads=8)
+    assert (res.idmaps >= 0).mean() > 0.99
+
+
+def test_medium_texels_s4(ora, medium):
+    """Four texel steps per triangle (10 texels each) on the paper-shaped room."""
+    scene, cams, probs = medium
+    s = np.full(len(scene.faces), 4, dtype=np.int32)
+    res = run_gpu(scene, cams, probs, "logsum", "image", texel_res=s, reraster=False)
+    check_against_oracle(ora, scene, cams, probs.cpu().numpy(), res, "logsum", "image", texel_res=s, nthreads=8)
+
+
+def _quantise(probs, kind):
+    """Per-pixel scaled BF16 / E4M3 storage (scale = max p, or max p / 448)."""
+    pmax = probs.amax(-1, keepdim=True)
+    if kind == "bf16":
+        scale = pmax
+        q = (probs / scale).to(torch.bfloat16)
+    else:
+        scale = pmax / 448.0
+        q = (probs / scale).to(torch.float8_e4m3fn)
+    scale = scale[..., 0].contiguous()
+    deq = (q.float() * scale[..., None]).cpu().numpy().astype(np.float32)
+    return q.contiguous(), scale, deq
+
+
+@pytest.mark.parametrize("kind", ["bf16", "fp8_e4m3"])
+@pytest.mark.parametrize("rule", ["logsum", "sum", "maxsum"])
+def test_precision_forms(ora, medium, kind, rule):
+    """BF16 / FP8-E4M3 storage with a per-pixel scale, FP32 accumulation: parity
+    with the oracle fed the same dequantised values."""
+    scene, cams, probs = medium
+    q, scale, deq = _quantise(probs, kind)
+    res = run_gpu(scene, cams, q, rule, "pixel", dtype=kind, scale=scale, reraster=False)
+    check_against_oracle(ora, scene, cams, deq, res, rule, "pixel", nthreads=8)
+
+
+def test_ragged_and_tiny_images(ora, dev):
+    scene = sg.tiny_room()
+    for (H, W) in [(1, 1), (1, 37), (29, 1), (37, 53)]:
+        cams = sg.circle_poses(n=3, H=H, W=W, fx=40.0, fy=40.0, cx=W / 2, cy=H / 2)
+        probs = sg.predictions(scene, cams, "tiny", device=dev)
+        res = run_gpu(scene, cams, probs, "sum", "image")
+        check_against_oracle(ora, scene, cams, probs.cpu().numpy(), res, "sum", "image")
+
+
+def test_class_count_extremes(ora, dev):
+    scene = sg.tiny_room()
+    cams = sg.circle_poses(n=4)
+    g = torch.Generator(device=dev).manual_seed(3)
+    for c in (1, 3, 254):
+        logits = torch.randn((4, cams.H, cams.W, c), generator=g, device=dev)
+        probs = torch.softmax(logits, -1).contiguous()
+        for rule in ("logsum", "maxsum"):
+            res = run_gpu(scene, cams, probs, rule, "pixel", reraster=False, n_classes=c)
+            check_against_oracle(ora, scene, cams, probs.cpu().numpy(), res, rule, "pixel")
+
+
+def test_empty_mesh_and_background(dev):
+    """No triangles: every pixel is background, nothing is accumulated, every
+    label pixel is 255."""
+    from paper_2111_11103_gb300 import labelfuse as lf
+    scene = sg.Scene(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32), np.zeros(0, np.int32), [], 4)
+    cams = sg.circle_poses(n=2)
+    probs = torch.full((2, cams.H, cams.W, 4), 0.25, device=dev)
+    res = run_gpu(scene, cams, probs, "sum", "pixel")
+    assert res.n_x == 0
+    assert np.all(res.idmaps == -1) and np.all(res.images == 255)
+
+
+def test_zero_frames_is_noop(dev):
+    from paper_2111_11103_gb300 import labelfuse as lf
+    scene = sg.tiny_room()
+    V = torch.as_tensor(scene.vertices, device=dev)
+    Fc = torch.as_tensor(scene.faces, device=dev)
+    m = lf.sm_mesh_upload(V, Fc, None, 4, "sum", "pixel")
+    try:
+        lf.sm_fuse_frames(m, None, "f32", None, None, None, 0, 48, 64, None)
+        acc = torch.ones((lf.sm_num_rows(m), 4), device=dev)
+        lf.sm_read_state(m, acc, None)
+        lf.sm_check(m)
+        assert torch.count_nonzero(acc) == 0
+    finally:
+        lf.sm_mesh_free(m)
+
+
+def test_invalid_arguments(dev):
+    from paper_2111_11103_gb300 import labelfuse as lf
+    scene = sg.tiny_room()
+    cams = sg.circle_poses(n=1)
+    V = torch.as_tensor(scene.vertices, device=dev)
+    Fc = torch.as_tensor(scene.faces, device=dev)
+    K = torch.as_tensor(cams.K, device=dev)
+    T = torch.as_tensor(cams.cam_to_world.reshape(1, 16), device=dev)
+    probs = torch.full((1, 48, 64, 4), 0.25, device=dev)
+    with pytest.raises(lf.LabelFuseError):
+        lf.sm_mesh_upload(V, Fc, None, 0, "sum", "pixel")
+    bad_s = torch.zeros(len(scene.faces), dtype=torch.int32, device=dev)
+    with pytest.raises(lf.LabelFuseError):
+        lf.sm_mesh_upload(V, Fc, bad_s, 4, "sum", "pixel")
+    m = lf.sm_mesh_upload(V, Fc, None, 4, "sum", "pixel")
+    try:
+        with pytest.raises(lf.LabelFuseError):
+            lf.sm_fuse_frames(m, probs, "f32", None, K, T, 1, 0, 64)
+        with pytest.raises(lf.LabelFuseError):
+            lf.sm_fuse_frames(m, probs, "bf16", None, K, T, 1, 48, 64)
+        with pytest.raises(lf.LabelFuseError):
+            lf.sm_fuse_frames(m, probs, "f32", probs[..., 0].contiguous(), K, T, 1, 48, 64)
+        with pytest.raises(lf.LabelFuseError):  # render before normalise
+            lf.sm_render_labels(m, K, T, 1, 48, 64, torch.empty((1, 48, 64), dtype=torch.uint8, device=dev))
+        lf.sm_check(m)
+    finally:
+        lf.sm_mesh_free(m)
+
+
+def test_bad_face_index_is_latched(ora, dev):
+    """A face with a vertex index outside [0, V) is never drawn and sm_check
+    reports it; the other faces render exactly as the oracle renders the
+    mesh without it."""
+    from paper_2111_11103_gb300 import labelfuse as lf
+    scene = sg.tiny_room()
+    cams = sg.circle_poses(n=2)
+    faces = scene.faces.copy()
+    faces[5, 1] = len(scene.vertices) + 10
+    V = torch.as_tensor(scene.vertices, device=dev)
+    Fc = torch.as_tensor(faces, device=dev)
+    m = lf.sm_mesh_upload(V, Fc, None, 4, "sum", "pixel")
+    try:
+        with pytest.raises(lf.LabelFuseError):
+            lf.sm_check(m)
+        K = torch.as_tensor(cams.K, device=dev)
+        T = torch.as_tensor(cams.cam_to_world.reshape(2, 16), device=dev)
+        probs = sg.predictions(scene, cams, "tiny", device=dev)
+        idm = torch.empty((2, 48, 64), dtype=torch.int32, device=dev)
+        lf.sm_fuse_frames(m, probs, "f32", None, K, T, 2, 48, 64, idm)
+        lf.sm_check(m)
+    finally:
+        lf.sm_mesh_free(m)
+    faces_o = faces.copy()
+    faces_o[5] = [0, 0, 0]  # zero area: never drawn by the oracle
+    mesh = ora.Mesh(scene.vertices, faces_o)
+    for i in range(2):
+        idm_o = ora.render_frame(mesh, cams.K[i], cams.cam_to_world[i], 48, 64)
+        assert np.array_equal(idm.cpu().numpy()[i], idm_o)
+
+
+def test_deterministic_and_order_invariant(dev, medium):
+    """Row maps are bit-identical across runs; fusing the frames in a random
+    order gives the same counts and accumulators within 1e-5 relative (Sec.
+    3.3.2: the aggregator is permutation invariant)."""
+    scene, cams, probs = medium
+    r1 = run_gpu(scene, cams, probs, "logsum", "image", reraster=False)
+    r2 = run_gpu(scene, cams, probs, "logsum", "image", reraster=False)
+    assert np.array_equal(r1.idmaps, r2.idmaps)
+    perm = np.random.default_rng(0).permutation(cams.K.shape[0])
+    cams_p = sg.Cameras(cams.K[perm], cams.cam_to_world[perm], cams.H, cams.W)
+    r3 = run_gpu(scene, cams_p, probs[torch.as_tensor(perm, device=dev)].contiguous(), "logsum", "image",
+                 reraster=False)
+    assert np.array_equal(r3.idmaps, r1.idmaps[perm])
+    assert np.array_equal(r3.cnt, r1.cnt)
+    assert_acc_close(r3.acc, r1.acc.astype(np.float64))
+
+
+def test_state_checkpoint_resume(dev, medium):
+    """Fusing the first half, saving the state, resetting, loading it back and
+    fusing the second half equals fusing all frames at once."""
+    from paper_2111_11103_gb300 import labelfuse as lf
+    from gpu_common import to_dev
+    scene, cams, probs = medium
+    N, H, W, c = cams.K.shape[0], cams.H, cams.W, scene.n_classes
+    V, Fc, K, T, _ = to_dev(scene, cams, None, dev)
+    m = lf.sm_mesh_upload(V, Fc, None, c, "sum", "pixel")
+    try:
+        n_x = lf.sm_num_rows(m)
+        h = N // 2
+        lf.sm_fuse_frames(m, probs[:h], "f32", None, K[:h], T[:h], h, H, W)
+        acc = torch.empty((n_x, c), device=dev)
+        cnt = torch.empty(n_x, dtype=torch.int32, device=dev)
+        lf.sm_read_state(m, acc, cnt)
+        lf.sm_reset(m)
+        lf.sm_load_state(m, acc, cnt)
+        lf.sm_fuse_frames(m, probs[h:], "f32", None, K[h:], T[h:], N - h, H, W)
+        lf.sm_read_state(m, acc, cnt)
+        lf.sm_check(m)
+    finally:
+        lf.sm_mesh_free(m)
+    full = run_gpu(scene, cams, probs, "sum", "pixel", reraster=False)
+    assert np.array_equal(cnt.cpu().numpy(), full.cnt)
+    assert_acc_close(acc.cpu().numpy(), full.acc.astype(np.float64))
+
+
+def test_kernel_timing_counts_launches(dev, tiny):
+    from paper_2111_11103_gb300 import labelfuse as lf
+    from gpu_common import to_dev
+    scene, cams, probs = tiny
+    V, Fc, K, T, _ = to_dev(scene, cams, None, dev)
+    m = lf.sm_mesh_upload(V, Fc, None, 4, "logsum", "image")
+    try:
+        lf.sm_profile_enable(m, True)
+        lf.sm_fuse_frames(m, probs, "f32", None, K, T, 8, 48, 64)
+        n, ms = lf.sm_profile_read(m, "scatter")
+        assert n >= 1 and ms > 0
+        n, ms = lf.sm_profile_read(m, "scatter")
+        assert n == 0 and ms == 0
+        lf.sm_check(m)
+    finally:
+        lf.sm_mesh_free(m)
