@@ -100,18 +100,23 @@ sm_status grow(T **buf, int64_t *cap, int64_t need, cudaStream_t s, int fill, co
 
 size_t dtype_size(sm_dtype d) { return d == SM_F32 ? 4 : (d == SM_BF16 ? 2 : 1); }
 
-// Frames per batch: the batch's 64-bit z-buffers stay within ~24 MB (they are
-// hammered by atomics and should live in L2); the per-frame row histograms of
-// the image weights within ~512 MB.
+// Frames per batch: a batch's 64-bit z-buffers stay within ~12 MB (they are
+// hammered by atomics and, double-buffered, should live in L2 next to the
+// hot accumulator rows); the per-frame row histograms of the image weights
+// within ~512 MB.
 int batch_frames(const sm_mesh *m, int64_t npix, int N)
 {
-    int64_t B = (int64_t)(24u << 20) / (npix * 8);
+    int64_t B = (int64_t)(12u << 20) / (npix * 8);
     if (m->weight == SM_WEIGHT_IMAGE && m->n_x > 0) {
         const int64_t Bi = (int64_t)(512u << 20) / (m->n_x * 4);
         if (Bi < B) B = Bi;
     }
     if (B < 1) B = 1;
     if (B > 64) B = 64;
+    // multiples of 4 frames keep every batch's probability, scale and row-map
+    // base 16-byte aligned for the bulk copies (4 H W c bytes is a multiple
+    // of 16 for c % 4 == 0)
+    B = (B < 4) ? 4 : (B & ~3LL);
     if (B > N) B = N;
     return (int)B;
 }
@@ -124,29 +129,48 @@ sm_status check_image(int32_t N, int32_t H, int32_t W)
     return SM_OK;
 }
 
-// Raster + resolve of frames [f0, f0 + nb) into idm (nb x H x W).
-sm_status raster_batch(sm_mesh *m, int f0, int nb, int H, int W, int32_t *idm, cudaStream_t s)
+// Raster of frames [f0, f0 + nb) into the z-buffer keys (nb x H x W).
+sm_status raster_only(sm_mesh *m, int f0, int nb, int H, int W, unsigned long long *keys, cudaStream_t s)
 {
     {
         ProfScope p(m, SM_K_RASTER, s);
-        lf::launch_raster(m->verts, m->faces, m->F, m->cams, f0, nb, H, W, m->keys, s);
+        lf::launch_raster(m->verts, m->faces, m->F, m->bounds, m->cams, f0, nb, H, W, keys, s);
     }
     LF_LAUNCHED("raster");
+    return SM_OK;
+}
+
+// z-buffer keys -> row map (re-arms the keys).
+sm_status resolve_only(sm_mesh *m, int f0, int nb, int H, int W, unsigned long long *keys, int32_t *idm,
+                       cudaStream_t s, int32_t *idm2 = nullptr)
+{
     {
         ProfScope p(m, SM_K_RESOLVE, s);
-        lf::launch_resolve(m->keys, nb, H, W, m->texel_mode ? m->row0 : nullptr, m->texinfo, m->verts, m->faces,
-                           m->cams, f0, idm, s);
+        lf::launch_resolve(keys, nb, H, W, m->texel_mode ? m->row0 : nullptr, m->texinfo, m->verts, m->faces,
+                           m->cams, f0, idm, idm2, s);
     }
     LF_LAUNCHED("resolve");
     return SM_OK;
 }
+
+// Raster + resolve of frames [f0, f0 + nb) into idm (nb x H x W), one stream.
+sm_status raster_batch(sm_mesh *m, int f0, int nb, int H, int W, int32_t *idm, cudaStream_t s)
+{
+    sm_status st = raster_only(m, f0, nb, H, W, m->keys, s);
+    if (st != SM_OK) return st;
+    return resolve_only(m, f0, nb, H, W, m->keys, idm, s);
+}
+
+// Elements per z-buffer slot, rounded so every slot starts 256-byte aligned.
+int64_t slot_stride(int B, int64_t npix) { return ((int64_t)B * npix + 31) & ~31LL; }
 
 sm_status prepare_frames(sm_mesh *m, const sm_intrinsics *d_K, const double *d_T, int N, int64_t npix, int B,
                          bool need_idbuf, cudaStream_t s)
 {
     sm_status st;
     if ((st = grow(&m->cams, &m->cams_cap, N, s, -1, "camera buffer")) != SM_OK) return st;
-    if ((st = grow(&m->keys, &m->keys_cap, (int64_t)B * npix, s, 0xFF, "z-buffer")) != SM_OK) return st;
+    // two z-buffer slots (raster of batch b+1 overlaps the scatter of batch b)
+    if ((st = grow(&m->keys, &m->keys_cap, 2 * slot_stride(B, npix), s, 0xFF, "z-buffer")) != SM_OK) return st;
     if (need_idbuf && (st = grow(&m->idbuf, &m->idbuf_cap, (int64_t)B * npix, s, -1, "row-map buffer")) != SM_OK)
         return st;
     {
@@ -213,8 +237,23 @@ sm_status sm_mesh_upload(const float *d_vertices, int64_t V, const int32_t *d_fa
         return bail(cuda_fail(e, "vertex buffer"));
     if ((e = cudaMalloc(&m->faces, (size_t)(F > 0 ? F : 1) * sizeof(int4))) != cudaSuccess)
         return bail(cuda_fail(e, "face buffer"));
+    const int64_t nclusters = (F + lf::kClusterFaces - 1) / lf::kClusterFaces;
+    if ((e = cudaMalloc(&m->bounds, (size_t)(nclusters > 0 ? 2 * nclusters : 2) * sizeof(float4))) != cudaSuccess)
+        return bail(cuda_fail(e, "cluster bounds"));
+    if ((e = cudaStreamCreateWithFlags(&m->rstream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(cuda_fail(e, "raster stream"));
+    if ((e = cudaEventCreateWithFlags(&m->ev_start, cudaEventDisableTiming)) != cudaSuccess)
+        return bail(cuda_fail(e, "events"));
+    for (int k = 0; k < 2; ++k) {
+        if ((e = cudaEventCreateWithFlags(&m->ev_rast[k], cudaEventDisableTiming)) != cudaSuccess)
+            return bail(cuda_fail(e, "events"));
+        if ((e = cudaEventCreateWithFlags(&m->ev_scat[k], cudaEventDisableTiming)) != cudaSuccess)
+            return bail(cuda_fail(e, "events"));
+    }
     lf::launch_pack_mesh(d_vertices, V, d_faces, F, m->verts, m->faces, m->err, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(e, "pack mesh"));
+    lf::launch_cluster_bounds(m->verts, m->faces, F, m->bounds, s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(e, "cluster bounds"));
 
     int64_t n_x = F;
     if (m->texel_mode) {
@@ -281,30 +320,60 @@ sm_status sm_fuse_frames(sm_mesh *m, const void *d_probs, sm_dtype dtype, const 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t npix = (int64_t)H * W;
     const int B = batch_frames(m, npix, N);
-    if ((st = prepare_frames(m, d_K, d_cam_to_world, N, npix, B, d_idmap_out == nullptr, s)) != SM_OK) return st;
     const bool image_w = m->weight == SM_WEIGHT_IMAGE;
+    const bool tma = lf::scatter_tma_supported(m->c);
+    // face mode with the pipelined scatter: the scatter reads the z-buffer
+    // keys itself; otherwise a resolve pass writes the row map first
+    const bool from_keys = tma && !m->texel_mode;
+    const bool need_ids = !from_keys || image_w;
+    // the pipelined scatter reads its row map from the library's aligned buffer
+    const bool ids_internal = need_ids && (!d_idmap_out || (tma && !from_keys));
+    if ((st = prepare_frames(m, d_K, d_cam_to_world, N, npix, B, ids_internal, s)) != SM_OK) return st;
     if (image_w && (st = grow(&m->fcnt, &m->fcnt_cap, (int64_t)B * m->n_x, s, 0, "row histograms")) != SM_OK)
         return st;
     const size_t esz = dtype_size(dtype);
-    for (int f0 = 0; f0 < N; f0 += B) {
+    cudaStream_t r = m->rstream;
+    LF_CUDA(cudaEventRecord(m->ev_start, s), "event");
+    LF_CUDA(cudaStreamWaitEvent(r, m->ev_start, 0), "event");
+    for (int b = 0, f0 = 0; f0 < N; ++b, f0 += B) {
         const int nb = (N - f0 < B) ? N - f0 : B;
-        int32_t *idm = d_idmap_out ? d_idmap_out + (int64_t)f0 * npix : m->idbuf;
-        if ((st = raster_batch(m, f0, nb, H, W, idm, s)) != SM_OK) return st;
+        const int slot = b & 1;
+        unsigned long long *keys = m->keys + (int64_t)slot * slot_stride(B, npix);
+        int32_t *user_idm = d_idmap_out ? d_idmap_out + (int64_t)f0 * npix : nullptr;
+        int32_t *idm = ids_internal ? m->idbuf : user_idm;
+        // raster of this batch on the raster stream, once the scatter that
+        // last used this z-buffer slot has re-armed it
+        if (b >= 2) LF_CUDA(cudaStreamWaitEvent(r, m->ev_scat[slot], 0), "event");
+        if ((st = raster_only(m, f0, nb, H, W, keys, r)) != SM_OK) return st;
+        LF_CUDA(cudaEventRecord(m->ev_rast[slot], r), "event");
+        LF_CUDA(cudaStreamWaitEvent(s, m->ev_rast[slot], 0), "event");
+        if (!from_keys &&
+            (st = resolve_only(m, f0, nb, H, W, keys, idm, s, idm != user_idm ? user_idm : nullptr)) != SM_OK)
+            return st;
         if (image_w) {
             ProfScope p(m, SM_K_COUNT, s);
-            lf::launch_count(idm, npix, nb, m->fcnt, m->n_x, s);
+            lf::launch_count(from_keys ? nullptr : idm, keys, npix, nb, m->fcnt, m->n_x, s);
         }
         {
             ProfScope p(m, SM_K_SCATTER, s);
             const char *probs = static_cast<const char *>(d_probs) + (size_t)f0 * npix * m->c * esz;
-            lf::launch_scatter(m->rule, dtype, probs, d_scale ? d_scale + (size_t)f0 * npix : nullptr, idm, npix,
-                               nb, m->c, image_w ? m->fcnt : nullptr, m->n_x, m->acc, m->cnt, m->err, s);
+            const float *scale = d_scale ? d_scale + (size_t)f0 * npix : nullptr;
+            const uint32_t *fcnt = image_w ? m->fcnt : nullptr;
+            if (tma)
+                lf::launch_scatter_tma(m->rule, dtype, probs, scale, from_keys ? keys : nullptr,
+                                       from_keys ? nullptr : idm, from_keys ? idm : nullptr, npix * nb, npix, m->c,
+                                       fcnt, m->n_x, m->acc, m->cnt, m->err, s);
+            else
+                lf::launch_scatter(m->rule, dtype, probs, scale, idm, npix, nb, m->c, fcnt, m->n_x, m->acc, m->cnt,
+                                   m->err, s);
         }
         LF_LAUNCHED("scatter");
         if (image_w) {
+            ProfScope p(m, SM_K_COUNT, s);
             lf::launch_count_reset(idm, npix, nb, m->fcnt, m->n_x, s);
-            LF_LAUNCHED("histogram reset");
         }
+        LF_LAUNCHED("histogram reset");
+        LF_CUDA(cudaEventRecord(m->ev_scat[slot], s), "event");
     }
     m->normalised = false;
     return SM_OK;
@@ -423,6 +492,8 @@ sm_status sm_check(sm_mesh *m, void *stream)
     if (latched != lf::kErrNone) {
         LF_CUDA(cudaMemsetAsync(m->err, 0, sizeof(int32_t), s), "clear error latch");
         LF_CUDA(cudaStreamSynchronize(s), "synchronise");
+        if (latched == lf::kErrTimeout)
+            return fail(SM_ERR_TIMEOUT, "a bounded wait inside a kernel gave up (code %d)", latched);
         const char *what = latched == lf::kErrFaceIndex   ? "a face references a vertex outside [0, V)"
                            : latched == lf::kErrRowRange  ? "a row index outside [0, n_x) reached the scatter"
                            : latched == lf::kErrTexelRes  ? "texel steps out of range"
@@ -442,10 +513,14 @@ sm_status sm_mesh_free(sm_mesh *m)
     {
         DeviceGuard g(m->device);
         cudaDeviceSynchronize();
-        void *bufs[] = {m->verts, m->faces, m->row0,  m->texinfo, m->acc,  m->cnt,
-                        m->labels8, m->err, m->cams, m->keys,    m->idbuf, m->fcnt};
+        void *bufs[] = {m->verts, m->faces, m->row0, m->texinfo, m->acc,   m->cnt, m->labels8,
+                        m->err,   m->cams,  m->keys, m->idbuf,   m->fcnt, m->bounds};
         for (void *b : bufs)
             if (b) cudaFree(b);
+        if (m->rstream) cudaStreamDestroy(m->rstream);
+        cudaEvent_t evs[] = {m->ev_start, m->ev_rast[0], m->ev_rast[1], m->ev_scat[0], m->ev_scat[1]};
+        for (cudaEvent_t e : evs)
+            if (e) cudaEventDestroy(e);
         for (int k = 0; k < SM_K_COUNT_KINDS; ++k)
             for (auto &p : m->ev[k]) {
                 cudaEventDestroy(p.a);

@@ -39,12 +39,20 @@ __device__ __forceinline__ float load_prob(const void *base, int64_t idx)
     return decode_e4m3(q);
 }
 
-__global__ void k_count(const int32_t *__restrict__ idmap, int64_t total, int64_t npix, uint32_t *__restrict__ fcnt,
-                        int64_t n_x)
+// |K_i ∩ K_x| for every frame i of the batch and row x: histogram of the row
+// map, or of the z-buffer keys (face mode, row = triangle) when idmap is null.
+__global__ void k_count(const int32_t *__restrict__ idmap, const unsigned long long *__restrict__ keys,
+                        int64_t total, int64_t npix, uint32_t *__restrict__ fcnt, int64_t n_x)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= total) return;
-    const int32_t row = idmap[p];
+    int64_t row;
+    if (idmap) {
+        row = idmap[p];
+    } else {
+        const unsigned long long key = keys[p];
+        row = (key == kEmptyKey) ? -1 : (int64_t)(unsigned int)key;
+    }
     if (row >= 0 && row < n_x) atomicAdd(fcnt + (p / npix) * n_x + row, 1u);
 }
 
@@ -163,6 +171,28 @@ __global__ void k_render(const int32_t *__restrict__ idmap, int64_t npix, const 
     out[p] = (row < 0 || row >= n_x) ? (uint8_t)255 : labels8[row];
 }
 
+// 16 pixels per thread: four 16-byte row-map loads, one 16-byte label store.
+__global__ void k_render16(const int4 *__restrict__ idmap, int64_t n16, const uint8_t *__restrict__ labels8,
+                           int64_t n_x, uint4 *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n16) return;
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int4 r = __ldcs(idmap + 4 * i + j);
+        const int rr[4] = {r.x, r.y, r.z, r.w};
+        uint32_t packed = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t lab = (rr[k] < 0 || rr[k] >= n_x) ? 255u : (uint32_t)labels8[rr[k]];
+            packed |= lab << (8 * k);
+        }
+        w[j] = packed;
+    }
+    __stcs(out + i, make_uint4(w[0], w[1], w[2], w[3]));
+}
+
 template <int RULE>
 void scatter_dt(sm_dtype dt, dim3 g, cudaStream_t s, const void *probs, const float *scale, const int32_t *idmap,
                 int64_t total, int64_t npix, int c, const uint32_t *fcnt, int64_t n_x, float *acc, uint32_t *cnt,
@@ -179,11 +209,12 @@ void scatter_dt(sm_dtype dt, dim3 g, cudaStream_t s, const void *probs, const fl
 
 }  // namespace
 
-void launch_count(const int32_t *idmap, int64_t npix, int nb, uint32_t *fcnt, int64_t n_x, cudaStream_t s)
+void launch_count(const int32_t *idmap, const unsigned long long *keys, int64_t npix, int nb, uint32_t *fcnt,
+                  int64_t n_x, cudaStream_t s)
 {
     const int64_t total = npix * nb;
     if (total <= 0) return;
-    k_count<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(idmap, total, npix, fcnt, n_x);
+    k_count<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(idmap, keys, total, npix, fcnt, n_x);
 }
 
 void launch_count_reset(const int32_t *idmap, int64_t npix, int nb, uint32_t *fcnt, int64_t n_x, cudaStream_t s)
@@ -227,7 +258,17 @@ void launch_render(const int32_t *idmap, int64_t npix, const uint8_t *labels8, i
                    cudaStream_t s)
 {
     if (npix <= 0) return;
-    k_render<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(idmap, npix, labels8, n_x, out);
+    int64_t done = 0;
+    if (((uintptr_t)idmap & 15) == 0 && ((uintptr_t)out & 15) == 0) {
+        const int64_t n16 = npix / 16;
+        if (n16 > 0)
+            k_render16<<<(unsigned)((n16 + 255) / 256), 256, 0, s>>>(reinterpret_cast<const int4 *>(idmap), n16,
+                                                                      labels8, n_x, reinterpret_cast<uint4 *>(out));
+        done = n16 * 16;
+    }
+    if (done < npix)
+        k_render<<<(unsigned)((npix - done + 255) / 256), 256, 0, s>>>(idmap + done, npix - done, labels8, n_x,
+                                                                        out + done);
 }
 
 }  // namespace lf

@@ -29,22 +29,39 @@ enum DeviceError : int32_t {
     kErrTexelRes = 2,     // texel steps outside [1, SM_MAX_TEXEL_RES]
     kErrRowRange = 3,     // a row index outside [0, n_x) reached the scatter
     kErrRowOverflow = 4,  // n_x >= 2^31
+    kErrTimeout = 5,      // a bounded wait inside a kernel gave up
 };
 
 // ---- kernels (raster.cu) ----
 void launch_project(const sm_intrinsics *K, const double *T, int N, Camera *out, cudaStream_t s);
-void launch_raster(const float4 *V, const int4 *faces, int64_t F, const Camera *cams, int frame0, int nb, int H,
-                   int W, unsigned long long *keys, cudaStream_t s);
+// Faces are processed in clusters of 32 (one warp); bounds holds two float4
+// (min, max corner; min.w != 0 marks a cluster without valid faces) per cluster.
+constexpr int kClusterFaces = 32;
+void launch_cluster_bounds(const float4 *V, const int4 *faces, int64_t F, float4 *bounds, cudaStream_t s);
+void launch_raster(const float4 *V, const int4 *faces, int64_t F, const float4 *bounds, const Camera *cams,
+                   int frame0, int nb, int H, int W, unsigned long long *keys, cudaStream_t s);
 void launch_resolve(unsigned long long *keys, int nb, int H, int W, const int32_t *row0, const int32_t *texinfo,
                     const float4 *V, const int4 *faces, const Camera *cams, int frame0, int32_t *idmap,
-                    cudaStream_t s);
+                    int32_t *idmap2, cudaStream_t s);
 
 // ---- kernels (fuse.cu) ----
-void launch_count(const int32_t *idmap, int64_t npix, int nb, uint32_t *fcnt, int64_t n_x, cudaStream_t s);
+// Row histogram from a row map, or (idmap == null) from z-buffer keys.
+void launch_count(const int32_t *idmap, const unsigned long long *keys, int64_t npix, int nb, uint32_t *fcnt,
+                  int64_t n_x, cudaStream_t s);
 void launch_count_reset(const int32_t *idmap, int64_t npix, int nb, uint32_t *fcnt, int64_t n_x, cudaStream_t s);
 void launch_scatter(sm_rule rule, sm_dtype dtype, const void *probs, const float *scale, const int32_t *idmap,
                     int64_t npix, int nb, int c, const uint32_t *fcnt, int64_t n_x, float *acc, uint32_t *cnt,
                     int32_t *err, cudaStream_t s);
+// Pipelined scatter (scatter.cu): TMA-streamed tiles, run-length
+// pre-reduction in registers, vector reductions into the rows.  Face mode
+// passes the z-buffer keys (read, re-armed, optionally written out as row
+// map); texel mode passes the resolved row map.  Requires
+// scatter_tma_supported(c).
+bool scatter_tma_supported(int c);
+void launch_scatter_tma(sm_rule rule, sm_dtype dtype, const void *probs, const float *scale,
+                        unsigned long long *keys, const int32_t *ids_in, int32_t *ids_out, int64_t total_px,
+                        int64_t npix, int c, const uint32_t *fcnt, int64_t n_x, float *acc, uint32_t *cnt,
+                        int32_t *err, cudaStream_t s);
 void launch_normalise(sm_rule rule, const float *acc, const uint32_t *cnt, int64_t n_x, int c, float *dist,
                       int32_t *labels, uint8_t *labels8, cudaStream_t s);
 void launch_render(const int32_t *idmap, int64_t npix, const uint8_t *labels8, int64_t n_x, uint8_t *out,
@@ -73,6 +90,7 @@ struct sm_mesh {
     bool normalised = false;
 
     float4 *verts = nullptr;   // V: x, y, z, 0
+    float4 *bounds = nullptr;  // per 32-face cluster: min, max corner
     int4 *faces = nullptr;     // F: i0, i1, i2, valid
     int32_t *row0 = nullptr;   // F: id_t (texel mode only)
     int32_t *texinfo = nullptr;  // F: s | origin << 16 (texel mode only)
@@ -90,6 +108,10 @@ struct sm_mesh {
     int64_t idbuf_cap = 0;
     uint32_t *fcnt = nullptr;
     int64_t fcnt_cap = 0;
+
+    // raster stream + events that pipeline raster(batch b+1) with scatter(batch b)
+    cudaStream_t rstream = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_rast[2] = {nullptr, nullptr}, ev_scat[2] = {nullptr, nullptr};
 
     // kernel timing
     bool prof = false;

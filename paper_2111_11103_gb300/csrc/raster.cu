@@ -8,6 +8,7 @@
 // positions, coverage, the depth key) are the same on every run and match the
 // project's raster reading bit for bit.
 #include "lf_internal.cuh"
+#include "ptx.cuh"
 
 namespace lf {
 namespace {
@@ -120,12 +121,124 @@ __device__ __forceinline__ int top_left(const Tri &t, int k)
 __device__ __forceinline__ int floor256(int a) { return a >> 8; }        // arithmetic shift = floor
 __device__ __forceinline__ int ceil256(int a) { return -((-a) >> 8); }
 
-// One thread per (triangle, frame): set-up, then every pixel centre of the
-// clamped bounding box is tested with incrementally stepped int64 edge
+// World-space bounding box of every cluster of 32 consecutive faces (one warp
+// per cluster); clusters without a valid face are marked with min.w = 1.
+__global__ void k_cluster_bounds(const float4 *__restrict__ V, const int4 *__restrict__ faces, int64_t F,
+                                 float4 *__restrict__ bounds)
+{
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t cl = f / kClusterFaces;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool any = false;
+    if (f < F) {
+        const int4 fc = faces[f];
+        if (fc.w) {
+            any = true;
+            const float4 p[3] = {V[fc.x], V[fc.y], V[fc.z]};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                lo[0] = fminf(lo[0], p[k].x);
+                lo[1] = fminf(lo[1], p[k].y);
+                lo[2] = fminf(lo[2], p[k].z);
+                hi[0] = fmaxf(hi[0], p[k].x);
+                hi[1] = fmaxf(hi[1], p[k].y);
+                hi[2] = fmaxf(hi[2], p[k].z);
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], off));
+            hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], off));
+        }
+    }
+    any = __any_sync(0xffffffffu, any);
+    if ((threadIdx.x & 31) == 0 && cl * kClusterFaces < F) {
+        bounds[2 * cl] = make_float4(lo[0], lo[1], lo[2], any ? 0.0f : 1.0f);
+        bounds[2 * cl + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
+    }
+}
+
+// Conservative frustum test of one cluster (whole warp, uniform result):
+// true when no triangle of the cluster can cover a pixel centre of this
+// frame.  Each of the box's 8 corners is evaluated in homogeneous image
+// coordinates; if one affine bound is violated at all corners it is violated
+// everywhere in the box: every vertex then projects more than 2 pixels left
+// of / right of / above / below the image, or lies in front of the near
+// plane (so every triangle is dropped by the renderer anyway).  The 2-pixel
+// and 0.01 m margins dwarf the binary32 evaluation error of this test.
+__device__ __forceinline__ bool cluster_culled(const float *A, const float4 *__restrict__ bounds, int64_t cl, int H,
+                                               int W, int lane)
+{
+    const float4 lo = bounds[2 * cl], hi = bounds[2 * cl + 1];
+    if (lo.w != 0.0f) return true;
+    const float px = (lane & 1) ? hi.x : lo.x, py = (lane & 2) ? hi.y : lo.y, pz = (lane & 4) ? hi.z : lo.z;
+    const float X = A[0] * px + A[1] * py + A[2] * pz + A[3];
+    const float Y = A[4] * px + A[5] * py + A[6] * pz + A[7];
+    const float Z = A[8] * px + A[9] * py + A[10] * pz + A[11];
+    const bool corner = lane < 8;
+    const bool left = !corner || X + 512.0f * Z < 0.0f;
+    const bool right = !corner || X - 256.0f * (float)(W + 1) * Z > 0.0f;
+    const bool top = !corner || Y + 512.0f * Z < 0.0f;
+    const bool bottom = !corner || Y - 256.0f * (float)(H + 1) * Z > 0.0f;
+    const bool near = !corner || Z < kZNear - 0.01f;
+    return __all_sync(0xffffffffu, left) || __all_sync(0xffffffffu, right) || __all_sync(0xffffffffu, top) ||
+           __all_sync(0xffffffffu, bottom) || __all_sync(0xffffffffu, near);
+}
+
+__device__ __forceinline__ float to_float(int v) { return __int2float_rn(v); }
+__device__ __forceinline__ float to_float(long long v) { return __ll2float_rn(v); }
+
+// Tests every pixel centre of the clamped box [x0, x1] x [y0, y1] with edge
+// functions stepped incrementally in integer type T; covered samples take a
+// 64-bit atomicMin of ((0xFFFFFFFF - bits(1/z)) << 32 | triangle).
+template <typename T>
+__device__ __forceinline__ void raster_box(const Tri &t, int x0, int x1, int y0, int y1, unsigned int fid,
+                                           unsigned long long *__restrict__ frame_keys, int W)
+{
+    T e_row[3], sx[3], sy[3];
+    int tl[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int bb = (k + 1) % 3, cc = (k + 2) % 3;
+        const T dx = (T)(t.x[cc] - t.x[bb]), dy = (T)(t.y[cc] - t.y[bb]);
+        e_row[k] = dx * ((T)256 * y0 - t.y[bb]) - dy * ((T)256 * x0 - t.x[bb]);
+        sx[k] = (T)-256 * dy;
+        sy[k] = (T)256 * dx;
+        tl[k] = top_left(t, k);
+    }
+    const float farea = i2f(t.area2);
+    for (int py = y0; py <= y1; ++py) {
+        T e0 = e_row[0], e1 = e_row[1], e2 = e_row[2];
+        unsigned long long *row_keys = frame_keys + (int64_t)py * W;
+        for (int px = x0; px <= x1; ++px) {
+            if (e0 + tl[0] > 0 && e1 + tl[1] > 0 && e2 + tl[2] > 0) {
+                const float num =
+                    fadd(fadd(fmul(to_float(e0), t.iz[0]), fmul(to_float(e1), t.iz[1])), fmul(to_float(e2), t.iz[2]));
+                const float inv_z = fdiv(num, farea);
+                const unsigned long long key = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(inv_z)) << 32) | fid;
+                red_min_u64(row_keys + px, key);
+            }
+            e0 += sx[0];
+            e1 += sx[1];
+            e2 += sx[2];
+        }
+        e_row[0] += sy[0];
+        e_row[1] += sy[1];
+        e_row[2] += sy[2];
+    }
+}
+
+// One warp per cluster of 32 faces and one thread per face, for one frame:
+// conservative cluster cull, then per triangle set-up; every pixel centre of
+// the clamped bounding box is tested with incrementally stepped int64 edge
 // functions; covered samples take a 64-bit atomicMin of
 // ((0xFFFFFFFF - bits(1/z)) << 32 | triangle) into the frame's z-buffer.
-__global__ void __launch_bounds__(256) k_raster(const float4 *__restrict__ V, const int4 *__restrict__ faces,
-                                                int64_t F, const Camera *__restrict__ cams, int frame0, int H, int W,
+__global__ void __launch_bounds__(256, 4) k_raster(const float4 *__restrict__ V, const int4 *__restrict__ faces,
+                                                int64_t F, const float4 *__restrict__ bounds,
+                                                const Camera *__restrict__ cams, int frame0, int H, int W,
                                                 unsigned long long *__restrict__ keys)
 {
     __shared__ float A[12];
@@ -133,6 +246,9 @@ __global__ void __launch_bounds__(256) k_raster(const float4 *__restrict__ V, co
     if (threadIdx.x < 12) A[threadIdx.x] = cams[frame0 + b].a[threadIdx.x];
     __syncthreads();
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t cl = f / kClusterFaces;
+    if (cl * kClusterFaces >= F) return;  // whole warp past the end
+    if (cluster_culled(A, bounds, cl, H, W, threadIdx.x & 31)) return;
     if (f >= F) return;
     const int4 fc = faces[f];
     if (!fc.w) return;
@@ -144,37 +260,15 @@ __global__ void __launch_bounds__(256) k_raster(const float4 *__restrict__ V, co
     int y0 = max(ceil256(miny), 0), y1 = min(floor256(maxy), H - 1);
     if (x0 > x1 || y0 > y1) return;
 
-    long long e_row[3], sx[3], sy[3];
-    int tl[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const int bb = (k + 1) % 3, cc = (k + 2) % 3;
-        long long dx = t.x[cc] - t.x[bb], dy = t.y[cc] - t.y[bb];
-        e_row[k] = edge_at(t, k, 256LL * x0, 256LL * y0);
-        sx[k] = -256LL * dy;
-        sy[k] = 256LL * dx;
-        tl[k] = top_left(t, k);
-    }
-    const float farea = i2f(t.area2);
+    const unsigned int fid = (unsigned int)f;
     unsigned long long *frame_keys = keys + (int64_t)b * H * W;
-    for (int py = y0; py <= y1; ++py) {
-        long long e0 = e_row[0], e1 = e_row[1], e2 = e_row[2];
-        for (int px = x0; px <= x1; ++px) {
-            if (e0 + tl[0] > 0 && e1 + tl[1] > 0 && e2 + tl[2] > 0) {
-                float num = fadd(fadd(fmul(i2f(e0), t.iz[0]), fmul(i2f(e1), t.iz[1])), fmul(i2f(e2), t.iz[2]));
-                float inv_z = fdiv(num, farea);
-                unsigned long long key =
-                    ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(inv_z)) << 32) | (unsigned int)f;
-                atomicMin(frame_keys + (int64_t)py * W + px, key);
-            }
-            e0 += sx[0];
-            e1 += sx[1];
-            e2 += sx[2];
-        }
-        e_row[0] += sy[0];
-        e_row[1] += sy[1];
-        e_row[2] += sy[2];
-    }
+    // Small triangles (extent <= 64 px, the common case) keep every edge
+    // function value below 2^30 in magnitude, so the same integers are
+    // stepped in 32 bits; larger ones use 64 bits.  Results are identical.
+    if (maxx - minx <= (1 << 14) && maxy - miny <= (1 << 14))
+        raster_box<int>(t, x0, x1, y0, y1, fid, frame_keys, W);
+    else
+        raster_box<long long>(t, x0, x1, y0, y1, fid, frame_keys, W);
 }
 
 // z-buffer -> row map, and re-arms the z-buffer for the next batch.  For a
@@ -188,7 +282,7 @@ __global__ void __launch_bounds__(256) k_resolve(unsigned long long *__restrict_
                                                  const int32_t *__restrict__ texinfo,
                                                  const float4 *__restrict__ V, const int4 *__restrict__ faces,
                                                  const Camera *__restrict__ cams, int frame0,
-                                                 int32_t *__restrict__ idmap)
+                                                 int32_t *__restrict__ idmap, int32_t *__restrict__ idmap2)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= total) return;
@@ -232,6 +326,7 @@ __global__ void __launch_bounds__(256) k_resolve(unsigned long long *__restrict_
         }
     }
     idmap[p] = row;
+    if (idmap2) idmap2[p] = row;
 }
 
 }  // namespace
@@ -242,22 +337,28 @@ void launch_project(const sm_intrinsics *K, const double *T, int N, Camera *out,
     k_project<<<(N + 127) / 128, 128, 0, s>>>(K, T, N, out);
 }
 
-void launch_raster(const float4 *V, const int4 *faces, int64_t F, const Camera *cams, int frame0, int nb, int H,
-                   int W, unsigned long long *keys, cudaStream_t s)
+void launch_cluster_bounds(const float4 *V, const int4 *faces, int64_t F, float4 *bounds, cudaStream_t s)
+{
+    if (F <= 0) return;
+    k_cluster_bounds<<<(unsigned)((F + 255) / 256), 256, 0, s>>>(V, faces, F, bounds);
+}
+
+void launch_raster(const float4 *V, const int4 *faces, int64_t F, const float4 *bounds, const Camera *cams,
+                   int frame0, int nb, int H, int W, unsigned long long *keys, cudaStream_t s)
 {
     if (F <= 0 || nb <= 0) return;
     dim3 grid((unsigned)((F + 255) / 256), (unsigned)nb);
-    k_raster<<<grid, 256, 0, s>>>(V, faces, F, cams, frame0, H, W, keys);
+    k_raster<<<grid, 256, 0, s>>>(V, faces, F, bounds, cams, frame0, H, W, keys);
 }
 
 void launch_resolve(unsigned long long *keys, int nb, int H, int W, const int32_t *row0, const int32_t *texinfo,
                     const float4 *V, const int4 *faces, const Camera *cams, int frame0, int32_t *idmap,
-                    cudaStream_t s)
+                    int32_t *idmap2, cudaStream_t s)
 {
     const int64_t total = (int64_t)nb * H * W;
     if (total <= 0) return;
     k_resolve<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(keys, total, H, W, row0, texinfo, V, faces, cams,
-                                                                frame0, idmap);
+                                                                frame0, idmap, idmap2);
 }
 
 }  // namespace lf

@@ -1,0 +1,392 @@
+// Scatter-accumulate of the probability stream into the accumulator rows
+// (Sec. 3.3.2: for every pixel the row l = id_t + id_x of P is updated with
+// the pixel's distribution under the fusion rule, Eqs. sum / mul / maxsum and
+// their weighted forms).  This is where the bytes are: every frame streams
+// H x W x c probabilities once.
+//
+// Design (GB300):
+//  * persistent CTAs, two per SM; warp 0 is a producer whose elected lane
+//    streams 256-pixel tiles into a ring of shared-memory stages with 1-D TMA
+//    bulk copies (cp.async.bulk, completion counted on an mbarrier).  A stage
+//    holds the tile's probabilities (L2 evict-first: read once) and the
+//    tile's per-pixel metadata: the z-buffer keys left by the raster (face
+//    mode; row = triangle of the nearest surface) or the resolved row map,
+//    and the per-pixel scales of BF16/FP8 storage;
+//  * 8 consumer warps, 32 pixels each.  A warp splits into groups of c/4
+//    lanes; each lane owns four classes and each group walks a contiguous run
+//    of pixels, keeping the running sum of phi(p) for the current row in
+//    registers, four pixels per software-pipelined step.  Only when the row
+//    changes (neighbouring pixels mostly see the same triangle) is the run
+//    flushed with one 16-byte vector reduction per lane into P, plus the run
+//    length into the observation count;
+//  * face mode: the consumers re-arm the z-buffer keys and write the row map
+//    when it is asked for, so no separate resolve pass runs;
+//  * log-sum uses the hardware log2 and converts each run sum to natural
+//    logarithms once per flush.
+// Bounded waits: a wait longer than 2 s latches kErrTimeout; the producer
+// always waits for its own copies in flight before it leaves.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "lf_internal.cuh"
+#include "ptx.cuh"
+
+namespace lf {
+namespace {
+
+constexpr int kTile = 256;           // pixels per tile
+constexpr int kConsumerWarps = 8;    // 32 pixels each
+constexpr int kThreads = 32 * (1 + kConsumerWarps);
+constexpr int kUnroll = 4;           // pixels per software-pipelined step
+constexpr uint64_t kWaitNs = 2000000000ull;
+constexpr float kLn2 = 0.693147180559945309f;
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int DT>
+struct Elem {
+    static constexpr int size = DT == SM_F32 ? 4 : (DT == SM_BF16 ? 2 : 1);
+};
+
+// Four consecutive classes starting at element index e (a multiple of 4).
+template <int DT, bool SMEM>
+__device__ __forceinline__ float4 load_quad(const uint8_t *base, int64_t e)
+{
+    if (DT == SM_F32) {
+        const float4 *p = reinterpret_cast<const float4 *>(base + e * 4);
+        return SMEM ? *p : __ldcs(p);
+    } else if (DT == SM_BF16) {
+        const uint2 *p = reinterpret_cast<const uint2 *>(base + e * 2);
+        const uint2 u = SMEM ? *p : __ldcs(p);
+        return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                           __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+    } else {
+        const unsigned int *p = reinterpret_cast<const unsigned int *>(base + e);
+        const unsigned int u = SMEM ? *p : __ldcs(p);
+        __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u & 0xffffu), __NV_E4M3);
+        __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u >> 16), __NV_E4M3);
+        const float2 a = __half22float2(*reinterpret_cast<__half2 *>(&lo));
+        const float2 b = __half22float2(*reinterpret_cast<__half2 *>(&hi));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+
+__device__ __forceinline__ float4 scale4(float4 v, float s)
+{
+    return make_float4(__fmul_rn(v.x, s), __fmul_rn(v.y, s), __fmul_rn(v.z, s), __fmul_rn(v.w, s));
+}
+
+struct Args {
+    const uint8_t *probs;
+    const float *scale;
+    unsigned long long *keys;  // face mode: z-buffer keys (read and re-armed)
+    const int32_t *ids_in;     // otherwise: row map (16-byte aligned)
+    int32_t *ids_out;          // optional row map output
+    int64_t total_px, npix;
+    int c;
+    const uint32_t *fcnt;      // per-frame row histogram (image weights) or null
+    int64_t n_x;
+    float *acc;
+    uint32_t *cnt;
+    int32_t *err;
+    bool scale_bulk;           // per-pixel scales copied with the tile
+};
+
+// Stage layout: probabilities | keys (8 B/px) or row ids (4 B/px) | scales.
+struct StageLayout {
+    uint32_t probs_bytes, meta_bytes, scale_bytes, stride;
+};
+
+template <int DT>
+__host__ __device__ __forceinline__ StageLayout stage_layout(const Args &a)
+{
+    StageLayout L;
+    L.probs_bytes = (uint32_t)kTile * a.c * Elem<DT>::size;
+    L.meta_bytes = kTile * (a.keys ? 8u : 4u);
+    L.scale_bytes = (DT != SM_F32 && a.scale_bulk) ? kTile * 4u : 0u;
+    L.stride = (L.probs_bytes + L.meta_bytes + L.scale_bytes + 127u) & ~127u;
+    return L;
+}
+
+// Row, weight and scale of pixel p.  meta/sscale point at the stage's
+// metadata (null for the ragged tile, which reads global memory); i is the
+// pixel's index within its tile.
+template <int DT>
+__device__ __forceinline__ void pixel_info(const Args &a, int64_t p, int i, const uint8_t *meta, const float *sscale,
+                                           int &row, float &w, float &sc)
+{
+    row = -1;
+    w = 1.0f;
+    sc = 1.0f;
+    if (p >= a.total_px) return;
+    if (a.keys) {
+        const unsigned long long key =
+            meta ? reinterpret_cast<const unsigned long long *>(meta)[i] : a.keys[p];
+        a.keys[p] = kEmptyKey;
+        row = (key == kEmptyKey) ? -1 : (int)(unsigned int)key;
+    } else {
+        row = meta ? reinterpret_cast<const int32_t *>(meta)[i] : a.ids_in[p];
+    }
+    if (a.ids_out) a.ids_out[p] = row;
+    if (row >= a.n_x) {
+        atomicCAS(a.err, 0, (int32_t)kErrRowRange);
+        row = -1;
+    }
+    if (a.fcnt && row >= 0) w = __fdiv_rn(1.0f, (float)a.fcnt[(p / a.npix) * a.n_x + row]);
+    if (DT != SM_F32) sc = sscale ? sscale[i] : a.scale[p];
+}
+
+// Adds a finished run into its row: one 16-byte reduction per lane (four
+// classes), and the run length into the row's observation count.
+template <int RULE>
+__device__ __forceinline__ void flush(const Args &a, float *accq, int cur, float4 s, uint32_t n, int q)
+{
+    if (cur < 0) return;
+    if (RULE == SM_RULE_LOGSUM) s = make_float4(s.x * kLn2, s.y * kLn2, s.z * kLn2, s.w * kLn2);
+    red_add_v4(accq + (int64_t)cur * a.c, s);
+    if (q == 0) red_add_u32(a.cnt + cur, n);
+}
+
+// phi(p) of one pixel added into the run sum s (weight wk); pix points at
+// the pixel's first element (max-sum and vote scan the whole pixel).
+template <int RULE, int DT, bool SMEM>
+__device__ __forceinline__ void accumulate(float4 &s, float4 v, float wk, float sk, const uint8_t *pix, int q, int Q)
+{
+    if (RULE == SM_RULE_SUM) {
+        s.x = fmaf(wk, v.x, s.x);
+        s.y = fmaf(wk, v.y, s.y);
+        s.z = fmaf(wk, v.z, s.z);
+        s.w = fmaf(wk, v.w, s.w);
+    } else if (RULE == SM_RULE_LOGSUM) {
+        s.x = fmaf(wk, __log2f(fmaxf(v.x, kPMin)), s.x);
+        s.y = fmaf(wk, __log2f(fmaxf(v.y, kPMin)), s.y);
+        s.z = fmaf(wk, __log2f(fmaxf(v.z, kPMin)), s.z);
+        s.w = fmaf(wk, __log2f(fmaxf(v.w, kPMin)), s.w);
+    } else {
+        // maximum (and first arg max) of the whole pixel, scanned in class order
+        float m = -INFINITY;
+        int am = 0;
+        for (int j = 0; j < Q; ++j) {
+            float4 u = load_quad<DT, SMEM>(pix, 4 * j);
+            if (DT != SM_F32) u = scale4(u, sk);
+            if (j == 0 || u.x > m) { m = u.x; am = 4 * j; }
+            if (u.y > m) { m = u.y; am = 4 * j + 1; }
+            if (u.z > m) { m = u.z; am = 4 * j + 2; }
+            if (u.w > m) { m = u.w; am = 4 * j + 3; }
+        }
+        if (RULE == SM_RULE_MAXSUM) {
+            if (v.x == m) s.x = fmaf(wk, v.x, s.x);
+            if (v.y == m) s.y = fmaf(wk, v.y, s.y);
+            if (v.z == m) s.z = fmaf(wk, v.z, s.z);
+            if (v.w == m) s.w = fmaf(wk, v.w, s.w);
+        } else {
+            const int d = am - 4 * q;
+            if (d == 0) s.x += wk;
+            if (d == 1) s.y += wk;
+            if (d == 2) s.z += wk;
+            if (d == 3) s.w += wk;
+        }
+    }
+}
+
+// One warp's 32 pixels of a tile.  base points at the tile's first element
+// (shared memory stage, or global memory for the ragged last tile); px0 is
+// the warp's first pixel within the tile; row/w/sc belong to pixel px0+lane.
+template <int RULE, int DT, bool SMEM, bool IMAGE>
+__device__ __forceinline__ void warp_tile(const Args &a, const uint8_t *base, int px0, int lane, int row, float w,
+                                          float sc)
+{
+    constexpr int ES = Elem<DT>::size;
+    const int Q = a.c >> 2;
+    const int G = 32 / Q;
+    const int g = lane / Q, q = lane - g * Q;
+    const bool active = g < G;
+    const int start = active ? (32 * g) / G : 0;
+    const int len = active ? (32 * (g + 1)) / G - start : 0;
+    const int iters = (32 + G - 1) / G;
+    const int pstride = a.c * ES;  // bytes per pixel
+    const uint8_t *pb = base + (px0 + start) * pstride;  // this group's first pixel
+    float *accq = a.acc + 4 * q;
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    int cur = -1;
+    uint32_t n = 0;
+    for (int i0 = 0; i0 < iters; i0 += kUnroll) {
+        int r[kUnroll];
+        float wv[kUnroll], sv[kUnroll];
+        float4 v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int k = (start + i0 + u) & 31;
+            r[u] = __shfl_sync(kFull, row, k);
+            wv[u] = IMAGE ? __shfl_sync(kFull, w, k) : 1.0f;
+            sv[u] = (DT != SM_F32) ? __shfl_sync(kFull, sc, k) : 1.0f;
+            if (i0 + u >= len) r[u] = -2;  // past this group's run (or inactive lane)
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r[u] >= 0) {
+                v[u] = load_quad<DT, SMEM>(pb + (i0 + u) * pstride, 4 * q);
+                if (DT != SM_F32) v[u] = scale4(v[u], sv[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            if (r[u] == -2) continue;
+            if (r[u] != cur) {
+                flush<RULE>(a, accq, cur, s, n, q);
+                cur = r[u];
+                s = make_float4(0.f, 0.f, 0.f, 0.f);
+                n = 0;
+            }
+            if (r[u] < 0) continue;
+            accumulate<RULE, DT, SMEM>(s, v[u], wv[u], sv[u], pb + (i0 + u) * pstride, q, Q);
+            ++n;
+        }
+    }
+    if (active) flush<RULE>(a, accq, cur, s, n, q);
+}
+
+template <int RULE, int DT, bool IMAGE>
+__global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + stages;
+    uint8_t *stage0 = smem + 128;
+    const StageLayout L = stage_layout<DT>(a);
+    const int64_t ntiles_full = a.total_px / kTile;
+    const bool ragged = ntiles_full * kTile < a.total_px;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, kConsumerWarps);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const uint64_t pol = l2_evict_first();
+            const uint32_t tx = L.probs_bytes + L.meta_bytes + L.scale_bytes;
+            int it = 0;
+            for (int64_t t = blockIdx.x; t < ntiles_full; t += gridDim.x, ++it) {
+                const int s = it % stages;
+                const uint32_t ph = (uint32_t)(it / stages) & 1u;
+                if (it >= stages && !mbar_wait(empty + s, ph ^ 1u, kWaitNs)) {
+                    atomicCAS(a.err, 0, (int32_t)kErrTimeout);
+                    break;
+                }
+                uint8_t *st = stage0 + (size_t)s * L.stride;
+                mbar_arrive_expect_tx(full + s, tx);
+                bulk_g2s(st, a.probs + (size_t)t * L.probs_bytes, L.probs_bytes, full + s, pol);
+                const void *meta = a.keys ? static_cast<const void *>(a.keys + t * kTile)
+                                          : static_cast<const void *>(a.ids_in + t * kTile);
+                bulk_g2s(st + L.probs_bytes, meta, L.meta_bytes, full + s, pol);
+                if (L.scale_bytes)
+                    bulk_g2s(st + L.probs_bytes + L.meta_bytes, a.scale + t * kTile, L.scale_bytes, full + s, pol);
+            }
+            // every issued copy has landed before this thread leaves
+            for (int j = it - stages; j < it; ++j) {
+                if (j < 0) continue;
+                if (!mbar_wait(full + (j % stages), (uint32_t)(j / stages) & 1u, kWaitNs))
+                    atomicCAS(a.err, 0, (int32_t)kErrTimeout);
+            }
+        }
+        return;
+    }
+
+    const int px0 = (warp - 1) * 32;
+    int it = 0;
+    for (int64_t t = blockIdx.x; t < ntiles_full; t += gridDim.x, ++it) {
+        const int s = it % stages;
+        const uint32_t ph = (uint32_t)(it / stages) & 1u;
+        const uint8_t *st = stage0 + (size_t)s * L.stride;
+        if (!mbar_wait(full + s, ph, kWaitNs)) {
+            atomicCAS(a.err, 0, (int32_t)kErrTimeout);
+            return;
+        }
+        int row;
+        float w, sc;
+        pixel_info<DT>(a, t * kTile + px0 + lane, px0 + lane, st + L.probs_bytes,
+                       L.scale_bytes ? reinterpret_cast<const float *>(st + L.probs_bytes + L.meta_bytes) : nullptr,
+                       row, w, sc);
+        warp_tile<RULE, DT, true, IMAGE>(a, st, px0, lane, row, w, sc);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty + s);
+    }
+    if (ragged && blockIdx.x == gridDim.x - 1) {
+        int row;
+        float w, sc;
+        pixel_info<DT>(a, ntiles_full * kTile + px0 + lane, px0 + lane, nullptr, nullptr, row, w, sc);
+        warp_tile<RULE, DT, false, IMAGE>(a, a.probs + (size_t)ntiles_full * L.probs_bytes, px0, lane, row, w, sc);
+    }
+}
+
+int g_num_sms = 0;
+
+template <int RULE, int DT, bool IMAGE>
+void launch_one(const Args &a, cudaStream_t s)
+{
+    static bool configured = false;
+    const StageLayout L = stage_layout<DT>(a);
+    int stages = (int)((96u << 10) / L.stride);
+    stages = stages < 1 ? 1 : (stages > 4 ? 4 : stages);
+    const size_t smem = 128 + (size_t)stages * L.stride;
+    if (!configured) {
+        cudaFuncSetAttribute(k_scatter_tma<RULE, DT, IMAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 << 10);
+        configured = true;
+    }
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    const int64_t ntiles = (a.total_px + kTile - 1) / kTile;
+    int64_t grid = 2LL * g_num_sms;
+    if (grid > ntiles) grid = ntiles;
+    if (grid < 1) grid = 1;
+    k_scatter_tma<RULE, DT, IMAGE><<<(unsigned)grid, kThreads, smem, s>>>(a, stages);
+}
+
+template <int RULE, bool IMAGE>
+void launch_dt(sm_dtype dt, const Args &a, cudaStream_t s)
+{
+    if (dt == SM_F32) launch_one<RULE, SM_F32, IMAGE>(a, s);
+    else if (dt == SM_BF16) launch_one<RULE, SM_BF16, IMAGE>(a, s);
+    else launch_one<RULE, SM_FP8_E4M3, IMAGE>(a, s);
+}
+
+template <int RULE>
+void launch_rule(sm_dtype dt, const Args &a, cudaStream_t s)
+{
+    if (a.fcnt) launch_dt<RULE, true>(dt, a, s);
+    else launch_dt<RULE, false>(dt, a, s);
+}
+
+}  // namespace
+
+bool scatter_tma_supported(int c) { return c % 4 == 0 && c >= 4 && c <= 128; }
+
+void launch_scatter_tma(sm_rule rule, sm_dtype dtype, const void *probs, const float *scale,
+                        unsigned long long *keys, const int32_t *ids_in, int32_t *ids_out, int64_t total_px,
+                        int64_t npix, int c, const uint32_t *fcnt, int64_t n_x, float *acc, uint32_t *cnt,
+                        int32_t *err, cudaStream_t s)
+{
+    if (total_px <= 0) return;
+    Args a{static_cast<const uint8_t *>(probs), scale, keys, ids_in, ids_out, total_px, npix, c, fcnt, n_x, acc,
+           cnt, err, scale != nullptr && ((uintptr_t)scale & 15) == 0};
+    switch (rule) {
+    case SM_RULE_SUM: launch_rule<SM_RULE_SUM>(dtype, a, s); break;
+    case SM_RULE_LOGSUM: launch_rule<SM_RULE_LOGSUM>(dtype, a, s); break;
+    case SM_RULE_MAXSUM: launch_rule<SM_RULE_MAXSUM>(dtype, a, s); break;
+    default: launch_rule<SM_RULE_VOTE>(dtype, a, s); break;
+    }
+}
+
+}  // namespace lf
