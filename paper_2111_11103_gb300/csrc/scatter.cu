@@ -7,22 +7,24 @@
 // Design (GB300):
 //  * persistent CTAs, two per SM; warp 0 is a producer whose elected lane
 //    streams 256-pixel tiles into a ring of shared-memory stages with 1-D TMA
-//    bulk copies (cp.async.bulk, completion counted on an mbarrier).  A stage
-//    holds the tile's probabilities (L2 evict-first: read once) and the
-//    tile's per-pixel metadata: the z-buffer keys left by the raster (face
-//    mode; row = triangle of the nearest surface) or the resolved row map,
-//    and the per-pixel scales of BF16/FP8 storage;
+//    bulk copies (cp.async.bulk, completion counted on an mbarrier) and keeps
+//    the CTA's next tiles on their way into L2 with bulk L2 prefetches.  A
+//    stage holds the tile's probabilities (L2 evict-first: read once) and its
+//    per-pixel metadata: the z-buffer keys left by the raster (face mode; row
+//    = triangle of the nearest surface) or the resolved row map, and the
+//    per-pixel scales of BF16/FP8 storage;
 //  * 8 consumer warps, 32 pixels each.  A warp splits into groups of c/4
 //    lanes; each lane owns four classes and each group walks a contiguous run
-//    of pixels, keeping the running sum of phi(p) for the current row in
-//    registers, four pixels per software-pipelined step.  Only when the row
-//    changes (neighbouring pixels mostly see the same triangle) is the run
-//    flushed with one 16-byte vector reduction per lane into P, plus the run
+//    of pixels, four pixels per software-pipelined step, keeping the running
+//    sum of phi(p) for the current row in registers.  Only when the row (or
+//    the pixel weight) changes is the run flushed: the group's lanes together
+//    add one contiguous row of P with 16-byte vector reductions, plus the run
 //    length into the observation count;
+//  * log-sum multiplies up to four clamped probabilities (>= 2^-30 each, so
+//    no underflow) before one hardware log2 per class: sum_k log p_k =
+//    log prod_k p_k, up to rounding;
 //  * face mode: the consumers re-arm the z-buffer keys and write the row map
-//    when it is asked for, so no separate resolve pass runs;
-//  * log-sum uses the hardware log2 and converts each run sum to natural
-//    logarithms once per flush.
+//    when it is asked for, so no separate resolve pass runs.
 // Bounded waits: a wait longer than 2 s latches kErrTimeout; the producer
 // always waits for its own copies in flight before it leaves.
 #include <cuda_bf16.h>
@@ -35,10 +37,11 @@
 namespace lf {
 namespace {
 
-constexpr int kTile = 256;           // pixels per tile
-constexpr int kConsumerWarps = 8;    // 32 pixels each
+constexpr int kTile = 256;          // pixels per tile
+constexpr int kConsumerWarps = 8;   // 32 pixels each
 constexpr int kThreads = 32 * (1 + kConsumerWarps);
-constexpr int kUnroll = 4;           // pixels per software-pipelined step
+constexpr int kUnroll = 4;          // pixels per software-pipelined step
+constexpr int kMaxFactors = 4;      // probabilities multiplied before one log2
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr float kLn2 = 0.693147180559945309f;
 constexpr unsigned kFull = 0xffffffffu;
@@ -50,7 +53,7 @@ struct Elem {
 
 // Four consecutive classes starting at element index e (a multiple of 4).
 template <int DT, bool SMEM>
-__device__ __forceinline__ float4 load_quad(const uint8_t *base, int64_t e)
+__device__ __forceinline__ float4 load_quad(const uint8_t *base, int e)
 {
     if (DT == SM_F32) {
         const float4 *p = reinterpret_cast<const float4 *>(base + e * 4);
@@ -111,7 +114,7 @@ __host__ __device__ __forceinline__ StageLayout stage_layout(const Args &a)
 // Row, weight and scale of pixel p.  meta/sscale point at the stage's
 // metadata (null for the ragged tile, which reads global memory); i is the
 // pixel's index within its tile.
-template <int DT>
+template <int DT, bool IMAGE>
 __device__ __forceinline__ void pixel_info(const Args &a, int64_t p, int i, const uint8_t *meta, const float *sscale,
                                            int &row, float &w, float &sc)
 {
@@ -132,36 +135,55 @@ __device__ __forceinline__ void pixel_info(const Args &a, int64_t p, int i, cons
         atomicCAS(a.err, 0, (int32_t)kErrRowRange);
         row = -1;
     }
-    if (a.fcnt && row >= 0) w = __fdiv_rn(1.0f, (float)a.fcnt[(p / a.npix) * a.n_x + row]);
+    if (IMAGE && row >= 0) w = __fdiv_rn(1.0f, (float)a.fcnt[(p / a.npix) * a.n_x + row]);
     if (DT != SM_F32) sc = sscale ? sscale[i] : a.scale[p];
 }
 
-// Adds a finished run into its row: one 16-byte reduction per lane (four
-// classes), and the run length into the row's observation count.
+// Running state of one lane's four classes over the current run.
+struct Run {
+    float4 s;     // sum of w * phi (log-sum: natural logarithms)
+    float4 prod;  // log-sum: product of the clamped probabilities not yet logged
+    int nf;       // factors in prod
+};
+
+__device__ __forceinline__ void fold_logs(Run &r, float w)
+{
+    const float wl = w * kLn2;
+    r.s.x = fmaf(lg2_ftz(r.prod.x), wl, r.s.x);
+    r.s.y = fmaf(lg2_ftz(r.prod.y), wl, r.s.y);
+    r.s.z = fmaf(lg2_ftz(r.prod.z), wl, r.s.z);
+    r.s.w = fmaf(lg2_ftz(r.prod.w), wl, r.s.w);
+    r.prod = make_float4(1.f, 1.f, 1.f, 1.f);
+    r.nf = 0;
+}
+
+// Adds a finished run into its row: the group's lanes write one contiguous
+// row (16 bytes each), the first lane adds the run length to the count.
 template <int RULE>
-__device__ __forceinline__ void flush(const Args &a, float *accq, int cur, float4 s, uint32_t n, int q)
+__device__ __forceinline__ void flush(const Args &a, float *accq, int cur, float w, Run &r, uint32_t n, int q)
 {
     if (cur < 0) return;
-    if (RULE == SM_RULE_LOGSUM) s = make_float4(s.x * kLn2, s.y * kLn2, s.z * kLn2, s.w * kLn2);
-    red_add_v4(accq + (int64_t)cur * a.c, s);
+    if (RULE == SM_RULE_LOGSUM && r.nf > 0) fold_logs(r, w);
+    red_add_v4(accq + (int64_t)cur * a.c, r.s);
     if (q == 0) red_add_u32(a.cnt + cur, n);
 }
 
-// phi(p) of one pixel added into the run sum s (weight wk); pix points at
-// the pixel's first element (max-sum and vote scan the whole pixel).
+// phi(p) of one pixel added into the run (weight wk); pix points at the
+// pixel's first element (max-sum and vote scan the whole pixel).
 template <int RULE, int DT, bool SMEM>
-__device__ __forceinline__ void accumulate(float4 &s, float4 v, float wk, float sk, const uint8_t *pix, int q, int Q)
+__device__ __forceinline__ void accumulate(Run &r, float4 v, float wk, float sk, const uint8_t *pix, int q, int Q)
 {
     if (RULE == SM_RULE_SUM) {
-        s.x = fmaf(wk, v.x, s.x);
-        s.y = fmaf(wk, v.y, s.y);
-        s.z = fmaf(wk, v.z, s.z);
-        s.w = fmaf(wk, v.w, s.w);
+        r.s.x = fmaf(wk, v.x, r.s.x);
+        r.s.y = fmaf(wk, v.y, r.s.y);
+        r.s.z = fmaf(wk, v.z, r.s.z);
+        r.s.w = fmaf(wk, v.w, r.s.w);
     } else if (RULE == SM_RULE_LOGSUM) {
-        s.x = fmaf(wk, __log2f(fmaxf(v.x, kPMin)), s.x);
-        s.y = fmaf(wk, __log2f(fmaxf(v.y, kPMin)), s.y);
-        s.z = fmaf(wk, __log2f(fmaxf(v.z, kPMin)), s.z);
-        s.w = fmaf(wk, __log2f(fmaxf(v.w, kPMin)), s.w);
+        r.prod.x *= fmaxf(v.x, kPMin);
+        r.prod.y *= fmaxf(v.y, kPMin);
+        r.prod.z *= fmaxf(v.z, kPMin);
+        r.prod.w *= fmaxf(v.w, kPMin);
+        if (++r.nf == kMaxFactors) fold_logs(r, wk);
     } else {
         // maximum (and first arg max) of the whole pixel, scanned in class order
         float m = -INFINITY;
@@ -175,16 +197,16 @@ __device__ __forceinline__ void accumulate(float4 &s, float4 v, float wk, float 
             if (u.w > m) { m = u.w; am = 4 * j + 3; }
         }
         if (RULE == SM_RULE_MAXSUM) {
-            if (v.x == m) s.x = fmaf(wk, v.x, s.x);
-            if (v.y == m) s.y = fmaf(wk, v.y, s.y);
-            if (v.z == m) s.z = fmaf(wk, v.z, s.z);
-            if (v.w == m) s.w = fmaf(wk, v.w, s.w);
+            if (v.x == m) r.s.x = fmaf(wk, v.x, r.s.x);
+            if (v.y == m) r.s.y = fmaf(wk, v.y, r.s.y);
+            if (v.z == m) r.s.z = fmaf(wk, v.z, r.s.z);
+            if (v.w == m) r.s.w = fmaf(wk, v.w, r.s.w);
         } else {
             const int d = am - 4 * q;
-            if (d == 0) s.x += wk;
-            if (d == 1) s.y += wk;
-            if (d == 2) s.z += wk;
-            if (d == 3) s.w += wk;
+            if (d == 0) r.s.x += wk;
+            if (d == 1) r.s.y += wk;
+            if (d == 2) r.s.z += wk;
+            if (d == 3) r.s.w += wk;
         }
     }
 }
@@ -192,6 +214,7 @@ __device__ __forceinline__ void accumulate(float4 &s, float4 v, float wk, float 
 // One warp's 32 pixels of a tile.  base points at the tile's first element
 // (shared memory stage, or global memory for the ragged last tile); px0 is
 // the warp's first pixel within the tile; row/w/sc belong to pixel px0+lane.
+// A run is cut where the row or the pixel weight changes.
 template <int RULE, int DT, bool SMEM, bool IMAGE>
 __device__ __forceinline__ void warp_tile(const Args &a, const uint8_t *base, int px0, int lane, int row, float w,
                                           float sc)
@@ -207,8 +230,9 @@ __device__ __forceinline__ void warp_tile(const Args &a, const uint8_t *base, in
     const int pstride = a.c * ES;  // bytes per pixel
     const uint8_t *pb = base + (px0 + start) * pstride;  // this group's first pixel
     float *accq = a.acc + 4 * q;
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    Run run{make_float4(0.f, 0.f, 0.f, 0.f), make_float4(1.f, 1.f, 1.f, 1.f), 0};
     int cur = -1;
+    float curw = 1.0f;
     uint32_t n = 0;
     for (int i0 = 0; i0 < iters; i0 += kUnroll) {
         int r[kUnroll];
@@ -233,18 +257,21 @@ __device__ __forceinline__ void warp_tile(const Args &a, const uint8_t *base, in
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             if (r[u] == -2) continue;
-            if (r[u] != cur) {
-                flush<RULE>(a, accq, cur, s, n, q);
+            if (r[u] != cur || (IMAGE && wv[u] != curw)) {
+                flush<RULE>(a, accq, cur, curw, run, n, q);
                 cur = r[u];
-                s = make_float4(0.f, 0.f, 0.f, 0.f);
+                curw = wv[u];
+                run.s = make_float4(0.f, 0.f, 0.f, 0.f);
+                run.prod = make_float4(1.f, 1.f, 1.f, 1.f);
+                run.nf = 0;
                 n = 0;
             }
             if (r[u] < 0) continue;
-            accumulate<RULE, DT, SMEM>(s, v[u], wv[u], sv[u], pb + (i0 + u) * pstride, q, Q);
+            accumulate<RULE, DT, SMEM>(run, v[u], wv[u], sv[u], pb + (i0 + u) * pstride, q, Q);
             ++n;
         }
     }
-    if (active) flush<RULE>(a, accq, cur, s, n, q);
+    if (active) flush<RULE>(a, accq, cur, curw, run, n, q);
 }
 
 template <int RULE, int DT, bool IMAGE>
@@ -272,6 +299,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
         if (lane == 0) {
             const uint64_t pol = l2_evict_first();
             const uint32_t tx = L.probs_bytes + L.meta_bytes + L.scale_bytes;
+            const int64_t ahead = (int64_t)((256u << 10) / L.probs_bytes + 1) * gridDim.x;
             int it = 0;
             for (int64_t t = blockIdx.x; t < ntiles_full; t += gridDim.x, ++it) {
                 const int s = it % stages;
@@ -288,6 +316,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
                 bulk_g2s(st + L.probs_bytes, meta, L.meta_bytes, full + s, pol);
                 if (L.scale_bytes)
                     bulk_g2s(st + L.probs_bytes + L.meta_bytes, a.scale + t * kTile, L.scale_bytes, full + s, pol);
+                // keep ~256 KB of this CTA's future tiles on their way into L2
+                if (t + ahead < ntiles_full)
+                    bulk_prefetch_l2(a.probs + (size_t)(t + ahead) * L.probs_bytes, L.probs_bytes);
             }
             // every issued copy has landed before this thread leaves
             for (int j = it - stages; j < it; ++j) {
@@ -311,9 +342,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
         }
         int row;
         float w, sc;
-        pixel_info<DT>(a, t * kTile + px0 + lane, px0 + lane, st + L.probs_bytes,
-                       L.scale_bytes ? reinterpret_cast<const float *>(st + L.probs_bytes + L.meta_bytes) : nullptr,
-                       row, w, sc);
+        pixel_info<DT, IMAGE>(
+            a, t * kTile + px0 + lane, px0 + lane, st + L.probs_bytes,
+            L.scale_bytes ? reinterpret_cast<const float *>(st + L.probs_bytes + L.meta_bytes) : nullptr, row, w,
+            sc);
         warp_tile<RULE, DT, true, IMAGE>(a, st, px0, lane, row, w, sc);
         __syncwarp();
         if (lane == 0) mbar_arrive(empty + s);
@@ -321,12 +353,339 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
     if (ragged && blockIdx.x == gridDim.x - 1) {
         int row;
         float w, sc;
-        pixel_info<DT>(a, ntiles_full * kTile + px0 + lane, px0 + lane, nullptr, nullptr, row, w, sc);
+        pixel_info<DT, IMAGE>(a, ntiles_full * kTile + px0 + lane, px0 + lane, nullptr, nullptr, row, w, sc);
         warp_tile<RULE, DT, false, IMAGE>(a, a.probs + (size_t)ntiles_full * L.probs_bytes, px0, lane, row, w, sc);
     }
 }
 
+// ---------------------------------------------------------------------------
+// Lane-pair path for c = 40 and c = 20 (QL = quads per lane, compile time).
+// A pixel stream is owned by two lanes (quads j = 2m + l, l the lane's
+// parity), so a pair's reductions of one row land in the same 32-byte
+// sectors.  A warp runs 16 streams of 4 consecutive pixels over a 64-pixel
+// tile; stream k visits its pixels in the order (i + k) mod 4, which makes
+// the 128-bit shared-memory reads of 8 lanes cover 32 distinct banks.  The
+// per-pixel control work is issued once per pair instead of once per group of
+// c/4 lanes.  Each consumer warp owns its own ring of stages (filled
+// round-robin by the producer), so every mbarrier advances phase by phase.
+// ---------------------------------------------------------------------------
+constexpr int kPairTile = 64;    // pixels per tile: 16 streams x 4 pixels
+constexpr int kPairWarps = 4;    // consumer warps per CTA, two CTAs per SM
+constexpr int kPairThreads = 32 * (1 + kPairWarps);
+
+template <int DT>
+__host__ __device__ __forceinline__ StageLayout pair_layout(const Args &a)
+{
+    StageLayout L;
+    L.probs_bytes = (uint32_t)kPairTile * a.c * Elem<DT>::size;
+    L.meta_bytes = kPairTile * (a.keys ? 8u : 4u);
+    L.scale_bytes = (DT != SM_F32 && a.scale_bulk) ? kPairTile * 4u : 0u;
+    L.stride = (L.probs_bytes + L.meta_bytes + L.scale_bytes + 127u) & ~127u;
+    return L;
+}
+
+// Row, weight and scale of one pixel of a stream (both lanes of the pair
+// read it; the even lane re-arms the key and writes the row map).
+template <int DT, bool IMAGE>
+__device__ __forceinline__ void pair_meta(const Args &a, int64_t p, int i, const uint8_t *meta, const float *sscale,
+                                          bool writer, int &row, float &w, float &sc)
+{
+    row = -1;
+    w = 1.0f;
+    sc = 1.0f;
+    if (p >= a.total_px) return;
+    if (a.keys) {
+        const unsigned long long key =
+            meta ? reinterpret_cast<const unsigned long long *>(meta)[i] : a.keys[p];
+        if (writer) a.keys[p] = kEmptyKey;
+        row = (key == kEmptyKey) ? -1 : (int)(unsigned int)key;
+    } else {
+        row = meta ? reinterpret_cast<const int32_t *>(meta)[i] : a.ids_in[p];
+    }
+    if (writer && a.ids_out) a.ids_out[p] = row;
+    if (row >= a.n_x) {
+        if (writer) atomicCAS(a.err, 0, (int32_t)kErrRowRange);
+        row = -1;
+    }
+    if (IMAGE && row >= 0) w = __fdiv_rn(1.0f, (float)a.fcnt[(p / a.npix) * a.n_x + row]);
+    if (DT != SM_F32) sc = sscale ? sscale[i] : a.scale[p];
+}
+
+template <int QL, int RULE, bool IMAGE>
+__device__ __forceinline__ void pair_flush(const Args &a, int cur, float w, const float4 (&R)[QL], int nf, uint32_t n,
+                                           int l, int Q)
+{
+    float *dst = a.acc + (int64_t)cur * a.c;
+#pragma unroll
+    for (int m = 0; m < QL; ++m) {
+        const int j = 2 * m + l;
+        if (j >= Q) continue;
+        float4 v = R[m];
+        if (RULE == SM_RULE_LOGSUM) {
+            // R holds the product of the run's nf clamped probabilities
+            const float wl = (IMAGE ? w : 1.0f) * kLn2;
+            v = nf ? make_float4(lg2_ftz(v.x) * wl, lg2_ftz(v.y) * wl, lg2_ftz(v.z) * wl, lg2_ftz(v.w) * wl)
+                   : make_float4(0.f, 0.f, 0.f, 0.f);
+        } else if (IMAGE) {
+            v = make_float4(v.x * w, v.y * w, v.z * w, v.w * w);
+        }
+        red_add_v4(dst + 4 * j, v);
+    }
+    if (l == 0) red_add_u32(a.cnt + cur, n);
+}
+
+template <int QL, int DT, bool SMEM>
+__device__ __forceinline__ void pair_load(float4 (&v)[QL], const uint8_t *pix, int l, int Q)
+{
+#pragma unroll
+    for (int m = 0; m < QL; ++m) {
+        const int j = 2 * m + l;
+        v[m] = (j < Q) ? load_quad<DT, SMEM>(pix, 4 * j) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// One warp's 64-pixel tile: stream k = lane / 2 takes pixels 4k .. 4k+3.
+// Runs are cut where the row or the weight changes; log-sum runs multiply at
+// most kMaxFactors clamped probabilities before their logarithm is taken
+// (at most 4 pixels per stream and tile, so exactly once per run).
+template <int QL, int RULE, int DT, bool SMEM, bool IMAGE>
+__device__ __forceinline__ void pair_tile(const Args &a, const uint8_t *tile, const uint8_t *meta,
+                                          const float *sscale, int64_t tile_p0, int lane)
+{
+    constexpr int ES = Elem<DT>::size;
+    const int Q = a.c >> 2;
+    const int k = lane >> 1, l = lane & 1;
+    const int pstride = a.c * ES;
+    int row[4];
+    float w[4], sc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int pi = 4 * k + ((i + k) & 3);
+        pair_meta<DT, IMAGE>(a, tile_p0 + pi, pi, meta, sscale, l == 0, row[i], w[i], sc[i]);
+    }
+    const float4 init = (RULE == SM_RULE_LOGSUM) ? make_float4(1.f, 1.f, 1.f, 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 R[QL], vn[QL];
+    int cur = -1, nf = 0;
+    float curw = 1.0f;
+    uint32_t n = 0;
+    if (row[0] >= 0) pair_load<QL, DT, SMEM>(vn, tile + (4 * k + (k & 3)) * pstride, l, Q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float4 v[QL];
+#pragma unroll
+        for (int m = 0; m < QL; ++m) v[m] = vn[m];
+        if (i < 3 && row[i + 1] >= 0) pair_load<QL, DT, SMEM>(vn, tile + (4 * k + ((i + 1 + k) & 3)) * pstride, l, Q);
+        const int r = row[i];
+        if (r != cur || (IMAGE && w[i] != curw)) {
+            if (cur >= 0) pair_flush<QL, RULE, IMAGE>(a, cur, curw, R, nf, n, l, Q);
+            cur = r;
+            curw = w[i];
+            n = 0;
+            nf = 0;
+#pragma unroll
+            for (int m = 0; m < QL; ++m) R[m] = init;
+        }
+        if (r < 0) continue;
+        if (DT != SM_F32) {
+#pragma unroll
+            for (int m = 0; m < QL; ++m) v[m] = scale4(v[m], sc[i]);
+        }
+        if (RULE == SM_RULE_SUM) {
+#pragma unroll
+            for (int m = 0; m < QL; ++m) {
+                R[m].x += v[m].x;
+                R[m].y += v[m].y;
+                R[m].z += v[m].z;
+                R[m].w += v[m].w;
+            }
+        } else if (RULE == SM_RULE_LOGSUM) {
+#pragma unroll
+            for (int m = 0; m < QL; ++m) {
+                R[m].x *= fmaxf(v[m].x, kPMin);
+                R[m].y *= fmaxf(v[m].y, kPMin);
+                R[m].z *= fmaxf(v[m].z, kPMin);
+                R[m].w *= fmaxf(v[m].w, kPMin);
+            }
+            ++nf;
+        } else {
+            // maximum and first arg max of the whole pixel: each lane scans
+            // its quads in class order, then the pair combines (ties go to
+            // the lower class index)
+            float m = -INFINITY;
+            int am = 0x7fffffff;
+#pragma unroll
+            for (int mm = 0; mm < QL; ++mm) {
+                const int j = 2 * mm + l;
+                if (j >= Q) continue;
+                if (v[mm].x > m) { m = v[mm].x; am = 4 * j; }
+                if (v[mm].y > m) { m = v[mm].y; am = 4 * j + 1; }
+                if (v[mm].z > m) { m = v[mm].z; am = 4 * j + 2; }
+                if (v[mm].w > m) { m = v[mm].w; am = 4 * j + 3; }
+            }
+            // both lanes of a pair share the stream's row, so they reach this
+            // point together; other pairs may have skipped a background pixel
+            const unsigned pair = 3u << (lane & ~1);
+            const float mo = __shfl_xor_sync(pair, m, 1);
+            const int amo = __shfl_xor_sync(pair, am, 1);
+            if (mo > m || (mo == m && amo < am)) {
+                m = mo;
+                am = amo;
+            }
+#pragma unroll
+            for (int mm = 0; mm < QL; ++mm) {
+                const int j = 2 * mm + l;
+                if (RULE == SM_RULE_MAXSUM) {
+                    if (v[mm].x == m) R[mm].x += v[mm].x;
+                    if (v[mm].y == m) R[mm].y += v[mm].y;
+                    if (v[mm].z == m) R[mm].z += v[mm].z;
+                    if (v[mm].w == m) R[mm].w += v[mm].w;
+                } else {
+                    if (am == 4 * j) R[mm].x += 1.0f;
+                    if (am == 4 * j + 1) R[mm].y += 1.0f;
+                    if (am == 4 * j + 2) R[mm].z += 1.0f;
+                    if (am == 4 * j + 3) R[mm].w += 1.0f;
+                }
+            }
+        }
+        ++n;
+    }
+    if (cur >= 0) pair_flush<QL, RULE, IMAGE>(a, cur, curw, R, nf, n, l, Q);
+}
+
+template <int QL, int RULE, int DT, bool IMAGE>
+__global__ void __launch_bounds__(kPairThreads, 2) k_scatter_pair(Args a, int spw)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int nst = kPairWarps * spw;  // stage s of consumer warp w is w * spw + s
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + nst;
+    uint8_t *stage0 = smem + 512;
+    const StageLayout L = pair_layout<DT>(a);
+    const int64_t ntiles_full = a.total_px / kPairTile;
+    const bool ragged = ntiles_full * kPairTile < a.total_px;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < nst; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const uint64_t pol = l2_evict_first();
+            const uint32_t tx = L.probs_bytes + L.meta_bytes + L.scale_bytes;
+            const int64_t ahead = (int64_t)((256u << 10) / L.probs_bytes + 1) * gridDim.x;
+            int64_t it = 0;
+            for (int64_t t = blockIdx.x; t < ntiles_full; t += gridDim.x, ++it) {
+                const int w = (int)(it % kPairWarps);
+                const int64_t kk = it / kPairWarps;  // this warp's kk-th tile
+                const int s = w * spw + (int)(kk % spw);
+                const uint32_t ph = (uint32_t)(kk / spw) & 1u;
+                if (kk >= spw && !mbar_wait(empty + s, ph ^ 1u, kWaitNs)) {
+                    atomicCAS(a.err, 0, (int32_t)kErrTimeout);
+                    break;
+                }
+                uint8_t *st = stage0 + (size_t)s * L.stride;
+                mbar_arrive_expect_tx(full + s, tx);
+                bulk_g2s(st, a.probs + (size_t)t * L.probs_bytes, L.probs_bytes, full + s, pol);
+                const void *meta = a.keys ? static_cast<const void *>(a.keys + t * kPairTile)
+                                          : static_cast<const void *>(a.ids_in + t * kPairTile);
+                bulk_g2s(st + L.probs_bytes, meta, L.meta_bytes, full + s, pol);
+                if (L.scale_bytes)
+                    bulk_g2s(st + L.probs_bytes + L.meta_bytes, a.scale + t * kPairTile, L.scale_bytes, full + s,
+                             pol);
+                if (t + ahead < ntiles_full)
+                    bulk_prefetch_l2(a.probs + (size_t)(t + ahead) * L.probs_bytes, L.probs_bytes);
+            }
+            // every issued copy has landed before this thread leaves
+            for (int64_t j = it - (int64_t)nst; j < it; ++j) {
+                if (j < 0) continue;
+                const int w = (int)(j % kPairWarps);
+                const int64_t kk = j / kPairWarps;
+                if (!mbar_wait(full + w * spw + (int)(kk % spw), (uint32_t)(kk / spw) & 1u, kWaitNs))
+                    atomicCAS(a.err, 0, (int32_t)kErrTimeout);
+            }
+        }
+        return;
+    }
+
+    const int cw = warp - 1;
+    int64_t kk = 0;
+    for (int64_t t = blockIdx.x + (int64_t)cw * gridDim.x; t < ntiles_full;
+         t += (int64_t)kPairWarps * gridDim.x, ++kk) {
+        const int s = cw * spw + (int)(kk % spw);
+        const uint32_t ph = (uint32_t)(kk / spw) & 1u;
+        const uint8_t *st = stage0 + (size_t)s * L.stride;
+        if (!mbar_wait(full + s, ph, kWaitNs)) {
+            atomicCAS(a.err, 0, (int32_t)kErrTimeout);
+            return;
+        }
+        pair_tile<QL, RULE, DT, true, IMAGE>(
+            a, st, st + L.probs_bytes,
+            L.scale_bytes ? reinterpret_cast<const float *>(st + L.probs_bytes + L.meta_bytes) : nullptr,
+            t * kPairTile, lane);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty + s);
+    }
+    if (ragged && cw == 0 && blockIdx.x == gridDim.x - 1)
+        pair_tile<QL, RULE, DT, false, IMAGE>(a, a.probs + (size_t)ntiles_full * L.probs_bytes, nullptr, nullptr,
+                                              ntiles_full * kPairTile, lane);
+}
+
 int g_num_sms = 0;
+
+void ensure_num_sms()
+{
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+}
+
+template <int QL, int RULE, int DT, bool IMAGE>
+void launch_pair(const Args &a, cudaStream_t s)
+{
+    static bool configured = false;
+    const StageLayout L = pair_layout<DT>(a);
+    int spw = (int)((96u << 10) / (kPairWarps * L.stride));
+    spw = spw < 1 ? 1 : (spw > 4 ? 4 : spw);
+    const size_t smem = 512 + (size_t)kPairWarps * spw * L.stride;
+    if (!configured) {
+        cudaFuncSetAttribute(k_scatter_pair<QL, RULE, DT, IMAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 << 10);
+        configured = true;
+    }
+    ensure_num_sms();
+    const int64_t ntiles = (a.total_px + kPairTile - 1) / kPairTile;
+    int64_t grid = 2LL * g_num_sms;
+    if (grid > ntiles) grid = ntiles;
+    if (grid < 1) grid = 1;
+    k_scatter_pair<QL, RULE, DT, IMAGE><<<(unsigned)grid, kPairThreads, smem, s>>>(a, spw);
+}
+
+template <int RULE, bool IMAGE>
+bool launch_pair_dt(sm_dtype dt, const Args &a, cudaStream_t s)
+{
+    if (a.c == 40) {
+        if (dt == SM_F32) launch_pair<5, RULE, SM_F32, IMAGE>(a, s);
+        else if (dt == SM_BF16) launch_pair<5, RULE, SM_BF16, IMAGE>(a, s);
+        else launch_pair<5, RULE, SM_FP8_E4M3, IMAGE>(a, s);
+        return true;
+    }
+    if (a.c == 20) {
+        if (dt == SM_F32) launch_pair<3, RULE, SM_F32, IMAGE>(a, s);
+        else if (dt == SM_BF16) launch_pair<3, RULE, SM_BF16, IMAGE>(a, s);
+        else launch_pair<3, RULE, SM_FP8_E4M3, IMAGE>(a, s);
+        return true;
+    }
+    return false;
+}
 
 template <int RULE, int DT, bool IMAGE>
 void launch_one(const Args &a, cudaStream_t s)
@@ -341,12 +700,7 @@ void launch_one(const Args &a, cudaStream_t s)
                              200 << 10);
         configured = true;
     }
-    if (g_num_sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (g_num_sms <= 0) g_num_sms = 1;
-    }
+    ensure_num_sms();
     const int64_t ntiles = (a.total_px + kTile - 1) / kTile;
     int64_t grid = 2LL * g_num_sms;
     if (grid > ntiles) grid = ntiles;
@@ -365,8 +719,11 @@ void launch_dt(sm_dtype dt, const Args &a, cudaStream_t s)
 template <int RULE>
 void launch_rule(sm_dtype dt, const Args &a, cudaStream_t s)
 {
-    if (a.fcnt) launch_dt<RULE, true>(dt, a, s);
-    else launch_dt<RULE, false>(dt, a, s);
+    if (a.fcnt) {
+        if (!launch_pair_dt<RULE, true>(dt, a, s)) launch_dt<RULE, true>(dt, a, s);
+    } else {
+        if (!launch_pair_dt<RULE, false>(dt, a, s)) launch_dt<RULE, false>(dt, a, s);
+    }
 }
 
 }  // namespace
