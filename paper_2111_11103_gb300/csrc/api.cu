@@ -100,13 +100,14 @@ sm_status grow(T **buf, int64_t *cap, int64_t need, cudaStream_t s, int fill, co
 
 size_t dtype_size(sm_dtype d) { return d == SM_F32 ? 4 : (d == SM_BF16 ? 2 : 1); }
 
-// Frames per batch: a batch's 64-bit z-buffers stay within ~12 MB (they are
-// hammered by atomics and, double-buffered, should live in L2 next to the
-// hot accumulator rows); the per-frame row histograms of the image weights
-// within ~512 MB.
+// Frames per batch: a batch's 64-bit z-buffers take up to ~48 MB (16 frames
+// of 640 x 480).  Longer batches keep the mostly-culled raster launches and
+// the streaming scatter launches long enough to fill the GPU, which matters
+// more than keeping both z-buffer slots in L2; the per-frame row histograms
+// of the image weights stay within ~512 MB.
 int batch_frames(const sm_mesh *m, int64_t npix, int N)
 {
-    int64_t B = (int64_t)(12u << 20) / (npix * 8);
+    int64_t B = (int64_t)(48u << 20) / (npix * 8);
     if (m->weight == SM_WEIGHT_IMAGE && m->n_x > 0) {
         const int64_t Bi = (int64_t)(512u << 20) / (m->n_x * 4);
         if (Bi < B) B = Bi;

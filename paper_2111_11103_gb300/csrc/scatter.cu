@@ -415,7 +415,7 @@ template <int QL, int RULE, bool IMAGE>
 __device__ __forceinline__ void pair_flush(const Args &a, int cur, float w, const float4 (&R)[QL], int nf, uint32_t n,
                                            int l, int Q)
 {
-    float *dst = a.acc + (int64_t)cur * a.c;
+    float *dst = a.acc + (int64_t)cur * (4 * Q);
 #pragma unroll
     for (int m = 0; m < QL; ++m) {
         const int j = 2 * m + l;
@@ -453,9 +453,10 @@ __device__ __forceinline__ void pair_tile(const Args &a, const uint8_t *tile, co
                                           const float *sscale, int64_t tile_p0, int lane)
 {
     constexpr int ES = Elem<DT>::size;
-    const int Q = a.c >> 2;
+    constexpr int C = (QL == 5) ? 40 : 20;  // the two class counts this path serves
+    constexpr int Q = C / 4;
+    constexpr int pstride = C * ES;         // bytes per pixel, known at compile time
     const int k = lane >> 1, l = lane & 1;
-    const int pstride = a.c * ES;
     int row[4];
     float w[4], sc[4];
 #pragma unroll
