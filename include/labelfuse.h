@@ -197,6 +197,38 @@ const char *sm_status_string(sm_status s);
 /* One-line detail of the calling thread's last failed call ("" if none). */
 const char *sm_last_error(void);
 
+/* Allocation-free rendering of row maps.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory, for
+ * example a plugin whose host application owns every device allocation
+ * through its own pool, or a latency-bound loop that must not call
+ * cudaMalloc / cudaFree because they can block and synchronise the device.
+ *
+ * Renders N frames of a mesh given as plain arrays (no sm_mesh, no upload)
+ * into d_idmap_out, N x H x W int32, with the same renderer as
+ * sm_fuse_frames: every pixel gets the index of the triangle it sees (one row
+ * per triangle, i.e. what sm_fuse_frames writes for a mesh uploaded without
+ * texel steps), -1 for background.  Faces with an index outside [0, V) are
+ * never drawn.  d_vertices V x 3 float32, d_faces F x 3 int32, d_K N
+ * intrinsics and d_cam_to_world N x 16 float64 are device pointers.
+ *
+ * Scratch: the z-buffer of one frame and the N cameras live in a static
+ * array of the library's device memory (SM_NOALLOC_MAX_PIXELS 64-bit keys +
+ * SM_NOALLOC_MAX_FRAMES cameras, about 12 MiB), which every GPU that loads
+ * the library holds until the process exits.  The call allocates nothing:
+ * no cudaMalloc, cudaFree or allocating library routine.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents (each
+ *     call re-arms the z-buffer first).  Calls whose work overlaps on the GPU
+ *     race on it: serialise them (one stream, or events).
+ * Errors: SM_ERR_INVALID_ARG (NULL pointer, H x W > SM_NOALLOC_MAX_PIXELS,
+ * N > SM_NOALLOC_MAX_FRAMES, V or F >= 2^31), SM_ERR_CUDA. */
+#define SM_NOALLOC_MAX_PIXELS 1572864 /* 1.5 Mi pixels, e.g. 1296 x 968 */
+#define SM_NOALLOC_MAX_FRAMES 1024
+sm_status sm_render_rows_noalloc(const float *d_vertices, int64_t V, const int32_t *d_faces, int64_t F,
+                                 const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N, int32_t H,
+                                 int32_t W, int32_t *d_idmap_out, void *stream);
+
 /* Kernel timing: when enabled, every launch of the kernels below is bracketed
  * by CUDA events on the launching stream.  sm_profile_read synchronises those
  * events and returns the launch count and total device time since the last

@@ -532,6 +532,28 @@ sm_status sm_mesh_free(sm_mesh *m)
     return SM_OK;
 }
 
+sm_status sm_render_rows_noalloc(const float *d_vertices, int64_t V, const int32_t *d_faces, int64_t F,
+                                 const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N, int32_t H,
+                                 int32_t W, int32_t *d_idmap_out, void *stream)
+{
+    sm_status st = check_image(N, H, W);
+    if (st != SM_OK) return st;
+    if (V < 0 || F < 0 || V >= (1LL << 31) || F >= (1LL << 31))
+        return fail(SM_ERR_INVALID_ARG, "V or F outside [0, 2^31)");
+    if ((int64_t)H * W > SM_NOALLOC_MAX_PIXELS)
+        return fail(SM_ERR_INVALID_ARG, "H x W = %lld pixels exceeds the static scratch (%d)", (long long)H * W,
+                    SM_NOALLOC_MAX_PIXELS);
+    if (N > SM_NOALLOC_MAX_FRAMES)
+        return fail(SM_ERR_INVALID_ARG, "N = %d frames exceeds the static scratch (%d)", N, SM_NOALLOC_MAX_FRAMES);
+    if (N == 0) return SM_OK;
+    if (!d_K || !d_cam_to_world || !d_idmap_out || (F > 0 && (!d_vertices || !d_faces)))
+        return fail(SM_ERR_INVALID_ARG, "NULL pointer");
+    cudaError_t e = lf::launch_render_rows_noalloc(d_vertices, V, d_faces, F, d_K, d_cam_to_world, N, H, W,
+                                                   d_idmap_out, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "render rows (no allocation)");
+    return SM_OK;
+}
+
 sm_status sm_profile_enable(sm_mesh *m, int32_t on)
 {
     if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");

@@ -44,6 +44,11 @@ void launch_resolve(unsigned long long *keys, int nb, int H, int W, const int32_
                     const float4 *V, const int4 *faces, const Camera *cams, int frame0, int32_t *idmap,
                     int32_t *idmap2, cudaStream_t s);
 
+// Row maps of N frames with the library's static scratch (no allocation).
+cudaError_t launch_render_rows_noalloc(const float *V, int64_t nV, const int32_t *faces, int64_t F,
+                                       const sm_intrinsics *K, const double *T, int N, int H, int W, int32_t *idmap,
+                                       cudaStream_t s);
+
 // ---- kernels (fuse.cu) ----
 // Row histogram from a row map, or (idmap == null) from z-buffer keys.
 void launch_count(const int32_t *idmap, const unsigned long long *keys, int64_t npix, int nb, uint32_t *fcnt,

@@ -7,6 +7,8 @@
 // compiler never contracts into FMAs, so the integer decisions (snapped vertex
 // positions, coverage, the depth key) are the same on every run and match the
 // project's raster reading bit for bit.
+#include <mutex>
+
 #include "lf_internal.cuh"
 #include "ptx.cuh"
 
@@ -329,7 +331,105 @@ __global__ void __launch_bounds__(256) k_resolve(unsigned long long *__restrict_
     if (idmap2) idmap2[p] = row;
 }
 
+// ---- raster for the allocation-free entry point (sm_render_rows_noalloc) ----
+
+// Same coverage and depth rules as k_raster, for one frame, reading the
+// caller's plain V x 3 vertices and F x 3 indices directly (no packed copies,
+// no cluster culling).  Faces with an index outside [0, V) are never drawn.
+__global__ void __launch_bounds__(256) k_raster_flat(const float *__restrict__ V, int64_t nV,
+                                                     const int32_t *__restrict__ faces, int64_t F,
+                                                     const Camera *__restrict__ cam, int H, int W,
+                                                     unsigned long long *__restrict__ keys)
+{
+    __shared__ float A[12];
+    if (threadIdx.x < 12) A[threadIdx.x] = cam->a[threadIdx.x];
+    __syncthreads();
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F) return;
+    const int i0 = faces[3 * f], i1 = faces[3 * f + 1], i2 = faces[3 * f + 2];
+    if (i0 < 0 || i0 >= nV || i1 < 0 || i1 >= nV || i2 < 0 || i2 >= nV) return;
+    float4 P[3];
+    const int ix[3] = {i0, i1, i2};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) P[k] = make_float4(V[3 * (int64_t)ix[k]], V[3 * (int64_t)ix[k] + 1],
+                                                   V[3 * (int64_t)ix[k] + 2], 0.0f);
+    Tri t;
+    if (!setup_triangle(A, P, make_int4(0, 1, 2, 1), t)) return;
+    int minx = min(t.x[0], min(t.x[1], t.x[2])), maxx = max(t.x[0], max(t.x[1], t.x[2]));
+    int miny = min(t.y[0], min(t.y[1], t.y[2])), maxy = max(t.y[0], max(t.y[1], t.y[2]));
+    int x0 = max(ceil256(minx), 0), x1 = min(floor256(maxx), W - 1);
+    int y0 = max(ceil256(miny), 0), y1 = min(floor256(maxy), H - 1);
+    if (x0 > x1 || y0 > y1) return;
+    if (maxx - minx <= (1 << 14) && maxy - miny <= (1 << 14))
+        raster_box<int>(t, x0, x1, y0, y1, (unsigned int)f, keys, W);
+    else
+        raster_box<long long>(t, x0, x1, y0, y1, (unsigned int)f, keys, W);
+}
+
+__global__ void k_fill_empty(unsigned long long *__restrict__ keys, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) keys[i] = kEmptyKey;
+}
+
 }  // namespace
+
+// Scratch of sm_render_rows_noalloc, in the library's static device memory
+// (present on every GPU that loads the library, for the life of the process):
+// the z-buffer of one frame (SM_NOALLOC_MAX_PIXELS 64-bit keys) followed by
+// the per-frame cameras (SM_NOALLOC_MAX_FRAMES x 48 bytes = 6 words each).
+// Host code may not use this name as an address; it asks the runtime for the
+// device address once per device (below).
+static __device__ __align__(256) unsigned long long
+    g_noalloc_scratch[SM_NOALLOC_MAX_PIXELS + 6 * SM_NOALLOC_MAX_FRAMES];
+
+namespace {
+std::mutex g_noalloc_mu;
+unsigned long long *g_noalloc_ptr[64] = {};  // device address of the scratch, per device ordinal
+}  // namespace
+
+// Device address of the static scratch on the current device; the first call
+// on a device looks it up (cudaGetSymbolAddress, which needs that device
+// current and allocates nothing).
+cudaError_t noalloc_scratch(unsigned long long **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<unsigned long long *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+// Renders N frames into d_idmap_out with the static scratch (see labelfuse.h).
+cudaError_t launch_render_rows_noalloc(const float *V, int64_t nV, const int32_t *faces, int64_t F,
+                                       const sm_intrinsics *K, const double *T, int N, int H, int W, int32_t *idmap,
+                                       cudaStream_t s)
+{
+    unsigned long long *scratch = nullptr;
+    cudaError_t e = noalloc_scratch(&scratch);
+    if (e != cudaSuccess) return e;
+    unsigned long long *keys = scratch;
+    Camera *cams = reinterpret_cast<Camera *>(scratch + SM_NOALLOC_MAX_PIXELS);
+    const int64_t npix = (int64_t)H * W;
+    // the scratch keeps the previous call's contents: re-arm the z-buffer
+    k_fill_empty<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(keys, npix);
+    k_project<<<(N + 127) / 128, 128, 0, s>>>(K, T, N, cams);
+    for (int i = 0; i < N; ++i) {
+        if (F > 0) k_raster_flat<<<(unsigned)((F + 255) / 256), 256, 0, s>>>(V, nV, faces, F, cams + i, H, W, keys);
+        // resolve in face mode (row = triangle); re-arms the z-buffer
+        k_resolve<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(keys, npix, H, W, nullptr, nullptr, nullptr, nullptr,
+                                                                  cams, i, idmap + (int64_t)i * npix, nullptr);
+    }
+    return cudaGetLastError();
+}
 
 void launch_project(const sm_intrinsics *K, const double *T, int N, Camera *out, cudaStream_t s)
 {

@@ -23,7 +23,9 @@ SM_OK = 0
 SM_MAX_CLASSES = 254
 SYMBOLS = ["sm_mesh_upload", "sm_fuse_frames", "sm_normalise", "sm_render_labels", "sm_render_idmap", "sm_reset",
            "sm_read_state", "sm_load_state", "sm_check", "sm_num_rows", "sm_num_classes", "sm_mesh_free",
-           "sm_status_string", "sm_last_error", "sm_profile_enable", "sm_profile_read"]
+           "sm_status_string", "sm_last_error", "sm_profile_enable", "sm_profile_read", "sm_render_rows_noalloc"]
+SM_NOALLOC_MAX_PIXELS = 1572864
+SM_NOALLOC_MAX_FRAMES = 1024
 
 
 class LabelFuseError(RuntimeError):
@@ -55,6 +57,7 @@ def lib() -> ctypes.CDLL:
             "sm_check": [P, P],
             "sm_mesh_free": [P],
             "sm_profile_enable": [P, i32],
+            "sm_render_rows_noalloc": [P, i64, P, i64, P, P, i32, i32, i32, P, P],
             "sm_profile_read": [P, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)],
         }
         for name, args in sig.items():
@@ -164,6 +167,15 @@ def sm_status_string(status: int) -> str:
 
 def sm_last_error() -> str:
     return lib().sm_last_error().decode()
+
+
+def sm_render_rows_noalloc(vertices, faces, K, cam_to_world, N: int, H: int, W: int, idmap_out, stream=None):
+    """Row maps (triangle per pixel) of N frames without any device allocation;
+    for callers whose device memory is owned elsewhere (see labelfuse.h)."""
+    V = int(vertices.shape[0]) if vertices is not None else 0
+    F = int(faces.shape[0]) if faces is not None else 0
+    _check(lib().sm_render_rows_noalloc(_ptr(vertices), V, _ptr(faces), F, _ptr(K), _ptr(cam_to_world), int(N),
+                                        int(H), int(W), _ptr(idmap_out), _stream(stream)))
 
 
 def sm_profile_enable(mesh: int, on: bool = True):
