@@ -164,6 +164,26 @@ sm_status sm_render_labels(sm_mesh *m, const sm_intrinsics *d_K, const double *d
 sm_status sm_render_idmap(sm_mesh *m, const int32_t *d_idmap, int64_t n_pixels, uint8_t *d_labels_out,
                           void *stream);
 
+/* End to end from host memory: fuses N frames whose predictions, scales and
+ * cameras are in HOST memory (pinned memory lets the copies overlap the
+ * work), then normalises and renders every frame's label image back into
+ * host memory.  Equivalent to copying the inputs to the device and calling
+ * sm_fuse_frames, sm_normalise and sm_render_idmap, but streamed: frames move
+ * host -> device in batches on a copy stream, double-buffered, while the
+ * previous batch is rendered and fused; row maps stay on the device.
+ *
+ *   h_probs        N x H x W x c in `dtype` (host), h_scale N x H x W (host,
+ *                  BF16/FP8 only), h_K N intrinsics, h_cam_to_world N x 16.
+ *   h_labels_out   N x H x W uint8 (host), 255 = no label.
+ * Accumulates into the mesh's current state (call sm_reset first for a fresh
+ * fusion).  Synchronises `stream` before returning.  Library-owned staging
+ * (two batches of predictions, the row maps and label images of all N
+ * frames) is allocated on first use and kept.
+ * Errors: SM_ERR_INVALID_ARG, SM_ERR_OOM, SM_ERR_CUDA. */
+sm_status sm_fuse_render_host(sm_mesh *m, const void *h_probs, sm_dtype dtype, const float *h_scale,
+                              const sm_intrinsics *h_K, const double *h_cam_to_world, int32_t N, int32_t H, int32_t W,
+                              uint8_t *h_labels_out, void *stream);
+
 /* Zeroes the accumulators and observation counts. */
 sm_status sm_reset(sm_mesh *m, void *stream);
 

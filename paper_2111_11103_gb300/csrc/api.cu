@@ -245,11 +245,13 @@ sm_status sm_mesh_upload(const float *d_vertices, int64_t V, const int32_t *d_fa
         return bail(cuda_fail(e, "raster stream"));
     if ((e = cudaEventCreateWithFlags(&m->ev_start, cudaEventDisableTiming)) != cudaSuccess)
         return bail(cuda_fail(e, "events"));
+    if ((e = cudaStreamCreateWithFlags(&m->cstream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(cuda_fail(e, "copy stream"));
     for (int k = 0; k < 2; ++k) {
-        if ((e = cudaEventCreateWithFlags(&m->ev_rast[k], cudaEventDisableTiming)) != cudaSuccess)
-            return bail(cuda_fail(e, "events"));
-        if ((e = cudaEventCreateWithFlags(&m->ev_scat[k], cudaEventDisableTiming)) != cudaSuccess)
-            return bail(cuda_fail(e, "events"));
+        cudaEvent_t *evs[] = {&m->ev_rast[k], &m->ev_scat[k], &m->ev_h2d[k], &m->ev_free[k]};
+        for (cudaEvent_t *ev : evs)
+            if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
+                return bail(cuda_fail(e, "events"));
     }
     lf::launch_pack_mesh(d_vertices, V, d_faces, F, m->verts, m->faces, m->err, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(e, "pack mesh"));
@@ -439,6 +441,64 @@ sm_status sm_render_idmap(sm_mesh *m, const int32_t *d_idmap, int64_t n_pixels, 
     return SM_OK;
 }
 
+sm_status sm_fuse_render_host(sm_mesh *m, const void *h_probs, sm_dtype dtype, const float *h_scale,
+                              const sm_intrinsics *h_K, const double *h_cam_to_world, int32_t N, int32_t H, int32_t W,
+                              uint8_t *h_labels_out, void *stream)
+{
+    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
+    sm_status st = check_image(N, H, W);
+    if (st != SM_OK) return st;
+    if ((int)dtype < 0 || (int)dtype > 2) return fail(SM_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
+    if (dtype == SM_F32 && h_scale) return fail(SM_ERR_INVALID_ARG, "F32 probabilities take no scale");
+    if (dtype != SM_F32 && !h_scale && N > 0) return fail(SM_ERR_INVALID_ARG, "BF16/FP8 need a per-pixel scale");
+    if (N == 0) return SM_OK;
+    if (!h_probs || !h_K || !h_cam_to_world || !h_labels_out) return fail(SM_ERR_INVALID_ARG, "NULL host pointer");
+    DeviceGuard g(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaStream_t cs = m->cstream;
+    const int64_t npix = (int64_t)H * W;
+    const int B = batch_frames(m, npix, N);
+    const size_t frame_bytes = (size_t)npix * m->c * dtype_size(dtype);
+    const size_t probs_slot = ((size_t)B * frame_bytes + 255) & ~(size_t)255;
+    const size_t slot_bytes = probs_slot + (dtype != SM_F32 ? (((size_t)B * npix * 4 + 255) & ~(size_t)255) : 0);
+    if ((st = grow(&m->hstage, &m->hstage_cap, 2 * (int64_t)slot_bytes, s, -1, "host staging")) != SM_OK) return st;
+    if ((st = grow(&m->hids, &m->hids_cap, (int64_t)N * npix, s, -1, "row maps")) != SM_OK) return st;
+    if ((st = grow(&m->hlabels, &m->hlabels_cap, (int64_t)N * npix, s, -1, "label images")) != SM_OK) return st;
+    if ((st = grow(&m->hcam, &m->hcam_cap, 20 * (int64_t)N, s, -1, "cameras")) != SM_OK) return st;
+    sm_intrinsics *d_K = reinterpret_cast<sm_intrinsics *>(m->hcam);
+    double *d_T = m->hcam + 4 * (int64_t)N;
+    LF_CUDA(cudaMemcpyAsync(d_K, h_K, sizeof(sm_intrinsics) * N, cudaMemcpyHostToDevice, s), "copy cameras");
+    LF_CUDA(cudaMemcpyAsync(d_T, h_cam_to_world, sizeof(double) * 16 * N, cudaMemcpyHostToDevice, s), "copy cameras");
+    // the copy stream may refill a staging slot once the fusion reading it is done
+    LF_CUDA(cudaEventRecord(m->ev_free[0], s), "event");
+    LF_CUDA(cudaEventRecord(m->ev_free[1], s), "event");
+    for (int b = 0, f0 = 0; f0 < N; ++b, f0 += B) {
+        const int nb = (N - f0 < B) ? N - f0 : B;
+        const int slot = b & 1;
+        uint8_t *dp = m->hstage + slot * slot_bytes;
+        float *dsc = dtype != SM_F32 ? reinterpret_cast<float *>(dp + probs_slot) : nullptr;
+        LF_CUDA(cudaStreamWaitEvent(cs, m->ev_free[slot], 0), "event");
+        LF_CUDA(cudaMemcpyAsync(dp, static_cast<const uint8_t *>(h_probs) + (size_t)f0 * frame_bytes,
+                                (size_t)nb * frame_bytes, cudaMemcpyHostToDevice, cs),
+                "copy predictions");
+        if (dsc)
+            LF_CUDA(cudaMemcpyAsync(dsc, h_scale + (size_t)f0 * npix, (size_t)nb * npix * sizeof(float),
+                                    cudaMemcpyHostToDevice, cs),
+                    "copy scales");
+        LF_CUDA(cudaEventRecord(m->ev_h2d[slot], cs), "event");
+        LF_CUDA(cudaStreamWaitEvent(s, m->ev_h2d[slot], 0), "event");
+        if ((st = sm_fuse_frames(m, dp, dtype, dsc, d_K + f0, d_T + 16 * (int64_t)f0, nb, H, W,
+                                 m->hids + (int64_t)f0 * npix, stream)) != SM_OK)
+            return st;
+        LF_CUDA(cudaEventRecord(m->ev_free[slot], s), "event");
+    }
+    if ((st = sm_normalise(m, nullptr, nullptr, stream)) != SM_OK) return st;
+    if ((st = sm_render_idmap(m, m->hids, (int64_t)N * npix, m->hlabels, stream)) != SM_OK) return st;
+    LF_CUDA(cudaMemcpyAsync(h_labels_out, m->hlabels, (size_t)N * npix, cudaMemcpyDeviceToHost, s), "copy labels");
+    LF_CUDA(cudaStreamSynchronize(s), "synchronise");
+    return SM_OK;
+}
+
 sm_status sm_reset(sm_mesh *m, void *stream)
 {
     if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
@@ -514,12 +574,15 @@ sm_status sm_mesh_free(sm_mesh *m)
     {
         DeviceGuard g(m->device);
         cudaDeviceSynchronize();
-        void *bufs[] = {m->verts, m->faces, m->row0, m->texinfo, m->acc,   m->cnt, m->labels8,
-                        m->err,   m->cams,  m->keys, m->idbuf,   m->fcnt, m->bounds};
+        void *bufs[] = {m->verts, m->faces,  m->row0,   m->texinfo, m->acc,     m->cnt,    m->labels8,
+                        m->err,   m->cams,   m->keys,   m->idbuf,   m->fcnt,    m->bounds, m->hstage,
+                        m->hids,  m->hlabels, m->hcam};
         for (void *b : bufs)
             if (b) cudaFree(b);
         if (m->rstream) cudaStreamDestroy(m->rstream);
-        cudaEvent_t evs[] = {m->ev_start, m->ev_rast[0], m->ev_rast[1], m->ev_scat[0], m->ev_scat[1]};
+        if (m->cstream) cudaStreamDestroy(m->cstream);
+        cudaEvent_t evs[] = {m->ev_start,  m->ev_rast[0], m->ev_rast[1], m->ev_scat[0], m->ev_scat[1],
+                             m->ev_h2d[0], m->ev_h2d[1],  m->ev_free[0], m->ev_free[1]};
         for (cudaEvent_t e : evs)
             if (e) cudaEventDestroy(e);
         for (int k = 0; k < SM_K_COUNT_KINDS; ++k)

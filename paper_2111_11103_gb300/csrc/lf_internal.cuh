@@ -118,6 +118,18 @@ struct sm_mesh {
     cudaStream_t rstream = nullptr;
     cudaEvent_t ev_start = nullptr, ev_rast[2] = {nullptr, nullptr}, ev_scat[2] = {nullptr, nullptr};
 
+    // host-streaming path (sm_fuse_render_host): copy stream, staging
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+    uint8_t *hstage = nullptr;   // two batches of predictions (+ scales)
+    int64_t hstage_cap = 0;      // bytes
+    int32_t *hids = nullptr;     // row maps of all frames of the call
+    int64_t hids_cap = 0;
+    uint8_t *hlabels = nullptr;  // label images of all frames of the call
+    int64_t hlabels_cap = 0;
+    double *hcam = nullptr;      // N x (4 + 16) camera parameters
+    int64_t hcam_cap = 0;
+
     // kernel timing
     bool prof = false;
     struct EvPair {

@@ -23,7 +23,8 @@ SM_OK = 0
 SM_MAX_CLASSES = 254
 SYMBOLS = ["sm_mesh_upload", "sm_fuse_frames", "sm_normalise", "sm_render_labels", "sm_render_idmap", "sm_reset",
            "sm_read_state", "sm_load_state", "sm_check", "sm_num_rows", "sm_num_classes", "sm_mesh_free",
-           "sm_status_string", "sm_last_error", "sm_profile_enable", "sm_profile_read", "sm_render_rows_noalloc"]
+           "sm_status_string", "sm_last_error", "sm_profile_enable", "sm_profile_read", "sm_render_rows_noalloc",
+           "sm_fuse_render_host"]
 SM_NOALLOC_MAX_PIXELS = 1572864
 SM_NOALLOC_MAX_FRAMES = 1024
 
@@ -58,6 +59,7 @@ def lib() -> ctypes.CDLL:
             "sm_mesh_free": [P],
             "sm_profile_enable": [P, i32],
             "sm_render_rows_noalloc": [P, i64, P, i64, P, P, i32, i32, i32, P, P],
+            "sm_fuse_render_host": [P, P, i32, P, P, P, i32, i32, i32, P, P],
             "sm_profile_read": [P, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)],
         }
         for name, args in sig.items():
@@ -131,6 +133,13 @@ def sm_render_labels(mesh: int, K, cam_to_world, N: int, H: int, W: int, labels_
 
 def sm_render_idmap(mesh: int, idmap, n_pixels: int, labels_out, stream=None):
     _check(lib().sm_render_idmap(mesh, _ptr(idmap), int(n_pixels), _ptr(labels_out), _stream(stream)))
+
+
+def sm_fuse_render_host(mesh: int, probs, dtype, scale, K, cam_to_world, N: int, H: int, W: int, labels_out,
+                        stream=None):
+    """Fuse + normalise + render with HOST tensors (pin them for overlap)."""
+    _check(lib().sm_fuse_render_host(mesh, _ptr(probs), _enum(SM_DTYPE, dtype), _ptr(scale), _ptr(K),
+                                     _ptr(cam_to_world), int(N), int(H), int(W), _ptr(labels_out), _stream(stream)))
 
 
 def sm_reset(mesh: int, stream=None):

@@ -264,6 +264,40 @@ def test_state_checkpoint_resume(dev, medium):
     assert_acc_close(acc.cpu().numpy(), full.acc.astype(np.float64))
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_streaming_matches_device_path(dev, medium, pinned):
+    """sm_fuse_render_host (inputs and label images in host memory, streamed
+    in batches) gives the same counts, accumulators (1e-5) and label images as
+    the device-resident calls."""
+    from paper_2111_11103_gb300 import labelfuse as lf
+    from gpu_common import to_dev
+    scene, cams, probs = medium
+    N, H, W, c = cams.K.shape[0], cams.H, cams.W, scene.n_classes
+    ref = run_gpu(scene, cams, probs, "logsum", "image", reraster=False)
+    V, Fc, _, _, _ = to_dev(scene, cams, None, dev)
+    h_probs = probs.cpu()
+    h_K = torch.as_tensor(cams.K)
+    h_T = torch.as_tensor(cams.cam_to_world.reshape(N, 16))
+    h_img = torch.empty((N, H, W), dtype=torch.uint8)
+    if pinned:
+        h_probs, h_K, h_T, h_img = (t.pin_memory() for t in (h_probs, h_K, h_T, h_img))
+    m = lf.sm_mesh_upload(V, Fc, None, c, "logsum", "image")
+    try:
+        for _ in range(2):  # a second call reuses the staging and starts from reset
+            lf.sm_reset(m)
+            lf.sm_fuse_render_host(m, h_probs, "f32", None, h_K, h_T, N, H, W, h_img)
+        n_x = lf.sm_num_rows(m)
+        acc = torch.empty((n_x, c), device=dev)
+        cnt = torch.empty(n_x, dtype=torch.int32, device=dev)
+        lf.sm_read_state(m, acc, cnt)
+        lf.sm_check(m)
+    finally:
+        lf.sm_mesh_free(m)
+    assert np.array_equal(cnt.cpu().numpy(), ref.cnt)
+    assert_acc_close(acc.cpu().numpy(), ref.acc.astype(np.float64))
+    assert np.array_equal(h_img.numpy(), ref.images)
+
+
 def test_kernel_timing_counts_launches(dev, tiny):
     from paper_2111_11103_gb300 import labelfuse as lf
     from gpu_common import to_dev
