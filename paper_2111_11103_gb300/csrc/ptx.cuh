@@ -98,16 +98,27 @@ __device__ __forceinline__ float lg2_ftz(float x)
     return y;
 }
 
-// Fire-and-forget reductions in L2 (no value returned, so no wait).
-__device__ __forceinline__ void red_add_v4(float *addr, float4 v)
+// L2 policy for data that should stay resident (the accumulator rows that
+// every frame updates): evict last.
+__device__ __forceinline__ uint64_t l2_evict_last()
 {
-    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// Fire-and-forget reductions in L2 (no value returned, so no wait), with an
+// L2 cache policy for the updated lines.
+__device__ __forceinline__ void red_add_v4(float *addr, float4 v, uint64_t policy)
+{
+    asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(addr), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w), "l"(policy)
                  : "memory");
 }
 
-__device__ __forceinline__ void red_add_u32(uint32_t *addr, uint32_t v)
+__device__ __forceinline__ void red_add_u32(uint32_t *addr, uint32_t v, uint64_t policy)
 {
-    asm volatile("red.global.add.u32 [%0], %1;" ::"l"(addr), "r"(v) : "memory");
+    asm volatile("red.global.add.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(addr), "r"(v), "l"(policy) : "memory");
 }
 
 __device__ __forceinline__ void red_min_u64(unsigned long long *addr, unsigned long long v)

@@ -7,8 +7,7 @@
 // Design (GB300):
 //  * persistent CTAs, two per SM; warp 0 is a producer whose elected lane
 //    streams 256-pixel tiles into a ring of shared-memory stages with 1-D TMA
-//    bulk copies (cp.async.bulk, completion counted on an mbarrier) and keeps
-//    the CTA's next tiles on their way into L2 with bulk L2 prefetches.  A
+//    bulk copies (cp.async.bulk, completion counted on an mbarrier).  A
 //    stage holds the tile's probabilities (L2 evict-first: read once) and its
 //    per-pixel metadata: the z-buffer keys left by the raster (face mode; row
 //    = triangle of the nearest surface) or the resolved row map, and the
@@ -18,8 +17,10 @@
 //    of pixels, four pixels per software-pipelined step, keeping the running
 //    sum of phi(p) for the current row in registers.  Only when the row (or
 //    the pixel weight) changes is the run flushed: the group's lanes together
-//    add one contiguous row of P with 16-byte vector reductions, plus the run
-//    length into the observation count;
+//    add one contiguous row of P with 16-byte vector reductions (L2
+//    evict-last, so the rows a trajectory keeps revisiting stay in L2 while
+//    the prediction stream passes through), plus the run length into the
+//    observation count;
 //  * log-sum multiplies up to four clamped probabilities (>= 2^-30 each, so
 //    no underflow) before one hardware log2 per class: sum_k log p_k =
 //    log prod_k p_k, up to rounding;
@@ -164,8 +165,9 @@ __device__ __forceinline__ void flush(const Args &a, float *accq, int cur, float
 {
     if (cur < 0) return;
     if (RULE == SM_RULE_LOGSUM && r.nf > 0) fold_logs(r, w);
-    red_add_v4(accq + (int64_t)cur * a.c, r.s);
-    if (q == 0) red_add_u32(a.cnt + cur, n);
+    const uint64_t keep = l2_evict_last();
+    red_add_v4(accq + (int64_t)cur * a.c, r.s, keep);
+    if (q == 0) red_add_u32(a.cnt + cur, n, keep);
 }
 
 // phi(p) of one pixel added into the run (weight wk); pix points at the
@@ -299,7 +301,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
         if (lane == 0) {
             const uint64_t pol = l2_evict_first();
             const uint32_t tx = L.probs_bytes + L.meta_bytes + L.scale_bytes;
-            const int64_t ahead = (int64_t)((256u << 10) / L.probs_bytes + 1) * gridDim.x;
             int it = 0;
             for (int64_t t = blockIdx.x; t < ntiles_full; t += gridDim.x, ++it) {
                 const int s = it % stages;
@@ -316,9 +317,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
                 bulk_g2s(st + L.probs_bytes, meta, L.meta_bytes, full + s, pol);
                 if (L.scale_bytes)
                     bulk_g2s(st + L.probs_bytes + L.meta_bytes, a.scale + t * kTile, L.scale_bytes, full + s, pol);
-                // keep ~256 KB of this CTA's future tiles on their way into L2
-                if (t + ahead < ntiles_full)
-                    bulk_prefetch_l2(a.probs + (size_t)(t + ahead) * L.probs_bytes, L.probs_bytes);
             }
             // every issued copy has landed before this thread leaves
             for (int j = it - stages; j < it; ++j) {
@@ -416,6 +414,7 @@ __device__ __forceinline__ void pair_flush(const Args &a, int cur, float w, cons
                                            int l, int Q)
 {
     float *dst = a.acc + (int64_t)cur * (4 * Q);
+    const uint64_t keep = l2_evict_last();
 #pragma unroll
     for (int m = 0; m < QL; ++m) {
         const int j = 2 * m + l;
@@ -429,9 +428,9 @@ __device__ __forceinline__ void pair_flush(const Args &a, int cur, float w, cons
         } else if (IMAGE) {
             v = make_float4(v.x * w, v.y * w, v.z * w, v.w * w);
         }
-        red_add_v4(dst + 4 * j, v);
+        red_add_v4(dst + 4 * j, v, keep);
     }
-    if (l == 0) red_add_u32(a.cnt + cur, n);
+    if (l == 0) red_add_u32(a.cnt + cur, n, keep);
 }
 
 template <int QL, int DT, bool SMEM>
@@ -579,7 +578,6 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_scatter_pair(Args a, int sp
         if (lane == 0) {
             const uint64_t pol = l2_evict_first();
             const uint32_t tx = L.probs_bytes + L.meta_bytes + L.scale_bytes;
-            const int64_t ahead = (int64_t)((256u << 10) / L.probs_bytes + 1) * gridDim.x;
             int64_t it = 0;
             for (int64_t t = blockIdx.x; t < ntiles_full; t += gridDim.x, ++it) {
                 const int w = (int)(it % kPairWarps);
@@ -599,8 +597,6 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_scatter_pair(Args a, int sp
                 if (L.scale_bytes)
                     bulk_g2s(st + L.probs_bytes + L.meta_bytes, a.scale + t * kPairTile, L.scale_bytes, full + s,
                              pol);
-                if (t + ahead < ntiles_full)
-                    bulk_prefetch_l2(a.probs + (size_t)(t + ahead) * L.probs_bytes, L.probs_bytes);
             }
             // every issued copy has landed before this thread leaves
             for (int64_t j = it - (int64_t)nst; j < it; ++j) {
