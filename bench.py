@@ -14,7 +14,9 @@ a bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -114,6 +116,24 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+def scatter_traffic_per_frame():
+    """DRAM bytes (read + write) per frame of the scatter kernel, from the
+    committed ncu summary, or None when the kernel's source has changed since
+    that capture (the counters would no longer describe it)."""
+    path = os.path.join(ROOT, "profiles", "scatter_pair_paper_room.md")
+    try:
+        fields = dict(re.findall(r"^\s+(\w+): (\S+)$", open(path).read(), re.M))
+        sha = hashlib.sha256()
+        for f in ("scatter.cu", "ptx.cuh"):
+            with open(os.path.join(ROOT, "paper_2111_11103_gb300", "csrc", f), "rb") as fh:
+                sha.update(fh.read())
+        if sha.hexdigest()[:16] != fields.get("source_sha"):
+            return None
+        return int(fields["traffic_bytes_per_launch"]) / int(fields["frames_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def dist_env():
@@ -253,6 +273,8 @@ def run_ours(args):
     achieved = bytes_per_frame_scatter * frames_per_launch / (ms_sc / max(n_sc, 1) / 1e3) / 1e9
     peak, peak_kind = peaks()
     kernels = {k: {"launches": n, "ms_per_step": t / args.steps} for k, (n, t) in prof.items() if n}
+    tpf = scatter_traffic_per_frame()
+    traffic = None if tpf is None or (H, W, c) != (480, 640, 40) else tpf * frames_per_launch
 
     line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -261,8 +283,9 @@ def run_ours(args):
                        "classes": c, "rule": args.rule, "weight": args.weight, "probs": "f32 HWC",
                        "l2": "inputs (49 GB) larger than L2, no flush", "parallelism": f"replicas{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "scatter",
-                         "peak_kind": peak_kind},
+                         "frac": achieved / peak, "traffic": traffic, "kernel": "scatter",
+                         "algorithmic_bytes_per_launch": bytes_per_frame_scatter * frames_per_launch,
+                         "frames_per_launch": frames_per_launch, "peak_kind": peak_kind},
             "kernels": kernels,
             "gpu_launches": launches,
             "clocks": clk.summary()}
