@@ -276,7 +276,169 @@ __device__ __forceinline__ void warp_tile(const Args &a, const uint8_t *base, in
     if (active) flush<RULE>(a, accq, cur, curw, run, n, q);
 }
 
-template <int RULE, int DT, bool IMAGE>
+// Same walk with a compile-time class count C and LPP lanes per pixel, each
+// lane owning QPL = C / (4 LPP) quads (lane q: quads q, q + LPP, ...).  With
+// 5 lanes per pixel a warp runs 6 groups, so the per-pixel control work is
+// shared by 6 pixels and a flush writes LPP x 16 contiguous bytes per
+// instruction.
+template <int C, int LPP, int RULE, int DT, bool SMEM, bool IMAGE>
+__device__ __forceinline__ void warp_tile_q(const Args &a, const uint8_t *base, int px0, int lane, int row, float w,
+                                            float sc)
+{
+    constexpr int ES = Elem<DT>::size;
+    constexpr int Q = C / 4;
+    constexpr int QPL = Q / LPP;
+    constexpr int G = 32 / LPP;
+    constexpr int ITERS = (32 + G - 1) / G;
+    constexpr int pstride = C * ES;
+    const int g = lane / LPP, q = lane - g * LPP;
+    const bool active = g < G;
+    const int start = active ? (32 * g) / G : 0;
+    const int len = active ? (32 * (g + 1)) / G - start : 0;
+    const uint8_t *pb = base + (px0 + start) * pstride;
+    float4 s[QPL], prod[QPL];
+    int cur = -1, nf = 0;
+    float curw = 1.0f;
+    uint32_t n = 0;
+#pragma unroll
+    for (int m = 0; m < QPL; ++m) {
+        s[m] = make_float4(0.f, 0.f, 0.f, 0.f);
+        prod[m] = make_float4(1.f, 1.f, 1.f, 1.f);
+    }
+    auto flush_run = [&]() {
+        if (cur < 0) return;
+        const uint64_t keep = l2_evict_last();
+        float *dst = a.acc + (int64_t)cur * C;
+#pragma unroll
+        for (int m = 0; m < QPL; ++m) {
+            float4 v = s[m];
+            if (RULE == SM_RULE_LOGSUM && nf > 0) {
+                const float wl = curw * kLn2;
+                v.x = fmaf(lg2_ftz(prod[m].x), wl, v.x);
+                v.y = fmaf(lg2_ftz(prod[m].y), wl, v.y);
+                v.z = fmaf(lg2_ftz(prod[m].z), wl, v.z);
+                v.w = fmaf(lg2_ftz(prod[m].w), wl, v.w);
+            }
+            red_add_v4(dst + 4 * (q + LPP * m), v, keep);
+        }
+        if (q == 0) red_add_u32(a.cnt + cur, n, keep);
+    };
+#pragma unroll
+    for (int i0 = 0; i0 < ITERS; i0 += kUnroll) {
+        int r[kUnroll];
+        float wv[kUnroll], sv[kUnroll];
+        float4 v[kUnroll][QPL];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int k = (start + i0 + u) & 31;
+            r[u] = __shfl_sync(kFull, row, k);
+            wv[u] = IMAGE ? __shfl_sync(kFull, w, k) : 1.0f;
+            sv[u] = (DT != SM_F32) ? __shfl_sync(kFull, sc, k) : 1.0f;
+            if (i0 + u >= len) r[u] = -2;  // past this group's run (or inactive lane)
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+            for (int m = 0; m < QPL; ++m) {
+                v[u][m] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (r[u] >= 0) {
+                    v[u][m] = load_quad<DT, SMEM>(pb + (i0 + u) * pstride, 4 * (q + LPP * m));
+                    if (DT != SM_F32) v[u][m] = scale4(v[u][m], sv[u]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            if (r[u] == -2) continue;
+            if (r[u] != cur || (IMAGE && wv[u] != curw)) {
+                flush_run();
+                cur = r[u];
+                curw = wv[u];
+                n = 0;
+                nf = 0;
+#pragma unroll
+                for (int m = 0; m < QPL; ++m) {
+                    s[m] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    prod[m] = make_float4(1.f, 1.f, 1.f, 1.f);
+                }
+            }
+            if (r[u] < 0) continue;
+            if (RULE == SM_RULE_SUM) {
+#pragma unroll
+                for (int m = 0; m < QPL; ++m) {
+                    s[m].x = fmaf(wv[u], v[u][m].x, s[m].x);
+                    s[m].y = fmaf(wv[u], v[u][m].y, s[m].y);
+                    s[m].z = fmaf(wv[u], v[u][m].z, s[m].z);
+                    s[m].w = fmaf(wv[u], v[u][m].w, s[m].w);
+                }
+            } else if (RULE == SM_RULE_LOGSUM) {
+#pragma unroll
+                for (int m = 0; m < QPL; ++m) {
+                    prod[m].x *= fmaxf(v[u][m].x, kPMin);
+                    prod[m].y *= fmaxf(v[u][m].y, kPMin);
+                    prod[m].z *= fmaxf(v[u][m].z, kPMin);
+                    prod[m].w *= fmaxf(v[u][m].w, kPMin);
+                }
+                if (++nf == kMaxFactors) {
+                    const float wl = curw * kLn2;
+#pragma unroll
+                    for (int m = 0; m < QPL; ++m) {
+                        s[m].x = fmaf(lg2_ftz(prod[m].x), wl, s[m].x);
+                        s[m].y = fmaf(lg2_ftz(prod[m].y), wl, s[m].y);
+                        s[m].z = fmaf(lg2_ftz(prod[m].z), wl, s[m].z);
+                        s[m].w = fmaf(lg2_ftz(prod[m].w), wl, s[m].w);
+                        prod[m] = make_float4(1.f, 1.f, 1.f, 1.f);
+                    }
+                    nf = 0;
+                }
+            } else {
+                // maximum and first arg max of the whole pixel: each lane scans its
+                // quads in class order, then the group combines (lowest class on ties)
+                float mx = -INFINITY;
+                int am = 0x7fffffff;
+#pragma unroll
+                for (int m = 0; m < QPL; ++m) {
+                    const int j = q + LPP * m;
+                    if (v[u][m].x > mx) { mx = v[u][m].x; am = 4 * j; }
+                    if (v[u][m].y > mx) { mx = v[u][m].y; am = 4 * j + 1; }
+                    if (v[u][m].z > mx) { mx = v[u][m].z; am = 4 * j + 2; }
+                    if (v[u][m].w > mx) { mx = v[u][m].w; am = 4 * j + 3; }
+                }
+                // the LPP lanes of a group reach this point together (same row)
+                const unsigned gmask = ((1u << LPP) - 1u) << (g * LPP);
+                float gm = mx;
+                int ga = am;
+                for (int t = 0; t < LPP; ++t) {
+                    const float om = __shfl_sync(gmask, mx, g * LPP + t);
+                    const int oa = __shfl_sync(gmask, am, g * LPP + t);
+                    if (om > gm || (om == gm && oa < ga)) {
+                        gm = om;
+                        ga = oa;
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < QPL; ++m) {
+                    const int j = q + LPP * m;
+                    if (RULE == SM_RULE_MAXSUM) {
+                        if (v[u][m].x == gm) s[m].x = fmaf(wv[u], v[u][m].x, s[m].x);
+                        if (v[u][m].y == gm) s[m].y = fmaf(wv[u], v[u][m].y, s[m].y);
+                        if (v[u][m].z == gm) s[m].z = fmaf(wv[u], v[u][m].z, s[m].z);
+                        if (v[u][m].w == gm) s[m].w = fmaf(wv[u], v[u][m].w, s[m].w);
+                    } else {
+                        if (ga == 4 * j) s[m].x += wv[u];
+                        if (ga == 4 * j + 1) s[m].y += wv[u];
+                        if (ga == 4 * j + 2) s[m].z += wv[u];
+                        if (ga == 4 * j + 3) s[m].w += wv[u];
+                    }
+                }
+            }
+            ++n;
+        }
+    }
+    if (active) flush_run();
+}
+
+template <int RULE, int DT, bool IMAGE, int C = 0>
 __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
 {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -344,7 +506,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
             a, t * kTile + px0 + lane, px0 + lane, st + L.probs_bytes,
             L.scale_bytes ? reinterpret_cast<const float *>(st + L.probs_bytes + L.meta_bytes) : nullptr, row, w,
             sc);
-        warp_tile<RULE, DT, true, IMAGE>(a, st, px0, lane, row, w, sc);
+        if constexpr (C != 0)
+            warp_tile_q<C, 5, RULE, DT, true, IMAGE>(a, st, px0, lane, row, w, sc);
+        else
+            warp_tile<RULE, DT, true, IMAGE>(a, st, px0, lane, row, w, sc);
         __syncwarp();
         if (lane == 0) mbar_arrive(empty + s);
     }
@@ -352,7 +517,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
         int row;
         float w, sc;
         pixel_info<DT, IMAGE>(a, ntiles_full * kTile + px0 + lane, px0 + lane, nullptr, nullptr, row, w, sc);
-        warp_tile<RULE, DT, false, IMAGE>(a, a.probs + (size_t)ntiles_full * L.probs_bytes, px0, lane, row, w, sc);
+        if constexpr (C != 0)
+            warp_tile_q<C, 5, RULE, DT, false, IMAGE>(a, a.probs + (size_t)ntiles_full * L.probs_bytes, px0, lane, row,
+                                                      w, sc);
+        else
+            warp_tile<RULE, DT, false, IMAGE>(a, a.probs + (size_t)ntiles_full * L.probs_bytes, px0, lane, row, w,
+                                              sc);
     }
 }
 
@@ -444,12 +614,15 @@ __device__ __forceinline__ void pair_load(float4 (&v)[QL], const uint8_t *pix, i
 }
 
 // One warp's 64-pixel tile: stream k = lane / 2 takes pixels 4k .. 4k+3.
-// Runs are cut where the row or the weight changes; log-sum runs multiply at
-// most kMaxFactors clamped probabilities before their logarithm is taken
-// (at most 4 pixels per stream and tile, so exactly once per run).
+// The lane first copies its share of the tile (4 pixels x QL quads) and the
+// metadata into registers; then the stage is released (release != null), so
+// the producer can refill it while this warp computes.  Runs are cut where
+// the row or the weight changes; log-sum runs multiply at most kMaxFactors
+// clamped probabilities before their logarithm is taken (at most 4 pixels
+// per stream and tile, so exactly once per run).
 template <int QL, int RULE, int DT, bool SMEM, bool IMAGE>
 __device__ __forceinline__ void pair_tile(const Args &a, const uint8_t *tile, const uint8_t *meta,
-                                          const float *sscale, int64_t tile_p0, int lane)
+                                          const float *sscale, int64_t tile_p0, int lane, uint64_t *release)
 {
     constexpr int ES = Elem<DT>::size;
     constexpr int C = (QL == 5) ? 40 : 20;  // the two class counts this path serves
@@ -463,18 +636,23 @@ __device__ __forceinline__ void pair_tile(const Args &a, const uint8_t *tile, co
         const int pi = 4 * k + ((i + k) & 3);
         pair_meta<DT, IMAGE>(a, tile_p0 + pi, pi, meta, sscale, l == 0, row[i], w[i], sc[i]);
     }
+    float4 V4[4][QL];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (row[i] >= 0) pair_load<QL, DT, SMEM>(V4[i], tile + (4 * k + ((i + k) & 3)) * pstride, l, Q);
+    }
+    __syncwarp();
+    if (release && lane == 0) mbar_arrive(release);
     const float4 init = (RULE == SM_RULE_LOGSUM) ? make_float4(1.f, 1.f, 1.f, 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 R[QL], vn[QL];
+    float4 R[QL];
     int cur = -1, nf = 0;
     float curw = 1.0f;
     uint32_t n = 0;
-    if (row[0] >= 0) pair_load<QL, DT, SMEM>(vn, tile + (4 * k + (k & 3)) * pstride, l, Q);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         float4 v[QL];
 #pragma unroll
-        for (int m = 0; m < QL; ++m) v[m] = vn[m];
-        if (i < 3 && row[i + 1] >= 0) pair_load<QL, DT, SMEM>(vn, tile + (4 * k + ((i + 1 + k) & 3)) * pstride, l, Q);
+        for (int m = 0; m < QL; ++m) v[m] = V4[i][m];
         const int r = row[i];
         if (r != cur || (IMAGE && w[i] != curw)) {
             if (cur >= 0) pair_flush<QL, RULE, IMAGE>(a, cur, curw, R, nf, n, l, Q);
@@ -621,16 +799,15 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_scatter_pair(Args a, int sp
             atomicCAS(a.err, 0, (int32_t)kErrTimeout);
             return;
         }
+        // pair_tile releases the stage as soon as its data is in registers
         pair_tile<QL, RULE, DT, true, IMAGE>(
             a, st, st + L.probs_bytes,
             L.scale_bytes ? reinterpret_cast<const float *>(st + L.probs_bytes + L.meta_bytes) : nullptr,
-            t * kPairTile, lane);
-        __syncwarp();
-        if (lane == 0) mbar_arrive(empty + s);
+            t * kPairTile, lane, empty + s);
     }
     if (ragged && cw == 0 && blockIdx.x == gridDim.x - 1)
         pair_tile<QL, RULE, DT, false, IMAGE>(a, a.probs + (size_t)ntiles_full * L.probs_bytes, nullptr, nullptr,
-                                              ntiles_full * kPairTile, lane);
+                                              ntiles_full * kPairTile, lane, nullptr);
 }
 
 int g_num_sms = 0;
@@ -684,7 +861,7 @@ bool launch_pair_dt(sm_dtype dt, const Args &a, cudaStream_t s)
     return false;
 }
 
-template <int RULE, int DT, bool IMAGE>
+template <int RULE, int DT, bool IMAGE, int C>
 void launch_one(const Args &a, cudaStream_t s)
 {
     static bool configured = false;
@@ -693,7 +870,7 @@ void launch_one(const Args &a, cudaStream_t s)
     stages = stages < 1 ? 1 : (stages > 4 ? 4 : stages);
     const size_t smem = 128 + (size_t)stages * L.stride;
     if (!configured) {
-        cudaFuncSetAttribute(k_scatter_tma<RULE, DT, IMAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_scatter_tma<RULE, DT, IMAGE, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 << 10);
         configured = true;
     }
@@ -702,25 +879,32 @@ void launch_one(const Args &a, cudaStream_t s)
     int64_t grid = 2LL * g_num_sms;
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
-    k_scatter_tma<RULE, DT, IMAGE><<<(unsigned)grid, kThreads, smem, s>>>(a, stages);
+    k_scatter_tma<RULE, DT, IMAGE, C><<<(unsigned)grid, kThreads, smem, s>>>(a, stages);
+}
+
+// c = 40 (the paper's class count) and c = 20 get a compile-time class count
+// and 5 lanes per pixel; other c take the runtime-c walk.
+template <int RULE, bool IMAGE, int DT>
+void launch_c(const Args &a, cudaStream_t s)
+{
+    if (a.c == 40) launch_one<RULE, DT, IMAGE, 40>(a, s);
+    else if (a.c == 20) launch_one<RULE, DT, IMAGE, 20>(a, s);
+    else launch_one<RULE, DT, IMAGE, 0>(a, s);
 }
 
 template <int RULE, bool IMAGE>
 void launch_dt(sm_dtype dt, const Args &a, cudaStream_t s)
 {
-    if (dt == SM_F32) launch_one<RULE, SM_F32, IMAGE>(a, s);
-    else if (dt == SM_BF16) launch_one<RULE, SM_BF16, IMAGE>(a, s);
-    else launch_one<RULE, SM_FP8_E4M3, IMAGE>(a, s);
+    if (dt == SM_F32) launch_c<RULE, IMAGE, SM_F32>(a, s);
+    else if (dt == SM_BF16) launch_c<RULE, IMAGE, SM_BF16>(a, s);
+    else launch_c<RULE, IMAGE, SM_FP8_E4M3>(a, s);
 }
 
 template <int RULE>
 void launch_rule(sm_dtype dt, const Args &a, cudaStream_t s)
 {
-    if (a.fcnt) {
-        if (!launch_pair_dt<RULE, true>(dt, a, s)) launch_dt<RULE, true>(dt, a, s);
-    } else {
-        if (!launch_pair_dt<RULE, false>(dt, a, s)) launch_dt<RULE, false>(dt, a, s);
-    }
+    if (a.fcnt) launch_dt<RULE, true>(dt, a, s);
+    else launch_dt<RULE, false>(dt, a, s);
 }
 
 }  // namespace
