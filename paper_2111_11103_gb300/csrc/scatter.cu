@@ -38,8 +38,8 @@
 namespace lf {
 namespace {
 
-constexpr int kTile = 256;          // pixels per tile
 constexpr int kConsumerWarps = 8;   // 32 pixels each
+constexpr int kTile = 32 * kConsumerWarps;  // pixels per tile
 constexpr int kThreads = 32 * (1 + kConsumerWarps);
 constexpr int kUnroll = 4;          // pixels per software-pipelined step
 constexpr int kMaxFactors = 4;      // probabilities multiplied before one log2
@@ -276,166 +276,213 @@ __device__ __forceinline__ void warp_tile(const Args &a, const uint8_t *base, in
     if (active) flush<RULE>(a, accq, cur, curw, run, n, q);
 }
 
-// Same walk with a compile-time class count C and LPP lanes per pixel, each
-// lane owning QPL = C / (4 LPP) quads (lane q: quads q, q + LPP, ...).  With
-// 5 lanes per pixel a warp runs 6 groups, so the per-pixel control work is
-// shared by 6 pixels and a flush writes LPP x 16 contiguous bytes per
-// instruction.
+// Per-warp queue of finished runs in shared memory, for a compile-time class
+// count C.  An entry is one run of pixels of one row: its C sums of w * phi
+// (log-sum: the C products of its clamped probabilities, at most kMaxFactors
+// each), the row, the run length and (log-sum) the pixel weight.  The whole
+// warp drains the queue together, so every reduction instruction runs with
+// all 32 lanes busy instead of only the lanes of the groups whose run ended.
+template <int C>
+struct RunQueue {
+    static constexpr int kCap = 16;
+    static constexpr uint32_t bytes = kCap * (C * 4 + 12);
+    uint8_t *base;  // kCap x C/4 quads (entry-major) | kCap rows | kCap lengths | kCap weights
+    int cnt;        // entries in use (warp-uniform)
+
+    __device__ __forceinline__ float4 *v() const { return reinterpret_cast<float4 *>(base); }
+    __device__ __forceinline__ int *row() const { return reinterpret_cast<int *>(base + kCap * C * 4); }
+    __device__ __forceinline__ uint32_t *n() const { return reinterpret_cast<uint32_t *>(row() + kCap); }
+    __device__ __forceinline__ float *w() const { return reinterpret_cast<float *>(n() + kCap); }
+};
+
+// Adds every queued run into its row of P (16-byte reductions, L2
+// evict-last: the rows a trajectory keeps revisiting stay in L2 while the
+// prediction stream passes through) and its length into the observation
+// count.  Called by the whole warp.
+template <int C, int RULE, bool IMAGE>
+__device__ __forceinline__ void drain(const Args &a, RunQueue<C> &qu, int lane)
+{
+    constexpr int Q = C / 4;
+    __syncwarp();
+    const uint64_t keep = l2_evict_last();
+    const int nq = qu.cnt * Q;
+    for (int k = lane; k < nq; k += 32) {
+        const int e = k / Q;
+        float4 v = qu.v()[k];
+        if (RULE == SM_RULE_LOGSUM) {
+            // sum_k w log p_k = w ln 2 log2 prod_k p_k
+            const float wl = (IMAGE ? qu.w()[e] : 1.0f) * kLn2;
+            v = make_float4(lg2_ftz(v.x) * wl, lg2_ftz(v.y) * wl, lg2_ftz(v.z) * wl, lg2_ftz(v.w) * wl);
+        }
+        red_add_v4(a.acc + (int64_t)qu.row()[e] * C + 4 * (k - e * Q), v, keep);
+    }
+    if (lane < qu.cnt) red_add_u32(a.cnt + qu.row()[lane], qu.n()[lane], keep);
+    __syncwarp();
+    qu.cnt = 0;
+}
+
+// One warp's 32 pixels of a tile with a compile-time class count C and LPP
+// lanes per pixel, each lane owning QPL = C / (4 LPP) quads (lane q: quads
+// q, q + LPP, ...).  The warp runs G = 32 / LPP groups, each over a
+// contiguous range of pixels, all in lock step: a step processes one pixel
+// per group, so the per-pixel control work is shared by G pixels and no
+// branch depends on a single group.  A run is cut where the row or the pixel
+// weight changes (log-sum: also after kMaxFactors pixels, so its product
+// cannot underflow); a finished run of a visible row is appended to the
+// queue, which is drained once it could not take another step's runs.
 template <int C, int LPP, int RULE, int DT, bool SMEM, bool IMAGE>
 __device__ __forceinline__ void warp_tile_q(const Args &a, const uint8_t *base, int px0, int lane, int row, float w,
-                                            float sc)
+                                            float sc, RunQueue<C> &qu, uint64_t *release)
 {
     constexpr int ES = Elem<DT>::size;
     constexpr int Q = C / 4;
     constexpr int QPL = Q / LPP;
     constexpr int G = 32 / LPP;
-    constexpr int ITERS = (32 + G - 1) / G;
+    constexpr int STEPS = (32 + G - 1) / G;  // the longest group range
     constexpr int pstride = C * ES;
+    constexpr bool PROD = RULE == SM_RULE_LOGSUM;
     const int g = lane / LPP, q = lane - g * LPP;
     const bool active = g < G;
     const int start = active ? (32 * g) / G : 0;
     const int len = active ? (32 * (g + 1)) / G - start : 0;
+    const unsigned below = (1u << (g * LPP)) - 1u;  // the lanes of the lower groups
     const uint8_t *pb = base + (px0 + start) * pstride;
-    float4 s[QPL], prod[QPL];
-    int cur = -1, nf = 0;
-    float curw = 1.0f;
-    uint32_t n = 0;
+
+    // rows, weights and scales of the group's pixels (-2: past its range)
+    int r[STEPS];
+    float wv[STEPS], sv[STEPS];
 #pragma unroll
-    for (int m = 0; m < QPL; ++m) {
-        s[m] = make_float4(0.f, 0.f, 0.f, 0.f);
-        prod[m] = make_float4(1.f, 1.f, 1.f, 1.f);
+    for (int u = 0; u < STEPS; ++u) {
+        const int k = (start + u) & 31;
+        r[u] = __shfl_sync(kFull, row, k);
+        wv[u] = IMAGE ? __shfl_sync(kFull, w, k) : 1.0f;
+        sv[u] = (DT != SM_F32) ? __shfl_sync(kFull, sc, k) : 1.0f;
+        if (u >= len) r[u] = -2;
     }
-    auto flush_run = [&]() {
-        if (cur < 0) return;
-        const uint64_t keep = l2_evict_last();
-        float *dst = a.acc + (int64_t)cur * C;
+    // the lane's quads of every step's pixel (a stage holds the whole tile;
+    // the ragged tile in global memory is read only where a pixel exists)
+    float4 v[STEPS][QPL];
+#pragma unroll
+    for (int u = 0; u < STEPS; ++u) {
 #pragma unroll
         for (int m = 0; m < QPL; ++m) {
-            float4 v = s[m];
-            if (RULE == SM_RULE_LOGSUM && nf > 0) {
-                const float wl = curw * kLn2;
-                v.x = fmaf(lg2_ftz(prod[m].x), wl, v.x);
-                v.y = fmaf(lg2_ftz(prod[m].y), wl, v.y);
-                v.z = fmaf(lg2_ftz(prod[m].z), wl, v.z);
-                v.w = fmaf(lg2_ftz(prod[m].w), wl, v.w);
+            v[u][m] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (SMEM || r[u] >= 0) {
+                v[u][m] = load_quad<DT, SMEM>(pb + u * pstride, 4 * (q + LPP * m));
+                if (DT != SM_F32) v[u][m] = scale4(v[u][m], sv[u]);
             }
-            red_add_v4(dst + 4 * (q + LPP * m), v, keep);
-        }
-        if (q == 0) red_add_u32(a.cnt + cur, n, keep);
-    };
-#pragma unroll
-    for (int i0 = 0; i0 < ITERS; i0 += kUnroll) {
-        int r[kUnroll];
-        float wv[kUnroll], sv[kUnroll];
-        float4 v[kUnroll][QPL];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int k = (start + i0 + u) & 31;
-            r[u] = __shfl_sync(kFull, row, k);
-            wv[u] = IMAGE ? __shfl_sync(kFull, w, k) : 1.0f;
-            sv[u] = (DT != SM_F32) ? __shfl_sync(kFull, sc, k) : 1.0f;
-            if (i0 + u >= len) r[u] = -2;  // past this group's run (or inactive lane)
-        }
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-#pragma unroll
-            for (int m = 0; m < QPL; ++m) {
-                v[u][m] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (r[u] >= 0) {
-                    v[u][m] = load_quad<DT, SMEM>(pb + (i0 + u) * pstride, 4 * (q + LPP * m));
-                    if (DT != SM_F32) v[u][m] = scale4(v[u][m], sv[u]);
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            if (r[u] == -2) continue;
-            if (r[u] != cur || (IMAGE && wv[u] != curw)) {
-                flush_run();
-                cur = r[u];
-                curw = wv[u];
-                n = 0;
-                nf = 0;
-#pragma unroll
-                for (int m = 0; m < QPL; ++m) {
-                    s[m] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    prod[m] = make_float4(1.f, 1.f, 1.f, 1.f);
-                }
-            }
-            if (r[u] < 0) continue;
-            if (RULE == SM_RULE_SUM) {
-#pragma unroll
-                for (int m = 0; m < QPL; ++m) {
-                    s[m].x = fmaf(wv[u], v[u][m].x, s[m].x);
-                    s[m].y = fmaf(wv[u], v[u][m].y, s[m].y);
-                    s[m].z = fmaf(wv[u], v[u][m].z, s[m].z);
-                    s[m].w = fmaf(wv[u], v[u][m].w, s[m].w);
-                }
-            } else if (RULE == SM_RULE_LOGSUM) {
-#pragma unroll
-                for (int m = 0; m < QPL; ++m) {
-                    prod[m].x *= fmaxf(v[u][m].x, kPMin);
-                    prod[m].y *= fmaxf(v[u][m].y, kPMin);
-                    prod[m].z *= fmaxf(v[u][m].z, kPMin);
-                    prod[m].w *= fmaxf(v[u][m].w, kPMin);
-                }
-                if (++nf == kMaxFactors) {
-                    const float wl = curw * kLn2;
-#pragma unroll
-                    for (int m = 0; m < QPL; ++m) {
-                        s[m].x = fmaf(lg2_ftz(prod[m].x), wl, s[m].x);
-                        s[m].y = fmaf(lg2_ftz(prod[m].y), wl, s[m].y);
-                        s[m].z = fmaf(lg2_ftz(prod[m].z), wl, s[m].z);
-                        s[m].w = fmaf(lg2_ftz(prod[m].w), wl, s[m].w);
-                        prod[m] = make_float4(1.f, 1.f, 1.f, 1.f);
-                    }
-                    nf = 0;
-                }
-            } else {
-                // maximum and first arg max of the whole pixel: each lane scans its
-                // quads in class order, then the group combines (lowest class on ties)
-                float mx = -INFINITY;
-                int am = 0x7fffffff;
-#pragma unroll
-                for (int m = 0; m < QPL; ++m) {
-                    const int j = q + LPP * m;
-                    if (v[u][m].x > mx) { mx = v[u][m].x; am = 4 * j; }
-                    if (v[u][m].y > mx) { mx = v[u][m].y; am = 4 * j + 1; }
-                    if (v[u][m].z > mx) { mx = v[u][m].z; am = 4 * j + 2; }
-                    if (v[u][m].w > mx) { mx = v[u][m].w; am = 4 * j + 3; }
-                }
-                // the LPP lanes of a group reach this point together (same row)
-                const unsigned gmask = ((1u << LPP) - 1u) << (g * LPP);
-                float gm = mx;
-                int ga = am;
-                for (int t = 0; t < LPP; ++t) {
-                    const float om = __shfl_sync(gmask, mx, g * LPP + t);
-                    const int oa = __shfl_sync(gmask, am, g * LPP + t);
-                    if (om > gm || (om == gm && oa < ga)) {
-                        gm = om;
-                        ga = oa;
-                    }
-                }
-#pragma unroll
-                for (int m = 0; m < QPL; ++m) {
-                    const int j = q + LPP * m;
-                    if (RULE == SM_RULE_MAXSUM) {
-                        if (v[u][m].x == gm) s[m].x = fmaf(wv[u], v[u][m].x, s[m].x);
-                        if (v[u][m].y == gm) s[m].y = fmaf(wv[u], v[u][m].y, s[m].y);
-                        if (v[u][m].z == gm) s[m].z = fmaf(wv[u], v[u][m].z, s[m].z);
-                        if (v[u][m].w == gm) s[m].w = fmaf(wv[u], v[u][m].w, s[m].w);
-                    } else {
-                        if (ga == 4 * j) s[m].x += wv[u];
-                        if (ga == 4 * j + 1) s[m].y += wv[u];
-                        if (ga == 4 * j + 2) s[m].z += wv[u];
-                        if (ga == 4 * j + 3) s[m].w += wv[u];
-                    }
-                }
-            }
-            ++n;
         }
     }
-    if (active) flush_run();
+    // the warp's share of the stage is in registers: hand it back to the
+    // producer now, so the refill overlaps this warp's arithmetic
+    if (release) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(release);
+    }
+
+    const float4 init = PROD ? make_float4(1.f, 1.f, 1.f, 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 s[QPL];
+#pragma unroll
+    for (int m = 0; m < QPL; ++m) s[m] = init;
+    int cur = -1;
+    uint32_t n = 0;
+    float curw = 1.0f;
+#pragma unroll
+    for (int u = 0; u <= STEPS; ++u) {
+        const int ru = u < STEPS ? r[u] : -2;
+        const bool cut = ru != cur || (IMAGE && u < STEPS && wv[u] != curw) || (PROD && n == kMaxFactors);
+        const bool fl = cut && cur >= 0;
+        const unsigned b = __ballot_sync(kFull, fl && q == 0);
+        if (b) {
+            if (fl) {
+                const int slot = qu.cnt + __popc(b & below);
+#pragma unroll
+                for (int m = 0; m < QPL; ++m) qu.v()[slot * Q + q + LPP * m] = s[m];
+                if (q == 0) {
+                    qu.row()[slot] = cur;
+                    qu.n()[slot] = n;
+                    if (IMAGE && PROD) qu.w()[slot] = curw;
+                }
+            }
+            qu.cnt += __popc(b);
+            if (qu.cnt > RunQueue<C>::kCap - G) drain<C, RULE, IMAGE>(a, qu, lane);
+        }
+        if (u == STEPS) break;
+        if (cut) {
+            cur = ru;
+            curw = wv[u];
+            n = 0;
+#pragma unroll
+            for (int m = 0; m < QPL; ++m) s[m] = init;
+        }
+        // background and past-range pixels are added too, into a run that is
+        // never queued (no branch on the pixel)
+        const float wk = wv[u];
+        if (RULE == SM_RULE_SUM) {
+#pragma unroll
+            for (int m = 0; m < QPL; ++m) {
+                s[m].x = fmaf(wk, v[u][m].x, s[m].x);
+                s[m].y = fmaf(wk, v[u][m].y, s[m].y);
+                s[m].z = fmaf(wk, v[u][m].z, s[m].z);
+                s[m].w = fmaf(wk, v[u][m].w, s[m].w);
+            }
+        } else if (RULE == SM_RULE_LOGSUM) {
+#pragma unroll
+            for (int m = 0; m < QPL; ++m) {
+                s[m].x *= fmaxf(v[u][m].x, kPMin);
+                s[m].y *= fmaxf(v[u][m].y, kPMin);
+                s[m].z *= fmaxf(v[u][m].z, kPMin);
+                s[m].w *= fmaxf(v[u][m].w, kPMin);
+            }
+        } else {
+            // maximum and first arg max of the whole pixel: each lane scans its
+            // quads in class order, then the group combines (lowest class on ties)
+            float mx = -INFINITY;
+            int am = 0x7fffffff;
+#pragma unroll
+            for (int m = 0; m < QPL; ++m) {
+                const int j = q + LPP * m;
+                if (v[u][m].x > mx) { mx = v[u][m].x; am = 4 * j; }
+                if (v[u][m].y > mx) { mx = v[u][m].y; am = 4 * j + 1; }
+                if (v[u][m].z > mx) { mx = v[u][m].z; am = 4 * j + 2; }
+                if (v[u][m].w > mx) { mx = v[u][m].w; am = 4 * j + 3; }
+            }
+            float gm = mx;
+            int ga = am;
+#pragma unroll
+            for (int t = 0; t < LPP; ++t) {
+                const float om = __shfl_sync(kFull, mx, g * LPP + t);
+                const int oa = __shfl_sync(kFull, am, g * LPP + t);
+                if (om > gm || (om == gm && oa < ga)) {
+                    gm = om;
+                    ga = oa;
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < QPL; ++m) {
+                const int j = q + LPP * m;
+                if (RULE == SM_RULE_MAXSUM) {
+                    if (v[u][m].x == gm) s[m].x = fmaf(wk, v[u][m].x, s[m].x);
+                    if (v[u][m].y == gm) s[m].y = fmaf(wk, v[u][m].y, s[m].y);
+                    if (v[u][m].z == gm) s[m].z = fmaf(wk, v[u][m].z, s[m].z);
+                    if (v[u][m].w == gm) s[m].w = fmaf(wk, v[u][m].w, s[m].w);
+                } else {
+                    if (ga == 4 * j) s[m].x += wk;
+                    if (ga == 4 * j + 1) s[m].y += wk;
+                    if (ga == 4 * j + 2) s[m].z += wk;
+                    if (ga == 4 * j + 3) s[m].w += wk;
+                }
+            }
+        }
+        ++n;
+    }
+}
+
+// Shared memory of the consumer warps' run queues (compile-time C only).
+template <int C>
+__host__ __device__ constexpr uint32_t queue_region()
+{
+    return C != 0 ? (kConsumerWarps * RunQueue<C>::bytes + 127u) & ~127u : 0u;
 }
 
 template <int RULE, int DT, bool IMAGE, int C = 0>
@@ -444,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + stages;
-    uint8_t *stage0 = smem + 128;
+    uint8_t *stage0 = smem + 128 + queue_region<C>();
     const StageLayout L = stage_layout<DT>(a);
     const int64_t ntiles_full = a.total_px / kTile;
     const bool ragged = ntiles_full * kTile < a.total_px;
@@ -491,6 +538,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
     }
 
     const int px0 = (warp - 1) * 32;
+    RunQueue<C> qu{smem + 128 + (warp - 1) * RunQueue<C>::bytes, 0};
     int it = 0;
     for (int64_t t = blockIdx.x; t < ntiles_full; t += gridDim.x, ++it) {
         const int s = it % stages;
@@ -506,12 +554,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
             a, t * kTile + px0 + lane, px0 + lane, st + L.probs_bytes,
             L.scale_bytes ? reinterpret_cast<const float *>(st + L.probs_bytes + L.meta_bytes) : nullptr, row, w,
             sc);
-        if constexpr (C != 0)
-            warp_tile_q<C, 5, RULE, DT, true, IMAGE>(a, st, px0, lane, row, w, sc);
-        else
+        if constexpr (C != 0) {
+            warp_tile_q<C, 5, RULE, DT, true, IMAGE>(a, st, px0, lane, row, w, sc, qu, empty + s);
+        } else {
             warp_tile<RULE, DT, true, IMAGE>(a, st, px0, lane, row, w, sc);
-        __syncwarp();
-        if (lane == 0) mbar_arrive(empty + s);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty + s);
+        }
     }
     if (ragged && blockIdx.x == gridDim.x - 1) {
         int row;
@@ -519,362 +568,51 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
         pixel_info<DT, IMAGE>(a, ntiles_full * kTile + px0 + lane, px0 + lane, nullptr, nullptr, row, w, sc);
         if constexpr (C != 0)
             warp_tile_q<C, 5, RULE, DT, false, IMAGE>(a, a.probs + (size_t)ntiles_full * L.probs_bytes, px0, lane, row,
-                                                      w, sc);
+                                                      w, sc, qu, nullptr);
         else
             warp_tile<RULE, DT, false, IMAGE>(a, a.probs + (size_t)ntiles_full * L.probs_bytes, px0, lane, row, w,
                                               sc);
     }
-}
-
-// ---------------------------------------------------------------------------
-// Lane-pair path for c = 40 and c = 20 (QL = quads per lane, compile time).
-// A pixel stream is owned by two lanes (quads j = 2m + l, l the lane's
-// parity), so a pair's reductions of one row land in the same 32-byte
-// sectors.  A warp runs 16 streams of 4 consecutive pixels over a 64-pixel
-// tile; stream k visits its pixels in the order (i + k) mod 4, which makes
-// the 128-bit shared-memory reads of 8 lanes cover 32 distinct banks.  The
-// per-pixel control work is issued once per pair instead of once per group of
-// c/4 lanes.  Each consumer warp owns its own ring of stages (filled
-// round-robin by the producer), so every mbarrier advances phase by phase.
-// ---------------------------------------------------------------------------
-constexpr int kPairTile = 64;    // pixels per tile: 16 streams x 4 pixels
-constexpr int kPairWarps = 4;    // consumer warps per CTA, two CTAs per SM
-constexpr int kPairThreads = 32 * (1 + kPairWarps);
-
-template <int DT>
-__host__ __device__ __forceinline__ StageLayout pair_layout(const Args &a)
-{
-    StageLayout L;
-    L.probs_bytes = (uint32_t)kPairTile * a.c * Elem<DT>::size;
-    L.meta_bytes = kPairTile * (a.keys ? 8u : 4u);
-    L.scale_bytes = (DT != SM_F32 && a.scale_bulk) ? kPairTile * 4u : 0u;
-    L.stride = (L.probs_bytes + L.meta_bytes + L.scale_bytes + 127u) & ~127u;
-    return L;
-}
-
-// Row, weight and scale of one pixel of a stream (both lanes of the pair
-// read it; the even lane re-arms the key and writes the row map).
-template <int DT, bool IMAGE>
-__device__ __forceinline__ void pair_meta(const Args &a, int64_t p, int i, const uint8_t *meta, const float *sscale,
-                                          bool writer, int &row, float &w, float &sc)
-{
-    row = -1;
-    w = 1.0f;
-    sc = 1.0f;
-    if (p >= a.total_px) return;
-    if (a.keys) {
-        const unsigned long long key =
-            meta ? reinterpret_cast<const unsigned long long *>(meta)[i] : a.keys[p];
-        if (writer) a.keys[p] = kEmptyKey;
-        row = (key == kEmptyKey) ? -1 : (int)(unsigned int)key;
-    } else {
-        row = meta ? reinterpret_cast<const int32_t *>(meta)[i] : a.ids_in[p];
+    if constexpr (C != 0) {
+        if (qu.cnt) drain<C, RULE, IMAGE>(a, qu, lane);
     }
-    if (writer && a.ids_out) a.ids_out[p] = row;
-    if (row >= a.n_x) {
-        if (writer) atomicCAS(a.err, 0, (int32_t)kErrRowRange);
-        row = -1;
-    }
-    if (IMAGE && row >= 0) w = __fdiv_rn(1.0f, (float)a.fcnt[(p / a.npix) * a.n_x + row]);
-    if (DT != SM_F32) sc = sscale ? sscale[i] : a.scale[p];
-}
-
-template <int QL, int RULE, bool IMAGE>
-__device__ __forceinline__ void pair_flush(const Args &a, int cur, float w, const float4 (&R)[QL], int nf, uint32_t n,
-                                           int l, int Q)
-{
-    float *dst = a.acc + (int64_t)cur * (4 * Q);
-    const uint64_t keep = l2_evict_last();
-#pragma unroll
-    for (int m = 0; m < QL; ++m) {
-        const int j = 2 * m + l;
-        if (j >= Q) continue;
-        float4 v = R[m];
-        if (RULE == SM_RULE_LOGSUM) {
-            // R holds the product of the run's nf clamped probabilities
-            const float wl = (IMAGE ? w : 1.0f) * kLn2;
-            v = nf ? make_float4(lg2_ftz(v.x) * wl, lg2_ftz(v.y) * wl, lg2_ftz(v.z) * wl, lg2_ftz(v.w) * wl)
-                   : make_float4(0.f, 0.f, 0.f, 0.f);
-        } else if (IMAGE) {
-            v = make_float4(v.x * w, v.y * w, v.z * w, v.w * w);
-        }
-        red_add_v4(dst + 4 * j, v, keep);
-    }
-    if (l == 0) red_add_u32(a.cnt + cur, n, keep);
-}
-
-template <int QL, int DT, bool SMEM>
-__device__ __forceinline__ void pair_load(float4 (&v)[QL], const uint8_t *pix, int l, int Q)
-{
-#pragma unroll
-    for (int m = 0; m < QL; ++m) {
-        const int j = 2 * m + l;
-        v[m] = (j < Q) ? load_quad<DT, SMEM>(pix, 4 * j) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-}
-
-// One warp's 64-pixel tile: stream k = lane / 2 takes pixels 4k .. 4k+3.
-// The lane first copies its share of the tile (4 pixels x QL quads) and the
-// metadata into registers; then the stage is released (release != null), so
-// the producer can refill it while this warp computes.  Runs are cut where
-// the row or the weight changes; log-sum runs multiply at most kMaxFactors
-// clamped probabilities before their logarithm is taken (at most 4 pixels
-// per stream and tile, so exactly once per run).
-template <int QL, int RULE, int DT, bool SMEM, bool IMAGE>
-__device__ __forceinline__ void pair_tile(const Args &a, const uint8_t *tile, const uint8_t *meta,
-                                          const float *sscale, int64_t tile_p0, int lane, uint64_t *release)
-{
-    constexpr int ES = Elem<DT>::size;
-    constexpr int C = (QL == 5) ? 40 : 20;  // the two class counts this path serves
-    constexpr int Q = C / 4;
-    constexpr int pstride = C * ES;         // bytes per pixel, known at compile time
-    const int k = lane >> 1, l = lane & 1;
-    int row[4];
-    float w[4], sc[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int pi = 4 * k + ((i + k) & 3);
-        pair_meta<DT, IMAGE>(a, tile_p0 + pi, pi, meta, sscale, l == 0, row[i], w[i], sc[i]);
-    }
-    float4 V4[4][QL];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        if (row[i] >= 0) pair_load<QL, DT, SMEM>(V4[i], tile + (4 * k + ((i + k) & 3)) * pstride, l, Q);
-    }
-    __syncwarp();
-    if (release && lane == 0) mbar_arrive(release);
-    const float4 init = (RULE == SM_RULE_LOGSUM) ? make_float4(1.f, 1.f, 1.f, 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 R[QL];
-    int cur = -1, nf = 0;
-    float curw = 1.0f;
-    uint32_t n = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        float4 v[QL];
-#pragma unroll
-        for (int m = 0; m < QL; ++m) v[m] = V4[i][m];
-        const int r = row[i];
-        if (r != cur || (IMAGE && w[i] != curw)) {
-            if (cur >= 0) pair_flush<QL, RULE, IMAGE>(a, cur, curw, R, nf, n, l, Q);
-            cur = r;
-            curw = w[i];
-            n = 0;
-            nf = 0;
-#pragma unroll
-            for (int m = 0; m < QL; ++m) R[m] = init;
-        }
-        if (r < 0) continue;
-        if (DT != SM_F32) {
-#pragma unroll
-            for (int m = 0; m < QL; ++m) v[m] = scale4(v[m], sc[i]);
-        }
-        if (RULE == SM_RULE_SUM) {
-#pragma unroll
-            for (int m = 0; m < QL; ++m) {
-                R[m].x += v[m].x;
-                R[m].y += v[m].y;
-                R[m].z += v[m].z;
-                R[m].w += v[m].w;
-            }
-        } else if (RULE == SM_RULE_LOGSUM) {
-#pragma unroll
-            for (int m = 0; m < QL; ++m) {
-                R[m].x *= fmaxf(v[m].x, kPMin);
-                R[m].y *= fmaxf(v[m].y, kPMin);
-                R[m].z *= fmaxf(v[m].z, kPMin);
-                R[m].w *= fmaxf(v[m].w, kPMin);
-            }
-            ++nf;
-        } else {
-            // maximum and first arg max of the whole pixel: each lane scans
-            // its quads in class order, then the pair combines (ties go to
-            // the lower class index)
-            float m = -INFINITY;
-            int am = 0x7fffffff;
-#pragma unroll
-            for (int mm = 0; mm < QL; ++mm) {
-                const int j = 2 * mm + l;
-                if (j >= Q) continue;
-                if (v[mm].x > m) { m = v[mm].x; am = 4 * j; }
-                if (v[mm].y > m) { m = v[mm].y; am = 4 * j + 1; }
-                if (v[mm].z > m) { m = v[mm].z; am = 4 * j + 2; }
-                if (v[mm].w > m) { m = v[mm].w; am = 4 * j + 3; }
-            }
-            // both lanes of a pair share the stream's row, so they reach this
-            // point together; other pairs may have skipped a background pixel
-            const unsigned pair = 3u << (lane & ~1);
-            const float mo = __shfl_xor_sync(pair, m, 1);
-            const int amo = __shfl_xor_sync(pair, am, 1);
-            if (mo > m || (mo == m && amo < am)) {
-                m = mo;
-                am = amo;
-            }
-#pragma unroll
-            for (int mm = 0; mm < QL; ++mm) {
-                const int j = 2 * mm + l;
-                if (RULE == SM_RULE_MAXSUM) {
-                    if (v[mm].x == m) R[mm].x += v[mm].x;
-                    if (v[mm].y == m) R[mm].y += v[mm].y;
-                    if (v[mm].z == m) R[mm].z += v[mm].z;
-                    if (v[mm].w == m) R[mm].w += v[mm].w;
-                } else {
-                    if (am == 4 * j) R[mm].x += 1.0f;
-                    if (am == 4 * j + 1) R[mm].y += 1.0f;
-                    if (am == 4 * j + 2) R[mm].z += 1.0f;
-                    if (am == 4 * j + 3) R[mm].w += 1.0f;
-                }
-            }
-        }
-        ++n;
-    }
-    if (cur >= 0) pair_flush<QL, RULE, IMAGE>(a, cur, curw, R, nf, n, l, Q);
-}
-
-template <int QL, int RULE, int DT, bool IMAGE>
-__global__ void __launch_bounds__(kPairThreads, 2) k_scatter_pair(Args a, int spw)
-{
-    extern __shared__ __align__(128) uint8_t smem[];
-    const int nst = kPairWarps * spw;  // stage s of consumer warp w is w * spw + s
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-    uint64_t *empty = full + nst;
-    uint8_t *stage0 = smem + 512;
-    const StageLayout L = pair_layout<DT>(a);
-    const int64_t ntiles_full = a.total_px / kPairTile;
-    const bool ragged = ntiles_full * kPairTile < a.total_px;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < nst; ++s) {
-            mbar_init(full + s, 1);
-            mbar_init(empty + s, 1);
-        }
-        fence_mbar_init();
-    }
-    __syncthreads();
-
-    if (warp == 0) {
-        if (lane == 0) {
-            const uint64_t pol = l2_evict_first();
-            const uint32_t tx = L.probs_bytes + L.meta_bytes + L.scale_bytes;
-            int64_t it = 0;
-            for (int64_t t = blockIdx.x; t < ntiles_full; t += gridDim.x, ++it) {
-                const int w = (int)(it % kPairWarps);
-                const int64_t kk = it / kPairWarps;  // this warp's kk-th tile
-                const int s = w * spw + (int)(kk % spw);
-                const uint32_t ph = (uint32_t)(kk / spw) & 1u;
-                if (kk >= spw && !mbar_wait(empty + s, ph ^ 1u, kWaitNs)) {
-                    atomicCAS(a.err, 0, (int32_t)kErrTimeout);
-                    break;
-                }
-                uint8_t *st = stage0 + (size_t)s * L.stride;
-                mbar_arrive_expect_tx(full + s, tx);
-                bulk_g2s(st, a.probs + (size_t)t * L.probs_bytes, L.probs_bytes, full + s, pol);
-                const void *meta = a.keys ? static_cast<const void *>(a.keys + t * kPairTile)
-                                          : static_cast<const void *>(a.ids_in + t * kPairTile);
-                bulk_g2s(st + L.probs_bytes, meta, L.meta_bytes, full + s, pol);
-                if (L.scale_bytes)
-                    bulk_g2s(st + L.probs_bytes + L.meta_bytes, a.scale + t * kPairTile, L.scale_bytes, full + s,
-                             pol);
-            }
-            // every issued copy has landed before this thread leaves
-            for (int64_t j = it - (int64_t)nst; j < it; ++j) {
-                if (j < 0) continue;
-                const int w = (int)(j % kPairWarps);
-                const int64_t kk = j / kPairWarps;
-                if (!mbar_wait(full + w * spw + (int)(kk % spw), (uint32_t)(kk / spw) & 1u, kWaitNs))
-                    atomicCAS(a.err, 0, (int32_t)kErrTimeout);
-            }
-        }
-        return;
-    }
-
-    const int cw = warp - 1;
-    int64_t kk = 0;
-    for (int64_t t = blockIdx.x + (int64_t)cw * gridDim.x; t < ntiles_full;
-         t += (int64_t)kPairWarps * gridDim.x, ++kk) {
-        const int s = cw * spw + (int)(kk % spw);
-        const uint32_t ph = (uint32_t)(kk / spw) & 1u;
-        const uint8_t *st = stage0 + (size_t)s * L.stride;
-        if (!mbar_wait(full + s, ph, kWaitNs)) {
-            atomicCAS(a.err, 0, (int32_t)kErrTimeout);
-            return;
-        }
-        // pair_tile releases the stage as soon as its data is in registers
-        pair_tile<QL, RULE, DT, true, IMAGE>(
-            a, st, st + L.probs_bytes,
-            L.scale_bytes ? reinterpret_cast<const float *>(st + L.probs_bytes + L.meta_bytes) : nullptr,
-            t * kPairTile, lane, empty + s);
-    }
-    if (ragged && cw == 0 && blockIdx.x == gridDim.x - 1)
-        pair_tile<QL, RULE, DT, false, IMAGE>(a, a.probs + (size_t)ntiles_full * L.probs_bytes, nullptr, nullptr,
-                                              ntiles_full * kPairTile, lane, nullptr);
 }
 
 int g_num_sms = 0;
+uint32_t g_cta_smem = 0;  // shared memory one CTA may take so that two fit on an SM
 
 void ensure_num_sms()
 {
     if (g_num_sms == 0) {
-        int dev = 0;
+        int dev = 0, per_sm = 0, reserved = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
         if (g_num_sms <= 0) g_num_sms = 1;
+        const int cta = per_sm / 2 - reserved;
+        g_cta_smem = cta > (96 << 10) ? (uint32_t)cta : (96u << 10);
     }
-}
-
-template <int QL, int RULE, int DT, bool IMAGE>
-void launch_pair(const Args &a, cudaStream_t s)
-{
-    static bool configured = false;
-    const StageLayout L = pair_layout<DT>(a);
-    int spw = (int)((96u << 10) / (kPairWarps * L.stride));
-    spw = spw < 1 ? 1 : (spw > 4 ? 4 : spw);
-    const size_t smem = 512 + (size_t)kPairWarps * spw * L.stride;
-    if (!configured) {
-        cudaFuncSetAttribute(k_scatter_pair<QL, RULE, DT, IMAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 << 10);
-        configured = true;
-    }
-    ensure_num_sms();
-    const int64_t ntiles = (a.total_px + kPairTile - 1) / kPairTile;
-    int64_t grid = 2LL * g_num_sms;
-    if (grid > ntiles) grid = ntiles;
-    if (grid < 1) grid = 1;
-    k_scatter_pair<QL, RULE, DT, IMAGE><<<(unsigned)grid, kPairThreads, smem, s>>>(a, spw);
-}
-
-template <int RULE, bool IMAGE>
-bool launch_pair_dt(sm_dtype dt, const Args &a, cudaStream_t s)
-{
-    if (a.c == 40) {
-        if (dt == SM_F32) launch_pair<5, RULE, SM_F32, IMAGE>(a, s);
-        else if (dt == SM_BF16) launch_pair<5, RULE, SM_BF16, IMAGE>(a, s);
-        else launch_pair<5, RULE, SM_FP8_E4M3, IMAGE>(a, s);
-        return true;
-    }
-    if (a.c == 20) {
-        if (dt == SM_F32) launch_pair<3, RULE, SM_F32, IMAGE>(a, s);
-        else if (dt == SM_BF16) launch_pair<3, RULE, SM_BF16, IMAGE>(a, s);
-        else launch_pair<3, RULE, SM_FP8_E4M3, IMAGE>(a, s);
-        return true;
-    }
-    return false;
 }
 
 template <int RULE, int DT, bool IMAGE, int C>
 void launch_one(const Args &a, cudaStream_t s)
 {
     static bool configured = false;
+    ensure_num_sms();
+    // as many stages (up to 4) as fit beside the run queues with two CTAs per SM
     const StageLayout L = stage_layout<DT>(a);
-    int stages = (int)((96u << 10) / L.stride);
+    int stages = (int)((g_cta_smem - 128u - queue_region<C>()) / L.stride);
     stages = stages < 1 ? 1 : (stages > 4 ? 4 : stages);
-    const size_t smem = 128 + (size_t)stages * L.stride;
+    const size_t smem = 128 + queue_region<C>() + (size_t)stages * L.stride;
     if (!configured) {
         cudaFuncSetAttribute(k_scatter_tma<RULE, DT, IMAGE, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 << 10);
+        // the whole unified L1 as shared memory, so that two CTAs fit
+        cudaFuncSetAttribute(k_scatter_tma<RULE, DT, IMAGE, C>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
         configured = true;
     }
-    ensure_num_sms();
     const int64_t ntiles = (a.total_px + kTile - 1) / kTile;
     int64_t grid = 2LL * g_num_sms;
     if (grid > ntiles) grid = ntiles;
