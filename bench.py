@@ -6,7 +6,9 @@ softmax predictions (FP32, pixel-major), log-sum fusion (f_mul) with
 w^(P), arg-max render-back of every frame.  One step = sm_reset +
 sm_fuse_frames(all frames, keeping the row maps) + sm_normalise +
 sm_render_idmap(all frames).  The 49 GB of predictions are resident in HBM
-before timing and are larger than L2, so no L2 flush is needed.
+before timing and are larger than L2, so no L2 flush is needed.  The same
+step is then timed with the predictions stored as BF16 and as FP8 E4M3 with a
+per-pixel scale ("forms" in the JSON line).
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
 a bounded sample of the same workload instead.
@@ -49,6 +51,7 @@ def parse():
     ap.add_argument("--cpu-frames", type=int, default=256, help="oracle sample size (frames)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the BF16 / FP8 storage forms")
     return ap.parse_args()
 
 
@@ -227,50 +230,57 @@ def run_ours(args):
     images = torch.empty((N, H, W), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
-        lf.sm_reset(m, stream)
-        lf.sm_fuse_frames(m, probs, "f32", None, K, T, N, H, W, idmaps, stream)
-        lf.sm_normalise(m, None, None, stream)
-        lf.sm_render_idmap(m, idmaps, N * H * W, images, stream)
-
-    for _ in range(max(args.warmup, 3)):
-        step()
-    lf.sm_check(m, stream)
-    for k in lf.SM_KERNEL:
-        lf.sm_profile_read(m, k)
-
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
-    lf.sm_profile_enable(m, True)
-    with ClockSampler(local) as clk:
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            step()
-        e1.record(stream)
-        barrier()
-    lf.sm_profile_enable(m, False)
-    ms_total = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-    lf.sm_check(m, stream)
-    prof = {k: lf.sm_profile_read(m, k) for k in lf.SM_KERNEL}
-    launches = sum(n for n, _ in prof.values())
-    ms_step = ms_total / args.steps
-    value = ws * N / (ms_step / 1e3)
+    def timed(dtype, x, scale):
+        """Warm-up, then args.steps timed steps of one storage form: device time
+        (max over ranks) and the per-kernel event totals of the timed region."""
+        def step():
+            lf.sm_reset(m, stream)
+            lf.sm_fuse_frames(m, x, dtype, scale, K, T, N, H, W, idmaps, stream)
+            lf.sm_normalise(m, None, None, stream)
+            lf.sm_render_idmap(m, idmaps, N * H * W, images, stream)
 
-    # roofline of the dominant kernel (the scatter): algorithmic bytes per
-    # launch = predictions + row-map read of the frames it processes
-    n_sc, ms_sc = prof["scatter"]
-    bytes_per_frame_scatter = H * W * c * 4 + H * W * 4
-    frames_per_launch = N * args.steps / max(n_sc, 1)
-    achieved = bytes_per_frame_scatter * frames_per_launch / (ms_sc / max(n_sc, 1) / 1e3) / 1e9
+        for _ in range(max(args.warmup, 3)):
+            step()
+        lf.sm_check(m, stream)
+        for k in lf.SM_KERNEL:
+            lf.sm_profile_read(m, k)
+        lf.sm_profile_enable(m, True)
+        with ClockSampler(local) as clk:
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                step()
+            e1.record(stream)
+            barrier()
+        lf.sm_profile_enable(m, False)
+        ms_total = e0.elapsed_time(e1)
+        if ws > 1:
+            t = torch.tensor([ms_total], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms_total = float(t.item())
+        lf.sm_check(m, stream)
+        return ms_total / args.steps, {k: lf.sm_profile_read(m, k) for k in lf.SM_KERNEL}, clk.summary()
+
+    def scatter_roofline(prof, elem_bytes, scaled):
+        """Roofline of the dominant kernel (the scatter): algorithmic bytes per
+        launch = predictions (+ per-pixel scales) + row-map bytes of the frames
+        one launch processes, over the launch's average event time."""
+        n_sc, ms_sc = prof["scatter"]
+        per_frame = H * W * c * elem_bytes + H * W * 4 + (H * W * 4 if scaled else 0)
+        fpl = N * args.steps / max(n_sc, 1)
+        achieved = per_frame * fpl / (ms_sc / max(n_sc, 1) / 1e3) / 1e9
+        return achieved, per_frame, fpl
+
+    ms_step, prof, clocks = timed("f32", probs, None)
+    launches = sum(n for n, _ in prof.values())
+    value = ws * N / (ms_step / 1e3)
+    achieved, bytes_per_frame_scatter, frames_per_launch = scatter_roofline(prof, 4, False)
     peak, peak_kind = peaks()
     kernels = {k: {"launches": n, "ms_per_step": t / args.steps} for k, (n, t) in prof.items() if n}
     tpf = scatter_traffic_per_frame()
@@ -288,11 +298,13 @@ def run_ours(args):
                          "frames_per_launch": frames_per_launch, "peak_kind": peak_kind},
             "kernels": kernels,
             "gpu_launches": launches,
-            "clocks": clk.summary()}
+            "clocks": clocks}
     # step-level HBM fraction on the algorithmic bytes of the whole path
     algo_step = N * (H * W * c * 4 + 2 * H * W * 4 + H * W) + 2 * sg_rows(m, lf) * c * 4
     line["step_hbm_frac"] = algo_step / (ms_step / 1e3) / 1e9 / peak
 
+    if not args.no_forms:
+        line["forms"] = storage_forms(probs, timed, scatter_roofline, peak, N, args.steps)
     if not args.no_e2e and rank == 0:
         try:
             line["e2e"] = e2e(args, lf, m, probs, K, T, dev, stream)
@@ -305,6 +317,44 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def quantise(probs, kind):
+    """Per-pixel scaled storage of the predictions (q = p / scale): BF16 with
+    scale = max_j p_j, or FP8 E4M3 with scale = max_j p_j / 448.  Input
+    preparation, done in chunks outside the timed region."""
+    N = probs.shape[0]
+    qt = torch.bfloat16 if kind == "bf16" else torch.float8_e4m3fn
+    q = torch.empty(probs.shape, dtype=qt, device=probs.device)
+    scale = torch.empty(probs.shape[:-1], dtype=torch.float32, device=probs.device)
+    for a in range(0, N, 50):
+        b = min(N, a + 50)
+        s = probs[a:b].amax(-1, keepdim=True)
+        if kind != "bf16":
+            s = s / 448.0
+        q[a:b] = (probs[a:b] / s).to(qt)
+        scale[a:b] = s[..., 0]
+    return q, scale
+
+
+def storage_forms(probs, timed, scatter_roofline, peak, N, steps):
+    """The same step with the predictions stored as BF16 or FP8 E4M3 plus a
+    per-pixel FP32 scale (FP32 accumulation): frames/s and the scatter's HBM
+    roofline fraction per form."""
+    out = {}
+    for kind, dt, eb in (("bf16", "bf16", 2), ("fp8_e4m3", "fp8_e4m3", 1)):
+        q, scale = quantise(probs, kind)
+        ms, prof, clocks = timed(dt, q, scale)
+        achieved, per_frame, fpl = scatter_roofline(prof, eb, True)
+        out[kind] = {"value": N * dist_env()[0] / (ms / 1e3), "unit": "frames/s", "ms_per_step": ms,
+                     "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                  "frac": achieved / peak, "kernel": "scatter",
+                                  "algorithmic_bytes_per_frame": per_frame, "frames_per_launch": fpl},
+                     "kernels": {k: {"launches": n, "ms_per_step": t / steps} for k, (n, t) in prof.items() if n},
+                     "clocks": clocks}
+        del q, scale
+        torch.cuda.empty_cache()
+    return out
 
 
 def sg_rows(m, lf):

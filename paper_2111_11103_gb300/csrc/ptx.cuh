@@ -98,6 +98,14 @@ __device__ __forceinline__ float lg2_ftz(float x)
     return y;
 }
 
+// Orders this thread's earlier generic-proxy accesses to shared memory before
+// later async-proxy (bulk copy) accesses to it, e.g. a TMA refill of a buffer
+// the thread has written.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // L2 policy for data that should stay resident (the accumulator rows that
 // every frame updates): evict last.
 __device__ __forceinline__ uint64_t l2_evict_last()

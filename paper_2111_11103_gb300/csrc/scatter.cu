@@ -42,7 +42,8 @@ constexpr int kConsumerWarps = 8;   // 32 pixels each
 constexpr int kTile = 32 * kConsumerWarps;  // pixels per tile
 constexpr int kThreads = 32 * (1 + kConsumerWarps);
 constexpr int kUnroll = 4;          // pixels per software-pipelined step
-constexpr int kMaxFactors = 4;      // probabilities multiplied before one log2
+constexpr int kMaxFactors = 4;      // probabilities multiplied before one log2 (a power of two)
+static_assert((kMaxFactors & (kMaxFactors - 1)) == 0, "run splitting masks with kMaxFactors - 1");
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr float kLn2 = 0.693147180559945309f;
 constexpr unsigned kFull = 0xffffffffu;
@@ -276,63 +277,77 @@ __device__ __forceinline__ void warp_tile(const Args &a, const uint8_t *base, in
     if (active) flush<RULE>(a, accq, cur, curw, run, n, q);
 }
 
-// Per-warp queue of finished runs in shared memory, for a compile-time class
-// count C.  An entry is one run of pixels of one row: its C sums of w * phi
-// (log-sum: the C products of its clamped probabilities, at most kMaxFactors
-// each), the row, the run length and (log-sum) the pixel weight.  The whole
-// warp drains the queue together, so every reduction instruction runs with
-// all 32 lanes busy instead of only the lanes of the groups whose run ended.
-template <int C>
-struct RunQueue {
-    static constexpr int kCap = 16;
-    static constexpr uint32_t bytes = kCap * (C * 4 + 12);
-    uint8_t *base;  // kCap x C/4 quads (entry-major) | kCap rows | kCap lengths | kCap weights
-    int cnt;        // entries in use (warp-uniform)
-
-    __device__ __forceinline__ float4 *v() const { return reinterpret_cast<float4 *>(base); }
-    __device__ __forceinline__ int *row() const { return reinterpret_cast<int *>(base + kCap * C * 4); }
-    __device__ __forceinline__ uint32_t *n() const { return reinterpret_cast<uint32_t *>(row() + kCap); }
-    __device__ __forceinline__ float *w() const { return reinterpret_cast<float *>(n() + kCap); }
+// Entries of one warp tile, for a compile-time class count C.  An entry is a
+// run of consecutive pixels of one group with the same row and weight (log-
+// sum: at most kMaxFactors pixels, so the product of its clamped
+// probabilities cannot underflow).  Its C values (sums of phi, or the
+// products) sit in a per-warp array of 32 entries in shared memory; row,
+// length and weight in EntryMeta.  A tile has at most 32 entries (one per
+// pixel), so the array never overflows.
+struct EntryMeta {
+    int row[32];
+    uint32_t n[32];
+    float w[32];
 };
 
-// Adds every queued run into its row of P (16-byte reductions, L2
+template <int C, int DT>
+struct QueueLayout {
+    // with FP32 storage a warp's 32 pixels of the stage are exactly 32
+    // entries: once they are in registers the entries overwrite them
+    static constexpr bool kInStage = Elem<DT>::size == 4;
+    static constexpr uint32_t kMetaBytes = kConsumerWarps * sizeof(EntryMeta);
+    static constexpr uint32_t kQueueBytes = kInStage ? 0u : kConsumerWarps * 32u * C * 4u;
+    static constexpr uint32_t bytes = C != 0 ? (kMetaBytes + kQueueBytes + 127u) & ~127u : 0u;
+};
+
+// Adds the warp's entries into their rows of P (16-byte reductions, L2
 // evict-last: the rows a trajectory keeps revisiting stay in L2 while the
-// prediction stream passes through) and its length into the observation
-// count.  Called by the whole warp.
+// prediction stream passes through) and their lengths into the observation
+// counts.  The whole warp takes part, 32 quads per instruction.
 template <int C, int RULE, bool IMAGE>
-__device__ __forceinline__ void drain(const Args &a, RunQueue<C> &qu, int lane)
+__device__ __forceinline__ void drain(const Args &a, const float4 *queue, const EntryMeta &meta, int E, int lane)
 {
     constexpr int Q = C / 4;
-    __syncwarp();
     const uint64_t keep = l2_evict_last();
-    const int nq = qu.cnt * Q;
-    for (int k = lane; k < nq; k += 32) {
+    for (int k = lane; k < E * Q; k += 32) {
         const int e = k / Q;
-        float4 v = qu.v()[k];
+        const int r = meta.row[e];
+        if ((uint64_t)(int64_t)r >= (uint64_t)a.n_x) {  // never for a consistent layout: latch, skip
+            atomicCAS(a.err, 0, (int32_t)kErrRowRange);
+            continue;
+        }
+        float4 v = queue[k];
         if (RULE == SM_RULE_LOGSUM) {
             // sum_k w log p_k = w ln 2 log2 prod_k p_k
-            const float wl = (IMAGE ? qu.w()[e] : 1.0f) * kLn2;
+            const float wl = (IMAGE ? meta.w[e] : 1.0f) * kLn2;
             v = make_float4(lg2_ftz(v.x) * wl, lg2_ftz(v.y) * wl, lg2_ftz(v.z) * wl, lg2_ftz(v.w) * wl);
+        } else if (IMAGE) {
+            const float we = meta.w[e];
+            v = make_float4(v.x * we, v.y * we, v.z * we, v.w * we);
         }
-        red_add_v4(a.acc + (int64_t)qu.row()[e] * C + 4 * (k - e * Q), v, keep);
+        red_add_v4(a.acc + (int64_t)r * C + 4 * (k - e * Q), v, keep);
     }
-    if (lane < qu.cnt) red_add_u32(a.cnt + qu.row()[lane], qu.n()[lane], keep);
-    __syncwarp();
-    qu.cnt = 0;
+    if (lane < E && (uint64_t)(int64_t)meta.row[lane] < (uint64_t)a.n_x)
+        red_add_u32(a.cnt + meta.row[lane], meta.n[lane], keep);
 }
 
 // One warp's 32 pixels of a tile with a compile-time class count C and LPP
 // lanes per pixel, each lane owning QPL = C / (4 LPP) quads (lane q: quads
-// q, q + LPP, ...).  The warp runs G = 32 / LPP groups, each over a
-// contiguous range of pixels, all in lock step: a step processes one pixel
-// per group, so the per-pixel control work is shared by G pixels and no
-// branch depends on a single group.  A run is cut where the row or the pixel
-// weight changes (log-sum: also after kMaxFactors pixels, so its product
-// cannot underflow); a finished run of a visible row is appended to the
-// queue, which is drained once it could not take another step's runs.
+// q, q + LPP, ...).  The warp runs G = 32 / LPP groups over contiguous pixel
+// ranges in lock step, one pixel per group and step.
+//  1. Layout, once per tile with lane k looking at pixel k: where entries
+//     start and end, each entry's slot (its rank among the tile's entries),
+//     row, length and weight -- a few ballots instead of per-step decisions.
+//  2. Steps: each lane multiplies (adds) its quads of the group's pixel into
+//     the running entry, restarting it where an entry starts, and stores it
+//     into the entry's slot where one ends.  No branch depends on a group.
+//  3. The warp adds all entries into P (drain).
+// queue: the warp's 32-entry array; meta: its entry metadata; release: the
+// stage's empty barrier, arrived on once the stage is no longer read (null
+// for the ragged tile).
 template <int C, int LPP, int RULE, int DT, bool SMEM, bool IMAGE>
 __device__ __forceinline__ void warp_tile_q(const Args &a, const uint8_t *base, int px0, int lane, int row, float w,
-                                            float sc, RunQueue<C> &qu, uint64_t *release)
+                                            float sc, float4 *queue, EntryMeta &meta, uint64_t *release)
 {
     constexpr int ES = Elem<DT>::size;
     constexpr int Q = C / 4;
@@ -341,98 +356,97 @@ __device__ __forceinline__ void warp_tile_q(const Args &a, const uint8_t *base, 
     constexpr int STEPS = (32 + G - 1) / G;  // the longest group range
     constexpr int pstride = C * ES;
     constexpr bool PROD = RULE == SM_RULE_LOGSUM;
+    // first and last pixel of every group range
+    constexpr uint32_t kFirst = [] {
+        uint32_t m = 0;
+        for (int g = 0; g < G; ++g) m |= 1u << ((32 * g) / G);
+        return m;
+    }();
+    constexpr uint32_t kLast = [] {
+        uint32_t m = 0;
+        for (int g = 0; g < G; ++g) m |= 1u << ((32 * (g + 1)) / G - 1);
+        return m;
+    }();
     const int g = lane / LPP, q = lane - g * LPP;
     const bool active = g < G;
     const int start = active ? (32 * g) / G : 0;
     const int len = active ? (32 * (g + 1)) / G - start : 0;
-    const unsigned below = (1u << (g * LPP)) - 1u;  // the lanes of the lower groups
     const uint8_t *pb = base + (px0 + start) * pstride;
 
-    // rows, weights and scales of the group's pixels (-2: past its range)
-    int r[STEPS];
-    float wv[STEPS], sv[STEPS];
-#pragma unroll
-    for (int u = 0; u < STEPS; ++u) {
-        const int k = (start + u) & 31;
-        r[u] = __shfl_sync(kFull, row, k);
-        wv[u] = IMAGE ? __shfl_sync(kFull, w, k) : 1.0f;
-        sv[u] = (DT != SM_F32) ? __shfl_sync(kFull, sc, k) : 1.0f;
-        if (u >= len) r[u] = -2;
-    }
     // the lane's quads of every step's pixel (a stage holds the whole tile;
     // the ragged tile in global memory is read only where a pixel exists)
     float4 v[STEPS][QPL];
+    float sv[STEPS];
 #pragma unroll
     for (int u = 0; u < STEPS; ++u) {
+        const int k = (start + u) & 31;
+        sv[u] = (DT != SM_F32) ? __shfl_sync(kFull, sc, k) : 1.0f;
+        const int rk = SMEM ? 0 : __shfl_sync(kFull, row, k);
 #pragma unroll
         for (int m = 0; m < QPL; ++m) {
             v[u][m] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (SMEM || r[u] >= 0) {
+            if (SMEM || rk >= 0) {
                 v[u][m] = load_quad<DT, SMEM>(pb + u * pstride, 4 * (q + LPP * m));
                 if (DT != SM_F32) v[u][m] = scale4(v[u][m], sv[u]);
             }
         }
     }
-    // the warp's share of the stage is in registers: hand it back to the
-    // producer now, so the refill overlaps this warp's arithmetic
-    if (release) {
-        __syncwarp();
-        if (lane == 0) mbar_arrive(release);
-    }
 
-    const float4 init = PROD ? make_float4(1.f, 1.f, 1.f, 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+    // 1. entry layout (lane = pixel)
+    const uint32_t le = lane == 31 ? kFull : ((2u << lane) - 1u);  // pixels 0 .. lane
+    // (every lane executes every shuffle and ballot: none sits behind a
+    // lane-dependent condition)
+    const int rprev = __shfl_up_sync(kFull, row, 1);
+    const float wprev = IMAGE ? __shfl_up_sync(kFull, w, 1) : w;
+    bool brk = ((kFirst >> lane) & 1u) || row != rprev;
+    if (IMAGE && w != wprev) brk = true;
+    bool first = brk;
+    if (PROD) {
+        // split runs every kMaxFactors pixels
+        const uint32_t B = __ballot_sync(kFull, brk);
+        const int pos = lane - (31 - __clz(B & le));
+        first = brk || (pos & (kMaxFactors - 1)) == 0;
+    }
+    const uint32_t S = __ballot_sync(kFull, first);                 // entry (or background run) starts
+    const uint32_t R = __ballot_sync(kFull, first && row >= 0);     // entry starts
+    const int E = __popc(R);
+    const int slot = __popc(R & le) - 1;
+    const uint32_t next = lane == 31 ? 0u : (S >> (lane + 1)) & 1u;   // the next pixel starts a run
+    const bool last = row >= 0 && (((kLast >> lane) & 1u) || next);
+    if (last && slot >= 0) {
+        meta.row[slot] = row;
+        meta.n[slot] = (uint32_t)(lane - (31 - __clz(S & le)) + 1);
+        if (IMAGE) meta.w[slot] = w;
+    }
+    const int info = (first ? 32 : 0) | (last ? 64 : 0) | (slot & 31);
+    __syncwarp();  // every lane's stage reads are done before entries may overwrite them
+
+    // 2. steps
     float4 s[QPL];
 #pragma unroll
-    for (int m = 0; m < QPL; ++m) s[m] = init;
-    int cur = -1;
-    uint32_t n = 0;
-    float curw = 1.0f;
+    for (int m = 0; m < QPL; ++m) s[m] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int u = 0; u <= STEPS; ++u) {
-        const int ru = u < STEPS ? r[u] : -2;
-        const bool cut = ru != cur || (IMAGE && u < STEPS && wv[u] != curw) || (PROD && n == kMaxFactors);
-        const bool fl = cut && cur >= 0;
-        const unsigned b = __ballot_sync(kFull, fl && q == 0);
-        if (b) {
-            if (fl) {
-                const int slot = qu.cnt + __popc(b & below);
-#pragma unroll
-                for (int m = 0; m < QPL; ++m) qu.v()[slot * Q + q + LPP * m] = s[m];
-                if (q == 0) {
-                    qu.row()[slot] = cur;
-                    qu.n()[slot] = n;
-                    if (IMAGE && PROD) qu.w()[slot] = curw;
-                }
-            }
-            qu.cnt += __popc(b);
-            if (qu.cnt > RunQueue<C>::kCap - G) drain<C, RULE, IMAGE>(a, qu, lane);
-        }
-        if (u == STEPS) break;
-        if (cut) {
-            cur = ru;
-            curw = wv[u];
-            n = 0;
-#pragma unroll
-            for (int m = 0; m < QPL; ++m) s[m] = init;
-        }
-        // background and past-range pixels are added too, into a run that is
-        // never queued (no branch on the pixel)
-        const float wk = wv[u];
+    for (int u = 0; u < STEPS; ++u) {
+        int inf = __shfl_sync(kFull, info, (start + u) & 31);
+        if (u >= len) inf = 0;  // past the group's range
+        const bool st = inf & 32;
         if (RULE == SM_RULE_SUM) {
 #pragma unroll
             for (int m = 0; m < QPL; ++m) {
-                s[m].x = fmaf(wk, v[u][m].x, s[m].x);
-                s[m].y = fmaf(wk, v[u][m].y, s[m].y);
-                s[m].z = fmaf(wk, v[u][m].z, s[m].z);
-                s[m].w = fmaf(wk, v[u][m].w, s[m].w);
+                s[m].x = st ? v[u][m].x : s[m].x + v[u][m].x;
+                s[m].y = st ? v[u][m].y : s[m].y + v[u][m].y;
+                s[m].z = st ? v[u][m].z : s[m].z + v[u][m].z;
+                s[m].w = st ? v[u][m].w : s[m].w + v[u][m].w;
             }
         } else if (RULE == SM_RULE_LOGSUM) {
 #pragma unroll
             for (int m = 0; m < QPL; ++m) {
-                s[m].x *= fmaxf(v[u][m].x, kPMin);
-                s[m].y *= fmaxf(v[u][m].y, kPMin);
-                s[m].z *= fmaxf(v[u][m].z, kPMin);
-                s[m].w *= fmaxf(v[u][m].w, kPMin);
+                const float4 c = make_float4(fmaxf(v[u][m].x, kPMin), fmaxf(v[u][m].y, kPMin),
+                                             fmaxf(v[u][m].z, kPMin), fmaxf(v[u][m].w, kPMin));
+                s[m].x = st ? c.x : s[m].x * c.x;
+                s[m].y = st ? c.y : s[m].y * c.y;
+                s[m].z = st ? c.z : s[m].z * c.z;
+                s[m].w = st ? c.w : s[m].w * c.w;
             }
         } else {
             // maximum and first arg max of the whole pixel: each lane scans its
@@ -461,28 +475,35 @@ __device__ __forceinline__ void warp_tile_q(const Args &a, const uint8_t *base, 
 #pragma unroll
             for (int m = 0; m < QPL; ++m) {
                 const int j = q + LPP * m;
+                float4 c;
                 if (RULE == SM_RULE_MAXSUM) {
-                    if (v[u][m].x == gm) s[m].x = fmaf(wk, v[u][m].x, s[m].x);
-                    if (v[u][m].y == gm) s[m].y = fmaf(wk, v[u][m].y, s[m].y);
-                    if (v[u][m].z == gm) s[m].z = fmaf(wk, v[u][m].z, s[m].z);
-                    if (v[u][m].w == gm) s[m].w = fmaf(wk, v[u][m].w, s[m].w);
+                    c = make_float4(v[u][m].x == gm ? v[u][m].x : 0.f, v[u][m].y == gm ? v[u][m].y : 0.f,
+                                    v[u][m].z == gm ? v[u][m].z : 0.f, v[u][m].w == gm ? v[u][m].w : 0.f);
                 } else {
-                    if (ga == 4 * j) s[m].x += wk;
-                    if (ga == 4 * j + 1) s[m].y += wk;
-                    if (ga == 4 * j + 2) s[m].z += wk;
-                    if (ga == 4 * j + 3) s[m].w += wk;
+                    c = make_float4(ga == 4 * j ? 1.f : 0.f, ga == 4 * j + 1 ? 1.f : 0.f,
+                                    ga == 4 * j + 2 ? 1.f : 0.f, ga == 4 * j + 3 ? 1.f : 0.f);
                 }
+                s[m].x = st ? c.x : s[m].x + c.x;
+                s[m].y = st ? c.y : s[m].y + c.y;
+                s[m].z = st ? c.z : s[m].z + c.z;
+                s[m].w = st ? c.w : s[m].w + c.w;
             }
         }
-        ++n;
+        if (inf & 64) {
+#pragma unroll
+            for (int m = 0; m < QPL; ++m) queue[(inf & 31) * Q + q + LPP * m] = s[m];
+        }
     }
-}
+    __syncwarp();
 
-// Shared memory of the consumer warps' run queues (compile-time C only).
-template <int C>
-__host__ __device__ constexpr uint32_t queue_region()
-{
-    return C != 0 ? (kConsumerWarps * RunQueue<C>::bytes + 127u) & ~127u : 0u;
+    // 3. drain, then hand the stage back (the entries written into it by
+    // plain stores must be ordered before the copy engine's next refill)
+    drain<C, RULE, IMAGE>(a, queue, meta, E, lane);
+    if (release) {
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(release);
+    }
 }
 
 template <int RULE, int DT, bool IMAGE, int C = 0>
@@ -491,7 +512,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + stages;
-    uint8_t *stage0 = smem + 128 + queue_region<C>();
+    uint8_t *stage0 = smem + 128 + QueueLayout<C, DT>::bytes;
     const StageLayout L = stage_layout<DT>(a);
     const int64_t ntiles_full = a.total_px / kTile;
     const bool ragged = ntiles_full * kTile < a.total_px;
@@ -538,7 +559,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
     }
 
     const int px0 = (warp - 1) * 32;
-    RunQueue<C> qu{smem + 128 + (warp - 1) * RunQueue<C>::bytes, 0};
+    EntryMeta &meta = reinterpret_cast<EntryMeta *>(smem + 128)[warp - 1];
+    float4 *own_queue = reinterpret_cast<float4 *>(smem + 128 + QueueLayout<C, DT>::kMetaBytes) + (warp - 1) * 8 * C;
     int it = 0;
     for (int64_t t = blockIdx.x; t < ntiles_full; t += gridDim.x, ++it) {
         const int s = it % stages;
@@ -555,7 +577,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
             L.scale_bytes ? reinterpret_cast<const float *>(st + L.probs_bytes + L.meta_bytes) : nullptr, row, w,
             sc);
         if constexpr (C != 0) {
-            warp_tile_q<C, 5, RULE, DT, true, IMAGE>(a, st, px0, lane, row, w, sc, qu, empty + s);
+            float4 *queue = QueueLayout<C, DT>::kInStage
+                                ? reinterpret_cast<float4 *>(const_cast<uint8_t *>(st) + px0 * C * 4)
+                                : own_queue;
+            warp_tile_q<C, 5, RULE, DT, true, IMAGE>(a, st, px0, lane, row, w, sc, queue, meta, empty + s);
         } else {
             warp_tile<RULE, DT, true, IMAGE>(a, st, px0, lane, row, w, sc);
             __syncwarp();
@@ -566,15 +591,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
         int row;
         float w, sc;
         pixel_info<DT, IMAGE>(a, ntiles_full * kTile + px0 + lane, px0 + lane, nullptr, nullptr, row, w, sc);
-        if constexpr (C != 0)
+        if constexpr (C != 0) {
+            // every stage has been consumed and no copy is in flight: the
+            // warp's share of stage 0 is free for the entries
+            float4 *queue = QueueLayout<C, DT>::kInStage ? reinterpret_cast<float4 *>(stage0 + px0 * C * 4)
+                                                         : own_queue;
             warp_tile_q<C, 5, RULE, DT, false, IMAGE>(a, a.probs + (size_t)ntiles_full * L.probs_bytes, px0, lane, row,
-                                                      w, sc, qu, nullptr);
-        else
+                                                      w, sc, queue, meta, nullptr);
+        } else {
             warp_tile<RULE, DT, false, IMAGE>(a, a.probs + (size_t)ntiles_full * L.probs_bytes, px0, lane, row, w,
                                               sc);
-    }
-    if constexpr (C != 0) {
-        if (qu.cnt) drain<C, RULE, IMAGE>(a, qu, lane);
+        }
     }
 }
 
@@ -600,11 +627,11 @@ void launch_one(const Args &a, cudaStream_t s)
 {
     static bool configured = false;
     ensure_num_sms();
-    // as many stages (up to 4) as fit beside the run queues with two CTAs per SM
+    // as many stages (up to 4) as fit beside the entry arrays with two CTAs per SM
     const StageLayout L = stage_layout<DT>(a);
-    int stages = (int)((g_cta_smem - 128u - queue_region<C>()) / L.stride);
+    int stages = (int)((g_cta_smem - 128u - QueueLayout<C, DT>::bytes) / L.stride);
     stages = stages < 1 ? 1 : (stages > 4 ? 4 : stages);
-    const size_t smem = 128 + queue_region<C>() + (size_t)stages * L.stride;
+    const size_t smem = 128 + QueueLayout<C, DT>::bytes + (size_t)stages * L.stride;
     if (!configured) {
         cudaFuncSetAttribute(k_scatter_tma<RULE, DT, IMAGE, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 << 10);

@@ -314,3 +314,27 @@ def test_kernel_timing_counts_launches(dev, tiny):
         lf.sm_check(m)
     finally:
         lf.sm_mesh_free(m)
+
+
+@pytest.mark.parametrize("kind", ["bf16", "fp8_e4m3"])
+@pytest.mark.parametrize("rule", ["logsum", "sum"])
+def test_precision_error_vs_fp64(ora, medium, kind, rule):
+    """Error of the BF16 / E4M3 storage forms against the FP64 oracle fed the
+    unquantised FP32 predictions: max |delta| of the normalised rows and arg-max
+    agreement.  The bounds hold with margin over what the quantisation itself
+    causes (the oracle fed the dequantised values shows the same figures)."""
+    scene, cams, probs = medium
+    q, scale, _ = _quantise(probs, kind)
+    res = run_gpu(scene, cams, q, rule, "pixel", dtype=kind, scale=scale, reraster=False)
+    mesh = ora.Mesh(scene.vertices, scene.faces)
+    A, cnt = ora.fuse_sequence(mesh, cams.K, cams.cam_to_world, probs.cpu().numpy(), rule, "pixel", nthreads=8)
+    dist, lab = ora.normalise(rule, A, cnt)
+    seen = cnt > 0
+    assert np.array_equal(res.cnt, cnt)
+    max_delta = float(np.abs(res.dist[seen] - dist[seen]).max())
+    agree = float((res.labels[seen] == lab[seen]).mean())
+    bound = {("bf16", "sum"): 1e-3, ("bf16", "logsum"): 0.02,
+             ("fp8_e4m3", "sum"): 0.02, ("fp8_e4m3", "logsum"): 0.1}[(kind, rule)]
+    print(f"{kind} {rule}: max |delta| {max_delta:.3g}, arg-max agreement {agree:.5f} over {seen.sum()} rows")
+    assert max_delta <= bound
+    assert agree >= (0.999 if kind == "bf16" else 0.998)
