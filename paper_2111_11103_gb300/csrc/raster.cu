@@ -11,14 +11,10 @@
 
 #include "lf_internal.cuh"
 #include "ptx.cuh"
+#include "raster_dev.cuh"
 
 namespace lf {
 namespace {
-
-__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
-__device__ __forceinline__ float i2f(long long v) { return __ll2float_rn(v); }
 
 // Camera set-up in binary64 (the only binary64 work on the device): world to
 // camera R = Rcw^T, t = -R C; image rows scaled by 256 (exact) for the
@@ -53,75 +49,6 @@ __global__ void k_project(const sm_intrinsics *__restrict__ Ks, const double *__
     cam.a[11] = __double2float_rn(t[2]);
     out[i] = cam;
 }
-
-// Projects and snaps one vertex; false if it is at/behind the near plane or
-// outside the snap range (its triangle is then dropped).
-__device__ __forceinline__ bool project_vertex(const float *A, float4 p, int &xs, int &ys, float &iz)
-{
-    float X = fadd(fadd(fadd(fmul(A[0], p.x), fmul(A[1], p.y)), fmul(A[2], p.z)), A[3]);
-    float Y = fadd(fadd(fadd(fmul(A[4], p.x), fmul(A[5], p.y)), fmul(A[6], p.z)), A[7]);
-    float Z = fadd(fadd(fadd(fmul(A[8], p.x), fmul(A[9], p.y)), fmul(A[10], p.z)), A[11]);
-    if (!(Z > kZNear)) return false;
-    float xf = fdiv(X, Z);
-    float yf = fdiv(Y, Z);
-    if (!(fabsf(xf) <= kSnapLimit) || !(fabsf(yf) <= kSnapLimit)) return false;
-    xs = __float2int_rn(xf);
-    ys = __float2int_rn(yf);
-    iz = fdiv(1.0f, Z);
-    return true;
-}
-
-// Screen-space triangle after orientation fix-up: positive area, so each edge
-// function is >= 0 inside.  perm[k] = original local index of vertex k.
-struct Tri {
-    int x[3], y[3];
-    float iz[3];
-    long long area2;
-    bool swapped;
-};
-
-__device__ __forceinline__ bool setup_triangle(const float *A, const float4 *__restrict__ V, int4 f, Tri &t)
-{
-    if (!project_vertex(A, V[f.x], t.x[0], t.y[0], t.iz[0])) return false;
-    if (!project_vertex(A, V[f.y], t.x[1], t.y[1], t.iz[1])) return false;
-    if (!project_vertex(A, V[f.z], t.x[2], t.y[2], t.iz[2])) return false;
-    long long area2 = (long long)(t.x[1] - t.x[0]) * (t.y[2] - t.y[0]) - (long long)(t.y[1] - t.y[0]) * (t.x[2] - t.x[0]);
-    if (area2 == 0) return false;
-    t.swapped = area2 < 0;
-    if (t.swapped) {
-        int tx = t.x[1], ty = t.y[1];
-        float tz = t.iz[1];
-        t.x[1] = t.x[2];
-        t.y[1] = t.y[2];
-        t.iz[1] = t.iz[2];
-        t.x[2] = tx;
-        t.y[2] = ty;
-        t.iz[2] = tz;
-        area2 = -area2;
-    }
-    t.area2 = area2;
-    return true;
-}
-
-// Edge function of vertex k (edge b -> c opposite it) at sample (px, py).
-__device__ __forceinline__ long long edge_at(const Tri &t, int k, long long px, long long py)
-{
-    const int b = (k + 1) % 3, c = (k + 2) % 3;
-    long long dx = t.x[c] - t.x[b], dy = t.y[c] - t.y[b];
-    return dx * (py - t.y[b]) - dy * (px - t.x[b]);
-}
-
-// Top-left rule in y-down image coordinates: an edge direction with dy < 0
-// is a left edge, dy == 0 && dx > 0 a top edge; samples on them are inside.
-__device__ __forceinline__ int top_left(const Tri &t, int k)
-{
-    const int b = (k + 1) % 3, c = (k + 2) % 3;
-    int dx = t.x[c] - t.x[b], dy = t.y[c] - t.y[b];
-    return (dy < 0 || (dy == 0 && dx > 0)) ? 1 : 0;
-}
-
-__device__ __forceinline__ int floor256(int a) { return a >> 8; }        // arithmetic shift = floor
-__device__ __forceinline__ int ceil256(int a) { return -((-a) >> 8); }
 
 // World-space bounding box of every cluster of 32 consecutive faces (one warp
 // per cluster); clusters without a valid face are marked with min.w = 1.
@@ -163,76 +90,6 @@ __global__ void k_cluster_bounds(const float4 *__restrict__ V, const int4 *__res
     }
 }
 
-// Conservative frustum test of one cluster (whole warp, uniform result):
-// true when no triangle of the cluster can cover a pixel centre of this
-// frame.  Each of the box's 8 corners is evaluated in homogeneous image
-// coordinates; if one affine bound is violated at all corners it is violated
-// everywhere in the box: every vertex then projects more than 2 pixels left
-// of / right of / above / below the image, or lies in front of the near
-// plane (so every triangle is dropped by the renderer anyway).  The 2-pixel
-// and 0.01 m margins dwarf the binary32 evaluation error of this test.
-__device__ __forceinline__ bool cluster_culled(const float *A, const float4 *__restrict__ bounds, int64_t cl, int H,
-                                               int W, int lane)
-{
-    const float4 lo = bounds[2 * cl], hi = bounds[2 * cl + 1];
-    if (lo.w != 0.0f) return true;
-    const float px = (lane & 1) ? hi.x : lo.x, py = (lane & 2) ? hi.y : lo.y, pz = (lane & 4) ? hi.z : lo.z;
-    const float X = A[0] * px + A[1] * py + A[2] * pz + A[3];
-    const float Y = A[4] * px + A[5] * py + A[6] * pz + A[7];
-    const float Z = A[8] * px + A[9] * py + A[10] * pz + A[11];
-    const bool corner = lane < 8;
-    const bool left = !corner || X + 512.0f * Z < 0.0f;
-    const bool right = !corner || X - 256.0f * (float)(W + 1) * Z > 0.0f;
-    const bool top = !corner || Y + 512.0f * Z < 0.0f;
-    const bool bottom = !corner || Y - 256.0f * (float)(H + 1) * Z > 0.0f;
-    const bool near = !corner || Z < kZNear - 0.01f;
-    return __all_sync(0xffffffffu, left) || __all_sync(0xffffffffu, right) || __all_sync(0xffffffffu, top) ||
-           __all_sync(0xffffffffu, bottom) || __all_sync(0xffffffffu, near);
-}
-
-__device__ __forceinline__ float to_float(int v) { return __int2float_rn(v); }
-__device__ __forceinline__ float to_float(long long v) { return __ll2float_rn(v); }
-
-// Tests every pixel centre of the clamped box [x0, x1] x [y0, y1] with edge
-// functions stepped incrementally in integer type T; covered samples take a
-// 64-bit atomicMin of ((0xFFFFFFFF - bits(1/z)) << 32 | triangle).
-template <typename T>
-__device__ __forceinline__ void raster_box(const Tri &t, int x0, int x1, int y0, int y1, unsigned int fid,
-                                           unsigned long long *__restrict__ frame_keys, int W)
-{
-    T e_row[3], sx[3], sy[3];
-    int tl[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const int bb = (k + 1) % 3, cc = (k + 2) % 3;
-        const T dx = (T)(t.x[cc] - t.x[bb]), dy = (T)(t.y[cc] - t.y[bb]);
-        e_row[k] = dx * ((T)256 * y0 - t.y[bb]) - dy * ((T)256 * x0 - t.x[bb]);
-        sx[k] = (T)-256 * dy;
-        sy[k] = (T)256 * dx;
-        tl[k] = top_left(t, k);
-    }
-    const float farea = i2f(t.area2);
-    for (int py = y0; py <= y1; ++py) {
-        T e0 = e_row[0], e1 = e_row[1], e2 = e_row[2];
-        unsigned long long *row_keys = frame_keys + (int64_t)py * W;
-        for (int px = x0; px <= x1; ++px) {
-            if (e0 + tl[0] > 0 && e1 + tl[1] > 0 && e2 + tl[2] > 0) {
-                const float num =
-                    fadd(fadd(fmul(to_float(e0), t.iz[0]), fmul(to_float(e1), t.iz[1])), fmul(to_float(e2), t.iz[2]));
-                const float inv_z = fdiv(num, farea);
-                const unsigned long long key = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(inv_z)) << 32) | fid;
-                red_min_u64(row_keys + px, key);
-            }
-            e0 += sx[0];
-            e1 += sx[1];
-            e2 += sx[2];
-        }
-        e_row[0] += sy[0];
-        e_row[1] += sy[1];
-        e_row[2] += sy[2];
-    }
-}
-
 // One warp per cluster of 32 faces and one thread per face, for one frame:
 // conservative cluster cull, then per triangle set-up; every pixel centre of
 // the clamped bounding box is tested with incrementally stepped int64 edge
@@ -251,26 +108,7 @@ __global__ void __launch_bounds__(256, 4) k_raster(const float4 *__restrict__ V,
     const int64_t cl = f / kClusterFaces;
     if (cl * kClusterFaces >= F) return;  // whole warp past the end
     if (cluster_culled(A, bounds, cl, H, W, threadIdx.x & 31)) return;
-    if (f >= F) return;
-    const int4 fc = faces[f];
-    if (!fc.w) return;
-    Tri t;
-    if (!setup_triangle(A, V, fc, t)) return;
-    int minx = min(t.x[0], min(t.x[1], t.x[2])), maxx = max(t.x[0], max(t.x[1], t.x[2]));
-    int miny = min(t.y[0], min(t.y[1], t.y[2])), maxy = max(t.y[0], max(t.y[1], t.y[2]));
-    int x0 = max(ceil256(minx), 0), x1 = min(floor256(maxx), W - 1);
-    int y0 = max(ceil256(miny), 0), y1 = min(floor256(maxy), H - 1);
-    if (x0 > x1 || y0 > y1) return;
-
-    const unsigned int fid = (unsigned int)f;
-    unsigned long long *frame_keys = keys + (int64_t)b * H * W;
-    // Small triangles (extent <= 64 px, the common case) keep every edge
-    // function value below 2^30 in magnitude, so the same integers are
-    // stepped in 32 bits; larger ones use 64 bits.  Results are identical.
-    if (maxx - minx <= (1 << 14) && maxy - miny <= (1 << 14))
-        raster_box<int>(t, x0, x1, y0, y1, fid, frame_keys, W);
-    else
-        raster_box<long long>(t, x0, x1, y0, y1, fid, frame_keys, W);
+    raster_face(A, V, faces, F, f, H, W, keys + (int64_t)b * H * W);
 }
 
 // z-buffer -> row map, and re-arms the z-buffer for the next batch.  For a
