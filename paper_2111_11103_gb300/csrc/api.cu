@@ -133,9 +133,13 @@ sm_status check_image(int32_t N, int32_t H, int32_t W)
 // Raster of frames [f0, f0 + nb) into the z-buffer keys (nb x H x W).
 sm_status raster_only(sm_mesh *m, int f0, int nb, int H, int W, unsigned long long *keys, cudaStream_t s)
 {
+    const int64_t ncl = (m->F + lf::kClusterFaces - 1) / lf::kClusterFaces;
+    sm_status st;
+    if ((st = grow(&m->clist, &m->clist_cap, (int64_t)nb * ncl, s, -1, "cluster lists")) != SM_OK) return st;
+    if ((st = grow(&m->ccount, &m->ccount_cap, (int64_t)nb, s, -1, "cluster counts")) != SM_OK) return st;
     {
         ProfScope p(m, SM_K_RASTER, s);
-        lf::launch_raster(m->verts, m->faces, m->F, m->bounds, m->cams, f0, nb, H, W, keys, s);
+        lf::launch_raster(m->verts, m->faces, m->F, m->bounds, m->cams, f0, nb, H, W, keys, m->clist, m->ccount, s);
     }
     LF_LAUNCHED("raster");
     return SM_OK;
@@ -576,7 +580,7 @@ sm_status sm_mesh_free(sm_mesh *m)
         cudaDeviceSynchronize();
         void *bufs[] = {m->verts, m->faces,  m->row0,   m->texinfo, m->acc,     m->cnt,    m->labels8,
                         m->err,   m->cams,   m->keys,   m->idbuf,   m->fcnt,    m->bounds, m->hstage,
-                        m->hids,  m->hlabels, m->hcam};
+                        m->hids,  m->hlabels, m->hcam,  m->clist,   m->ccount};
         for (void *b : bufs)
             if (b) cudaFree(b);
         if (m->rstream) cudaStreamDestroy(m->rstream);

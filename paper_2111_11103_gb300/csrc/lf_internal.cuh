@@ -38,8 +38,13 @@ void launch_project(const sm_intrinsics *K, const double *T, int N, Camera *out,
 // (min, max corner; min.w != 0 marks a cluster without valid faces) per cluster.
 constexpr int kClusterFaces = 32;
 void launch_cluster_bounds(const float4 *V, const int4 *faces, int64_t F, float4 *bounds, cudaStream_t s);
+// Raster of frames [frame0, frame0 + nb) into keys (nb x H x W z-buffer
+// keys): a cluster cull pass writes per-frame lists of the clusters that may
+// be visible (list: nb x ncl entries, count: nb), then the listed clusters
+// are rasterised.
 void launch_raster(const float4 *V, const int4 *faces, int64_t F, const float4 *bounds, const Camera *cams,
-                   int frame0, int nb, int H, int W, unsigned long long *keys, cudaStream_t s);
+                   int frame0, int nb, int H, int W, unsigned long long *keys, int32_t *list, uint32_t *count,
+                   cudaStream_t s);
 void launch_resolve(unsigned long long *keys, int nb, int H, int W, const int32_t *row0, const int32_t *texinfo,
                     const float4 *V, const int4 *faces, const Camera *cams, int frame0, int32_t *idmap,
                     int32_t *idmap2, cudaStream_t s);
@@ -109,6 +114,10 @@ struct sm_mesh {
     int64_t cams_cap = 0;
     unsigned long long *keys = nullptr;
     int64_t keys_cap = 0;
+    int32_t *clist = nullptr;   // visible-cluster lists of one raster batch
+    int64_t clist_cap = 0;
+    uint32_t *ccount = nullptr;  // their lengths
+    int64_t ccount_cap = 0;
     int32_t *idbuf = nullptr;
     int64_t idbuf_cap = 0;
     uint32_t *fcnt = nullptr;

@@ -90,25 +90,72 @@ __global__ void k_cluster_bounds(const float4 *__restrict__ V, const int4 *__res
     }
 }
 
-// One warp per cluster of 32 faces and one thread per face, for one frame:
-// conservative cluster cull, then per triangle set-up; every pixel centre of
-// the clamped bounding box is tested with incrementally stepped int64 edge
-// functions; covered samples take a 64-bit atomicMin of
-// ((0xFFFFFFFF - bits(1/z)) << 32 | triangle) into the frame's z-buffer.
-__global__ void __launch_bounds__(256, 4) k_raster(const float4 *__restrict__ V, const int4 *__restrict__ faces,
-                                                int64_t F, const float4 *__restrict__ bounds,
-                                                const Camera *__restrict__ cams, int frame0, int H, int W,
-                                                unsigned long long *__restrict__ keys)
+// Cluster cull of one batch: one thread per (cluster, frame) evaluates the 8
+// corners of the cluster's world box in homogeneous image coordinates.  If
+// one affine bound is violated at all corners it is violated everywhere in
+// the box: every vertex then projects more than 2 pixels left of / right of /
+// above / below the image, or lies in front of the near plane (so the
+// renderer drops every triangle anyway); the 2-pixel and 0.01 m margins
+// dwarf the binary32 evaluation error.  Every other cluster is appended to
+// its frame's list (one atomic per warp).  blockIdx.y = frame in the batch.
+__global__ void __launch_bounds__(256) k_cull_clusters(const float4 *__restrict__ bounds, int64_t ncl,
+                                                       const Camera *__restrict__ cams, int frame0, int H, int W,
+                                                       int32_t *__restrict__ list, uint32_t *__restrict__ count)
 {
     __shared__ float A[12];
     const int b = blockIdx.y;
     if (threadIdx.x < 12) A[threadIdx.x] = cams[frame0 + b].a[threadIdx.x];
     __syncthreads();
-    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t cl = f / kClusterFaces;
-    if (cl * kClusterFaces >= F) return;  // whole warp past the end
-    if (cluster_culled(A, bounds, cl, H, W, threadIdx.x & 31)) return;
-    raster_face(A, V, faces, F, f, H, W, keys + (int64_t)b * H * W);
+    const int64_t cl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool keep = false;
+    if (cl < ncl) {
+        const float4 lo = bounds[2 * cl], hi = bounds[2 * cl + 1];
+        if (lo.w == 0.0f) {
+            bool left = true, right = true, top = true, bottom = true, near = true;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float px = (k & 1) ? hi.x : lo.x, py = (k & 2) ? hi.y : lo.y, pz = (k & 4) ? hi.z : lo.z;
+                const float X = A[0] * px + A[1] * py + A[2] * pz + A[3];
+                const float Y = A[4] * px + A[5] * py + A[6] * pz + A[7];
+                const float Z = A[8] * px + A[9] * py + A[10] * pz + A[11];
+                left = left && X + 512.0f * Z < 0.0f;
+                right = right && X - 256.0f * (float)(W + 1) * Z > 0.0f;
+                top = top && Y + 512.0f * Z < 0.0f;
+                bottom = bottom && Y - 256.0f * (float)(H + 1) * Z > 0.0f;
+                near = near && Z < kZNear - 0.01f;
+            }
+            keep = !(left || right || top || bottom || near);
+        }
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, keep);
+    if (!mask) return;
+    const int lane = threadIdx.x & 31;
+    uint32_t base = 0;
+    if (lane == __ffs(mask) - 1) base = atomicAdd(count + b, (uint32_t)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
+    if (keep) list[(int64_t)b * ncl + base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)cl;
+}
+
+// Raster of the listed clusters: one warp per cluster and one thread per
+// face; blockIdx.y = frame in the batch, the x blocks' warps stride over the
+// frame's list.  Set-up and box walk as in raster_face.
+__global__ void __launch_bounds__(256, 4) k_raster_list(const float4 *__restrict__ V, const int4 *__restrict__ faces,
+                                                     int64_t F, int64_t ncl, const int32_t *__restrict__ list,
+                                                     const uint32_t *__restrict__ count,
+                                                     const Camera *__restrict__ cams, int frame0, int H, int W,
+                                                     unsigned long long *__restrict__ keys)
+{
+    __shared__ float A[12];
+    const int b = blockIdx.y;
+    if (threadIdx.x < 12) A[threadIdx.x] = cams[frame0 + b].a[threadIdx.x];
+    __syncthreads();
+    const uint32_t n = count[b];
+    const int warps = blockDim.x >> 5;
+    unsigned long long *frame_keys = keys + (int64_t)b * H * W;
+    for (uint32_t j = blockIdx.x * warps + (threadIdx.x >> 5); j < n; j += gridDim.x * warps) {
+        const int64_t cl = list[(int64_t)b * ncl + j];
+        raster_face(A, V, faces, F, cl * kClusterFaces + (threadIdx.x & 31), H, W, frame_keys);
+    }
 }
 
 // z-buffer -> row map, and re-arms the z-buffer for the next batch.  For a
@@ -282,11 +329,18 @@ void launch_cluster_bounds(const float4 *V, const int4 *faces, int64_t F, float4
 }
 
 void launch_raster(const float4 *V, const int4 *faces, int64_t F, const float4 *bounds, const Camera *cams,
-                   int frame0, int nb, int H, int W, unsigned long long *keys, cudaStream_t s)
+                   int frame0, int nb, int H, int W, unsigned long long *keys, int32_t *list, uint32_t *count,
+                   cudaStream_t s)
 {
     if (F <= 0 || nb <= 0) return;
-    dim3 grid((unsigned)((F + 255) / 256), (unsigned)nb);
-    k_raster<<<grid, 256, 0, s>>>(V, faces, F, bounds, cams, frame0, H, W, keys);
+    const int64_t ncl = (F + kClusterFaces - 1) / kClusterFaces;
+    cudaMemsetAsync(count, 0, (size_t)nb * sizeof(uint32_t), s);
+    k_cull_clusters<<<dim3((unsigned)((ncl + 255) / 256), (unsigned)nb), 256, 0, s>>>(bounds, ncl, cams, frame0, H,
+                                                                                     W, list, count);
+    // enough warps per frame for a typical visible fraction; warps loop over longer lists
+    const int64_t bx = ncl / 32 < 1 ? 1 : (ncl / 32 > 128 ? 128 : ncl / 32);
+    k_raster_list<<<dim3((unsigned)bx, (unsigned)nb), 256, 0, s>>>(V, faces, F, ncl, list, count, cams, frame0, H, W,
+                                                                   keys);
 }
 
 void launch_resolve(unsigned long long *keys, int nb, int H, int W, const int32_t *row0, const int32_t *texinfo,

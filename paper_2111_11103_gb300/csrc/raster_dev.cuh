@@ -1,7 +1,6 @@
 // Device-side raster rules shared by the raster kernels and the fused
 // scatter (Sec. 3.3.1): camera-space transform and 1/256-pixel snap of a
-// vertex, triangle set-up with orientation fix-up, the conservative cluster
-// frustum test, and the bounding-box walk that tests every pixel centre with
+// vertex, triangle set-up with orientation fix-up, and the bounding-box walk that tests every pixel centre with
 // integer edge functions (top-left fill rule) and keeps the nearest surface
 // per pixel with a 64-bit atomicMin of ((0xFFFFFFFF - bits(1/z)) << 32 | triangle).
 //
@@ -89,33 +88,6 @@ __device__ __forceinline__ int top_left(const Tri &t, int k)
 __device__ __forceinline__ int floor256(int a) { return a >> 8; }        // arithmetic shift = floor
 __device__ __forceinline__ int ceil256(int a) { return -((-a) >> 8); }
 
-// Conservative frustum test of one cluster (whole warp, uniform result):
-// true when no triangle of the cluster can cover a pixel centre of this
-// frame.  Each of the box's 8 corners is evaluated in homogeneous image
-// coordinates; if one affine bound is violated at all corners it is violated
-// everywhere in the box: every vertex then projects more than 2 pixels left
-// of / right of / above / below the image, or lies in front of the near
-// plane (so every triangle is dropped by the renderer anyway).  The 2-pixel
-// and 0.01 m margins dwarf the binary32 evaluation error of this test.
-__device__ __forceinline__ bool cluster_culled(const float *A, const float4 *__restrict__ bounds, int64_t cl, int H,
-                                               int W, int lane)
-{
-    const float4 lo = bounds[2 * cl], hi = bounds[2 * cl + 1];
-    if (lo.w != 0.0f) return true;
-    const float px = (lane & 1) ? hi.x : lo.x, py = (lane & 2) ? hi.y : lo.y, pz = (lane & 4) ? hi.z : lo.z;
-    const float X = A[0] * px + A[1] * py + A[2] * pz + A[3];
-    const float Y = A[4] * px + A[5] * py + A[6] * pz + A[7];
-    const float Z = A[8] * px + A[9] * py + A[10] * pz + A[11];
-    const bool corner = lane < 8;
-    const bool left = !corner || X + 512.0f * Z < 0.0f;
-    const bool right = !corner || X - 256.0f * (float)(W + 1) * Z > 0.0f;
-    const bool top = !corner || Y + 512.0f * Z < 0.0f;
-    const bool bottom = !corner || Y - 256.0f * (float)(H + 1) * Z > 0.0f;
-    const bool near = !corner || Z < kZNear - 0.01f;
-    return __all_sync(0xffffffffu, left) || __all_sync(0xffffffffu, right) || __all_sync(0xffffffffu, top) ||
-           __all_sync(0xffffffffu, bottom) || __all_sync(0xffffffffu, near);
-}
-
 __device__ __forceinline__ float to_float(int v) { return __int2float_rn(v); }
 __device__ __forceinline__ float to_float(long long v) { return __ll2float_rn(v); }
 
@@ -132,20 +104,28 @@ __device__ __forceinline__ void raster_box(const Tri &t, int x0, int x1, int y0,
     for (int k = 0; k < 3; ++k) {
         const int bb = (k + 1) % 3, cc = (k + 2) % 3;
         const T dx = (T)(t.x[cc] - t.x[bb]), dy = (T)(t.y[cc] - t.y[bb]);
-        e_row[k] = dx * ((T)256 * y0 - t.y[bb]) - dy * ((T)256 * x0 - t.x[bb]);
+        tl[k] = top_left(t, k);
+        // stepped with the fill-rule bias folded in: inside iff every biased value > 0
+        e_row[k] = dx * ((T)256 * y0 - t.y[bb]) - dy * ((T)256 * x0 - t.x[bb]) + (T)tl[k];
         sx[k] = (T)-256 * dy;
         sy[k] = (T)256 * dx;
-        tl[k] = top_left(t, k);
     }
+    // inv_z = RN(num / area2) by Markstein's correction (P. Markstein, IBM J.
+    // Res. Dev. 34(1), 1990): with y = RN(1 / b) and q = RN(a y), the exact
+    // remainder r = a - b q (one FMA) gives RN(a / b) = RN(q + r y) for
+    // normal, non-overflowing quotients -- here 1/z of a vertex in front of the
+    // near plane.  One division per triangle instead of one per pixel.
     const float farea = i2f(t.area2);
+    const float rcp = fdiv(1.0f, farea);
     for (int py = y0; py <= y1; ++py) {
         T e0 = e_row[0], e1 = e_row[1], e2 = e_row[2];
         unsigned long long *row_keys = frame_keys + (int64_t)py * W;
         for (int px = x0; px <= x1; ++px) {
-            if (e0 + tl[0] > 0 && e1 + tl[1] > 0 && e2 + tl[2] > 0) {
-                const float num =
-                    fadd(fadd(fmul(to_float(e0), t.iz[0]), fmul(to_float(e1), t.iz[1])), fmul(to_float(e2), t.iz[2]));
-                const float inv_z = fdiv(num, farea);
+            if (e0 > 0 && e1 > 0 && e2 > 0) {
+                const float num = fadd(fadd(fmul(to_float(e0 - tl[0]), t.iz[0]), fmul(to_float(e1 - tl[1]), t.iz[1])),
+                                       fmul(to_float(e2 - tl[2]), t.iz[2]));
+                const float q = fmul(num, rcp);
+                const float inv_z = __fmaf_rn(__fmaf_rn(-farea, q, num), rcp, q);
                 const unsigned long long key = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(inv_z)) << 32) | fid;
                 red_min_u64(row_keys + px, key);
             }
