@@ -250,9 +250,10 @@ sm_status sm_render_rows_noalloc(const float *d_vertices, int64_t V, const int32
                                  int32_t W, int32_t *d_idmap_out, void *stream);
 
 /* Kernel timing: when enabled, every launch of the kernels below is bracketed
- * by CUDA events on the launching stream.  sm_profile_read synchronises those
- * events and returns the launch count and total device time since the last
- * read (then clears them). */
+ * by CUDA events on the launching stream (the raster kind brackets its two
+ * kernels, cluster cull and raster, together).  sm_profile_read synchronises
+ * those events and returns the number of kernel launches and the total device
+ * time since the last read (then clears them). */
 typedef enum sm_kernel {
     SM_K_PROJECT = 0,   /* per-frame camera set-up (binary64)                  */
     SM_K_RASTER = 1,    /* triangle set-up, coverage and depth test            */

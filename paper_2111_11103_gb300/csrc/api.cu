@@ -62,9 +62,11 @@ struct ProfScope {
     int k;
     cudaStream_t s;
     sm_mesh::EvPair *ev = nullptr;
-    ProfScope(sm_mesh *m_, sm_kernel k_, cudaStream_t s_) : m(m_), k((int)k_), s(s_)
+    // kernels: how many kernel launches the scope brackets
+    ProfScope(sm_mesh *m_, sm_kernel k_, cudaStream_t s_, int kernels = 1) : m(m_), k((int)k_), s(s_)
     {
         if (!m->prof) return;
+        m->ev_kernels[k] += kernels;
         if (m->ev_used[k] == m->ev[k].size()) {
             sm_mesh::EvPair p;
             if (cudaEventCreate(&p.a) != cudaSuccess) return;
@@ -138,7 +140,7 @@ sm_status raster_only(sm_mesh *m, int f0, int nb, int H, int W, unsigned long lo
     if ((st = grow(&m->clist, &m->clist_cap, (int64_t)nb * ncl, s, -1, "cluster lists")) != SM_OK) return st;
     if ((st = grow(&m->ccount, &m->ccount_cap, (int64_t)nb, s, -1, "cluster counts")) != SM_OK) return st;
     {
-        ProfScope p(m, SM_K_RASTER, s);
+        ProfScope p(m, SM_K_RASTER, s, 2);
         lf::launch_raster(m->verts, m->faces, m->F, m->bounds, m->cams, f0, nb, H, W, keys, m->clist, m->ccount, s);
     }
     LF_LAUNCHED("raster");
@@ -641,9 +643,10 @@ sm_status sm_profile_read(sm_mesh *m, sm_kernel kernel, int64_t *launches, doubl
         LF_CUDA(cudaEventElapsedTime(&ms, m->ev[k][i].a, m->ev[k][i].b), "profile");
         tot += ms;
     }
-    if (launches) *launches = (int64_t)m->ev_used[k];
+    if (launches) *launches = m->ev_kernels[k];
     if (total_ms) *total_ms = tot;
     m->ev_used[k] = 0;
+    m->ev_kernels[k] = 0;
     return SM_OK;
 }
 

@@ -146,4 +146,5 @@ struct sm_mesh {
     };
     std::vector<EvPair> ev[SM_K_COUNT_KINDS];
     size_t ev_used[SM_K_COUNT_KINDS] = {};
+    int64_t ev_kernels[SM_K_COUNT_KINDS] = {};  // kernel launches inside the used scopes
 };

@@ -311,6 +311,8 @@ def test_kernel_timing_counts_launches(dev, tiny):
         assert n >= 1 and ms > 0
         n, ms = lf.sm_profile_read(m, "scatter")
         assert n == 0 and ms == 0
+        n, ms = lf.sm_profile_read(m, "raster")  # one batch: cluster cull + raster
+        assert n == 2 and ms > 0
         lf.sm_check(m)
     finally:
         lf.sm_mesh_free(m)
