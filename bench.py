@@ -125,7 +125,7 @@ def scatter_traffic_per_frame():
     """DRAM bytes (read + write) per frame of the scatter kernel, from the
     committed ncu summary, or None when the kernel's source has changed since
     that capture (the counters would no longer describe it)."""
-    path = os.path.join(ROOT, "profiles", "scatter_pair_paper_room.md")
+    path = os.path.join(ROOT, "profiles", "scatter_paper_room.md")
     try:
         fields = dict(re.findall(r"^\s+(\w+): (\S+)$", open(path).read(), re.M))
         sha = hashlib.sha256()
