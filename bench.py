@@ -378,13 +378,22 @@ def sg_rows(m, lf):
 def e2e(args, lf, m, probs, K, T, dev, stream):
     """Same metric end to end through the C ABI with HOST buffers: one
     sm_fuse_render_host call per step streams the predictions and cameras
-    host -> device (pinned memory), fuses, normalises, renders every frame and
-    copies the label images back, all inside the timed region."""
+    host -> device (page-locked memory from sm_host_alloc), fuses, normalises,
+    renders every frame and copies the label images back, all inside the
+    timed region."""
     N, H, W, c = probs.shape
-    h_probs = torch.empty(probs.shape, dtype=probs.dtype, pin_memory=True)
-    h_probs.copy_(probs)
+    # page-locked host buffers from the library (one block each), written by
+    # the CPU as a data loader would (staged through pageable memory: pages
+    # that the GPU itself wrote by DMA stream back markedly slower here)
+    h_probs = lf.pinned_empty(probs.shape, probs.dtype)
+    tmp = torch.empty((50,) + tuple(probs.shape[1:]), dtype=probs.dtype)
+    for a in range(0, N, 50):
+        n = min(50, N - a)
+        tmp[:n].copy_(probs[a:a + n])
+        h_probs[a:a + n].copy_(tmp[:n])
+    del tmp
     h_K, h_T = K.cpu().pin_memory(), T.cpu().pin_memory()
-    h_img = torch.empty((N, H, W), dtype=torch.uint8, pin_memory=True)
+    h_img = lf.pinned_empty((N, H, W), torch.uint8)
 
     def step():
         lf.sm_reset(m, stream)

@@ -184,6 +184,16 @@ sm_status sm_fuse_render_host(sm_mesh *m, const void *h_probs, sm_dtype dtype, c
                               const sm_intrinsics *h_K, const double *h_cam_to_world, int32_t N, int32_t H, int32_t W,
                               uint8_t *h_labels_out, void *stream);
 
+/* Page-locked host memory for the host buffers of sm_fuse_render_host (the
+ * paper has no counterpart: this is plumbing of the host path).  Memory from
+ * here is copied to the device at the host link's full rate in one piece,
+ * whatever its size; some runtimes pin very large tensors in ways that copy
+ * markedly slower.  *out receives bytes > 0 bytes of host memory, owned by the
+ * caller until sm_host_free(*out).
+ * Errors: SM_ERR_INVALID_ARG (NULL out, bytes == 0), SM_ERR_OOM. */
+sm_status sm_host_alloc(uint64_t bytes, void **out);
+sm_status sm_host_free(void *p);
+
 /* Zeroes the accumulators and observation counts. */
 sm_status sm_reset(sm_mesh *m, void *stream);
 

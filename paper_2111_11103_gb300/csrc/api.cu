@@ -251,12 +251,16 @@ sm_status sm_mesh_upload(const float *d_vertices, int64_t V, const int32_t *d_fa
         return bail(cuda_fail(e, "raster stream"));
     if ((e = cudaEventCreateWithFlags(&m->ev_start, cudaEventDisableTiming)) != cudaSuccess)
         return bail(cuda_fail(e, "events"));
-    if ((e = cudaStreamCreateWithFlags(&m->cstream, cudaStreamNonBlocking)) != cudaSuccess)
-        return bail(cuda_fail(e, "copy stream"));
+    for (cudaStream_t &cs : m->cstream)
+        if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess)
+            return bail(cuda_fail(e, "copy stream"));
     for (int k = 0; k < 2; ++k) {
-        cudaEvent_t *evs[] = {&m->ev_rast[k], &m->ev_scat[k], &m->ev_h2d[k], &m->ev_free[k]};
+        cudaEvent_t *evs[] = {&m->ev_rast[k], &m->ev_scat[k], &m->ev_free[k]};
         for (cudaEvent_t *ev : evs)
             if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
+                return bail(cuda_fail(e, "events"));
+        for (cudaEvent_t &ev : m->ev_h2d[k])
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
                 return bail(cuda_fail(e, "events"));
     }
     lf::launch_pack_mesh(d_vertices, V, d_faces, F, m->verts, m->faces, m->err, s);
@@ -447,6 +451,26 @@ sm_status sm_render_idmap(sm_mesh *m, const int32_t *d_idmap, int64_t n_pixels, 
     return SM_OK;
 }
 
+sm_status sm_host_alloc(uint64_t bytes, void **out)
+{
+    if (!out || bytes == 0) return fail(SM_ERR_INVALID_ARG, "sm_host_alloc: NULL out or zero bytes");
+    *out = nullptr;
+    const cudaError_t e = cudaHostAlloc(out, (size_t)bytes, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return fail(SM_ERR_OOM, "cudaHostAlloc(%llu bytes): %s", (unsigned long long)bytes, cudaGetErrorString(e));
+    }
+    return SM_OK;
+}
+
+sm_status sm_host_free(void *p)
+{
+    if (!p) return SM_OK;
+    const cudaError_t e = cudaFreeHost(p);
+    return e == cudaSuccess ? SM_OK : cuda_fail(e, "cudaFreeHost");
+}
+
 sm_status sm_fuse_render_host(sm_mesh *m, const void *h_probs, sm_dtype dtype, const float *h_scale,
                               const sm_intrinsics *h_K, const double *h_cam_to_world, int32_t N, int32_t H, int32_t W,
                               uint8_t *h_labels_out, void *stream)
@@ -461,7 +485,7 @@ sm_status sm_fuse_render_host(sm_mesh *m, const void *h_probs, sm_dtype dtype, c
     if (!h_probs || !h_K || !h_cam_to_world || !h_labels_out) return fail(SM_ERR_INVALID_ARG, "NULL host pointer");
     DeviceGuard g(m->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaStream_t cs = m->cstream;
+    constexpr int NC = sm_mesh::kCopyStreams;
     const int64_t npix = (int64_t)H * W;
     const int B = batch_frames(m, npix, N);
     const size_t frame_bytes = (size_t)npix * m->c * dtype_size(dtype);
@@ -483,16 +507,25 @@ sm_status sm_fuse_render_host(sm_mesh *m, const void *h_probs, sm_dtype dtype, c
         const int slot = b & 1;
         uint8_t *dp = m->hstage + slot * slot_bytes;
         float *dsc = dtype != SM_F32 ? reinterpret_cast<float *>(dp + probs_slot) : nullptr;
-        LF_CUDA(cudaStreamWaitEvent(cs, m->ev_free[slot], 0), "event");
-        LF_CUDA(cudaMemcpyAsync(dp, static_cast<const uint8_t *>(h_probs) + (size_t)f0 * frame_bytes,
-                                (size_t)nb * frame_bytes, cudaMemcpyHostToDevice, cs),
-                "copy predictions");
-        if (dsc)
-            LF_CUDA(cudaMemcpyAsync(dsc, h_scale + (size_t)f0 * npix, (size_t)nb * npix * sizeof(float),
-                                    cudaMemcpyHostToDevice, cs),
-                    "copy scales");
-        LF_CUDA(cudaEventRecord(m->ev_h2d[slot], cs), "event");
-        LF_CUDA(cudaStreamWaitEvent(s, m->ev_h2d[slot], 0), "event");
+        // the batch's predictions in NC parts of whole 4 KiB pages, one per copy stream
+        const size_t total = (size_t)nb * frame_bytes;
+        const size_t part = ((total + NC - 1) / NC + 4095) & ~(size_t)4095;
+        const uint8_t *src = static_cast<const uint8_t *>(h_probs) + (size_t)f0 * frame_bytes;
+        for (int k = 0; k < NC; ++k) {
+            cudaStream_t cs = m->cstream[k];
+            LF_CUDA(cudaStreamWaitEvent(cs, m->ev_free[slot], 0), "event");
+            const size_t off = (size_t)k * part;
+            if (off < total)
+                LF_CUDA(cudaMemcpyAsync(dp + off, src + off, total - off < part ? total - off : part,
+                                        cudaMemcpyHostToDevice, cs),
+                        "copy predictions");
+            if (dsc && k == NC - 1)
+                LF_CUDA(cudaMemcpyAsync(dsc, h_scale + (size_t)f0 * npix, (size_t)nb * npix * sizeof(float),
+                                        cudaMemcpyHostToDevice, cs),
+                        "copy scales");
+            LF_CUDA(cudaEventRecord(m->ev_h2d[slot][k], cs), "event");
+            LF_CUDA(cudaStreamWaitEvent(s, m->ev_h2d[slot][k], 0), "event");
+        }
         if ((st = sm_fuse_frames(m, dp, dtype, dsc, d_K + f0, d_T + 16 * (int64_t)f0, nb, H, W,
                                  m->hids + (int64_t)f0 * npix, stream)) != SM_OK)
             return st;
@@ -586,11 +619,15 @@ sm_status sm_mesh_free(sm_mesh *m)
         for (void *b : bufs)
             if (b) cudaFree(b);
         if (m->rstream) cudaStreamDestroy(m->rstream);
-        if (m->cstream) cudaStreamDestroy(m->cstream);
-        cudaEvent_t evs[] = {m->ev_start,  m->ev_rast[0], m->ev_rast[1], m->ev_scat[0], m->ev_scat[1],
-                             m->ev_h2d[0], m->ev_h2d[1],  m->ev_free[0], m->ev_free[1]};
+        for (cudaStream_t cs : m->cstream)
+            if (cs) cudaStreamDestroy(cs);
+        cudaEvent_t evs[] = {m->ev_start,  m->ev_rast[0], m->ev_rast[1], m->ev_scat[0],
+                             m->ev_scat[1], m->ev_free[0], m->ev_free[1]};
         for (cudaEvent_t e : evs)
             if (e) cudaEventDestroy(e);
+        for (auto &slot : m->ev_h2d)
+            for (cudaEvent_t e : slot)
+                if (e) cudaEventDestroy(e);
         for (int k = 0; k < SM_K_COUNT_KINDS; ++k)
             for (auto &p : m->ev[k]) {
                 cudaEventDestroy(p.a);

@@ -127,9 +127,11 @@ struct sm_mesh {
     cudaStream_t rstream = nullptr;
     cudaEvent_t ev_start = nullptr, ev_rast[2] = {nullptr, nullptr}, ev_scat[2] = {nullptr, nullptr};
 
-    // host-streaming path (sm_fuse_render_host): copy stream, staging
-    cudaStream_t cstream = nullptr;
-    cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+    // host-streaming path (sm_fuse_render_host): copy streams (a batch's copy
+    // is split over them so that several copy engines work at once), staging
+    static constexpr int kCopyStreams = 4;
+    cudaStream_t cstream[kCopyStreams] = {};
+    cudaEvent_t ev_h2d[2][kCopyStreams] = {}, ev_free[2] = {nullptr, nullptr};
     uint8_t *hstage = nullptr;   // two batches of predictions (+ scales)
     int64_t hstage_cap = 0;      // bytes
     int32_t *hids = nullptr;     // row maps of all frames of the call

@@ -24,7 +24,7 @@ SM_MAX_CLASSES = 254
 SYMBOLS = ["sm_mesh_upload", "sm_fuse_frames", "sm_normalise", "sm_render_labels", "sm_render_idmap", "sm_reset",
            "sm_read_state", "sm_load_state", "sm_check", "sm_num_rows", "sm_num_classes", "sm_mesh_free",
            "sm_status_string", "sm_last_error", "sm_profile_enable", "sm_profile_read", "sm_render_rows_noalloc",
-           "sm_fuse_render_host"]
+           "sm_fuse_render_host", "sm_host_alloc", "sm_host_free"]
 SM_NOALLOC_MAX_PIXELS = 1572864
 SM_NOALLOC_MAX_FRAMES = 1024
 
@@ -61,6 +61,8 @@ def lib() -> ctypes.CDLL:
             "sm_render_rows_noalloc": [P, i64, P, i64, P, P, i32, i32, i32, P, P],
             "sm_fuse_render_host": [P, P, i32, P, P, P, i32, i32, i32, P, P],
             "sm_profile_read": [P, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)],
+            "sm_host_alloc": [ctypes.c_uint64, ctypes.POINTER(P)],
+            "sm_host_free": [P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -140,6 +142,43 @@ def sm_fuse_render_host(mesh: int, probs, dtype, scale, K, cam_to_world, N: int,
     """Fuse + normalise + render with HOST tensors (pin them for overlap)."""
     _check(lib().sm_fuse_render_host(mesh, _ptr(probs), _enum(SM_DTYPE, dtype), _ptr(scale), _ptr(K),
                                      _ptr(cam_to_world), int(N), int(H), int(W), _ptr(labels_out), _stream(stream)))
+
+
+def sm_host_alloc(nbytes: int) -> int:
+    p = ctypes.c_void_p()
+    _check(lib().sm_host_alloc(int(nbytes), ctypes.byref(p)))
+    return p.value
+
+
+def sm_host_free(p: int):
+    _check(lib().sm_host_free(p))
+
+
+class _HostBlock:
+    """Owns one sm_host_alloc block; freed when the last tensor viewing it dies."""
+
+    def __init__(self, nbytes: int):
+        self.ptr = sm_host_alloc(nbytes)
+        self.nbytes = nbytes
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            lib().sm_host_free(self.ptr)
+            self.ptr = None
+
+
+def pinned_empty(shape, dtype):
+    """Uninitialised CPU tensor in page-locked memory from sm_host_alloc (one
+    block, copied to the device at the host link's full rate).  The memory is
+    released with the tensor."""
+    import math
+    import torch
+    shape = tuple(int(d) for d in shape)
+    nbytes = max(1, math.prod(shape)) * torch.empty((), dtype=dtype).element_size()
+    block = _HostBlock(nbytes)
+    buf = (ctypes.c_uint8 * nbytes).from_address(block.ptr)
+    buf._block = block  # the block lives as long as the buffer, which the tensor keeps
+    return torch.frombuffer(buf, dtype=torch.uint8).view(dtype)[: math.prod(shape)].view(shape)
 
 
 def sm_reset(mesh: int, stream=None):

@@ -264,7 +264,7 @@ def test_state_checkpoint_resume(dev, medium):
     assert_acc_close(acc.cpu().numpy(), full.acc.astype(np.float64))
 
 
-@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("pinned", ["torch", "library", "pageable"])
 def test_host_streaming_matches_device_path(dev, medium, pinned):
     """sm_fuse_render_host (inputs and label images in host memory, streamed
     in batches) gives the same counts, accumulators (1e-5) and label images as
@@ -279,8 +279,13 @@ def test_host_streaming_matches_device_path(dev, medium, pinned):
     h_K = torch.as_tensor(cams.K)
     h_T = torch.as_tensor(cams.cam_to_world.reshape(N, 16))
     h_img = torch.empty((N, H, W), dtype=torch.uint8)
-    if pinned:
+    if pinned == "torch":
         h_probs, h_K, h_T, h_img = (t.pin_memory() for t in (h_probs, h_K, h_T, h_img))
+    elif pinned == "library":  # page-locked blocks from sm_host_alloc
+        blocks = [lf.pinned_empty(t.shape, t.dtype) for t in (h_probs, h_K, h_T, h_img)]
+        for b, t in zip(blocks, (h_probs, h_K, h_T, h_img)):
+            b.copy_(t)
+        h_probs, h_K, h_T, h_img = blocks
     m = lf.sm_mesh_upload(V, Fc, None, c, "logsum", "image")
     try:
         for _ in range(2):  # a second call reuses the staging and starts from reset
