@@ -67,7 +67,7 @@ def lib() -> ctypes.CDLL:
             L.ora_phi.restype = None
             L.ora_phi.argtypes = [i32, P, i32, P]
             L.ora_frame_weights.restype = None
-            L.ora_frame_weights.argtypes = [i32, P, i64, i64, P, P]
+            L.ora_frame_weights.argtypes = [i32, ctypes.c_double, P, i64, i64, P, P]
             L.ora_accumulate.restype = None
             L.ora_accumulate.argtypes = [i32, i64, P, P, P, i32, P, P]
             L.ora_normalise.restype = None
@@ -76,7 +76,11 @@ def lib() -> ctypes.CDLL:
             L.ora_render_labels.argtypes = [P, i64, P, P]
             L.ora_fuse_sequence.restype = ctypes.c_int
             L.ora_fuse_sequence.argtypes = [P, i64, P, i64, P, P, P, i64, P, P, P, i32, i32, i32, i32, i32,
-                                            i32, i32, P, P, P]
+                                            i32, ctypes.c_double, i32, P, P, P]
+            L.ora_visible_area.restype = ctypes.c_int
+            L.ora_visible_area.argtypes = [P, i64, P, i64, P, P, i32, i32, i32, i32, P]
+            L.ora_texel_res_from_gamma.restype = None
+            L.ora_texel_res_from_gamma.argtypes = [P, i64, ctypes.c_float, P]
             L.ora_render_sequence.restype = ctypes.c_int
             L.ora_render_sequence.argtypes = [P, i64, P, i64, P, P, P, P, P, i32, i32, i32, i32, P]
             _lib = L
@@ -190,11 +194,13 @@ def phi(rule: str, p) -> np.ndarray:
     return out
 
 
-def frame_weights(weight: str, idmap, n_x: int) -> np.ndarray:
+def frame_weights(weight: str, idmap, n_x: int, alpha: float = 1.0) -> np.ndarray:
+    """Per-pixel weights of one frame: w^(P) = 1, or (1 - alpha) + alpha / n
+    with n = pixels of the frame on the same row (alpha = 1: w^(I))."""
     idmap = _c(idmap, np.int32).ravel()
     counts = np.zeros(max(n_x, 1), dtype=np.int64)
     w = np.empty(idmap.size, dtype=np.float64)
-    lib().ora_frame_weights(WEIGHTS[weight], _p(idmap), idmap.size, int(n_x), _p(counts), _p(w))
+    lib().ora_frame_weights(WEIGHTS[weight], float(alpha), _p(idmap), idmap.size, int(n_x), _p(counts), _p(w))
     return w
 
 
@@ -223,8 +229,10 @@ def fuse_frames(rule: str, weight: str, idmaps, probs, n_x: int, A=None, cnt=Non
     return A, cnt
 
 
-def fuse_sequence(mesh: Mesh, K, T, probs, rule: str, weight: str, nthreads: int = 1, want_idmaps: bool = False):
-    """Renders and fuses all frames: returns (A, cnt[, idmaps])."""
+def fuse_sequence(mesh: Mesh, K, T, probs, rule: str, weight: str, nthreads: int = 1, want_idmaps: bool = False,
+                  alpha: float = 1.0):
+    """Renders and fuses all frames: returns (A, cnt[, idmaps]).  alpha mixes
+    the image weight (weight == "image"): w = (1 - alpha) + alpha / n."""
     K = _c(np.asarray(K).reshape(-1, 4), np.float64)
     T = _c(np.asarray(T).reshape(-1, 16), np.float64)
     probs = _c(probs, np.float32)
@@ -234,10 +242,31 @@ def fuse_sequence(mesh: Mesh, K, T, probs, rule: str, weight: str, nthreads: int
     idm = np.empty((N, H, W), dtype=np.int32) if want_idmaps else None
     rc = lib().ora_fuse_sequence(_p(mesh.V), mesh.V.shape[0], _p(mesh.faces), mesh.F, _p(mesh.s), _p(mesh.origin),
                                  _p(mesh.id_t), mesh.n_x, _p(K), _p(T), _p(probs), N, H, W, c, RULES[rule],
-                                 WEIGHTS[weight], int(nthreads), _p(A), _p(cnt), _p(idm))
+                                 WEIGHTS[weight], float(alpha), int(nthreads), _p(A), _p(cnt), _p(idm))
     if rc:
         raise MemoryError("oracle fuse_sequence")
     return (A, cnt, idm) if want_idmaps else (A, cnt)
+
+
+def visible_area(vertices, faces, K, T, H: int, W: int, nthreads: int = 1) -> np.ndarray:
+    """a_t: per triangle, the most pixels it is visible on in any one frame."""
+    V = _c(vertices, np.float32).reshape(-1, 3)
+    Fc = _c(faces, np.int32).reshape(-1, 3)
+    K = _c(np.asarray(K).reshape(-1, 4), np.float64)
+    T = _c(np.asarray(T).reshape(-1, 16), np.float64)
+    area = np.zeros(Fc.shape[0], dtype=np.int64)
+    if lib().ora_visible_area(_p(V), V.shape[0], _p(Fc), Fc.shape[0], _p(K), _p(T), K.shape[0], int(H), int(W),
+                              int(nthreads), _p(area)):
+        raise MemoryError("oracle visible_area")
+    return area
+
+
+def texel_res_from_gamma(area, gamma: float) -> np.ndarray:
+    """s_t = max(1, ceil(gamma sqrt(a_t))) in binary32 (Sec. 3.1)."""
+    area = _c(area, np.int64)
+    s = np.empty(area.size, dtype=np.int32)
+    lib().ora_texel_res_from_gamma(_p(area), area.size, float(gamma), _p(s))
+    return s
 
 
 def normalise(rule: str, A, cnt):

@@ -31,6 +31,14 @@
  *   - fusion rules f_sum, f_mul, f_maxsum ..... Eqs. (sum), (mul), (maxsum)
  *     and weighted forms ...................... Eqs. (w-sum), (w-mul), (w-maxsum)
  *   - weights w^(P)=1, w^(I)=1/|K_i ∩ K_x| .... Sec. 3.2.2
+ *   - interpolated weight (1-a) + a/|K_i ∩ K_x|  Fig. 5a (the paper does not
+ *                                               print its form; this linear
+ *                                               mix is the project's reading)
+ *   - texel steps s_t = max(1, ceil(g sqrt a_t)) Sec. 3.1, with a_t read as the
+ *     and the visible-area pre-pass ........... largest number of pixels of
+ *                                               triangle t visible in one
+ *                                               frame (the paper's "area in
+ *                                               pixels" is not pinned down)
  *   - L1 normalisation, argmax ................ Sec. 3.2.1
  *   - render-back of the fused labels ......... Sec. 3.2.1 (rendering the fused
  *                                               mesh from the original poses)
@@ -396,8 +404,8 @@ void ora_phi(int32_t rule, const float *p, int32_t c, double *out)
  * K_x|, the reciprocal of how many pixels of this frame land on the same row.
  * Background pixels get weight 0.  counts is scratch of n_x entries that must
  * be zero on entry and is zero again on exit. */
-void ora_frame_weights(int32_t weight, const int32_t *idmap, int64_t npix, int64_t n_x, int64_t *counts,
-                       double *w_out)
+void ora_frame_weights(int32_t weight, double alpha, const int32_t *idmap, int64_t npix, int64_t n_x,
+                       int64_t *counts, double *w_out)
 {
     (void)n_x;
     if (weight == ORA_WEIGHT_IMAGE) {
@@ -406,7 +414,7 @@ void ora_frame_weights(int32_t weight, const int32_t *idmap, int64_t npix, int64
     }
     for (int64_t k = 0; k < npix; ++k) {
         if (idmap[k] < 0) w_out[k] = 0.0;
-        else if (weight == ORA_WEIGHT_IMAGE) w_out[k] = 1.0 / (double)counts[idmap[k]];
+        else if (weight == ORA_WEIGHT_IMAGE) w_out[k] = (1.0 - alpha) + alpha / (double)counts[idmap[k]];
         else w_out[k] = 1.0;
     }
     if (weight == ORA_WEIGHT_IMAGE) {
@@ -493,6 +501,7 @@ typedef struct {
     const double *T;     /* N x 16 */
     const float *probs;  /* N x H x W x c */
     int32_t N, H, W, c, rule, weight;
+    double alpha;        /* weight mix of w^(I) (1: pure w^(I)) */
     int32_t *idmaps_out; /* N x H x W or NULL */
     int32_t nthreads, tid;
     double *A;           /* this thread's n_x x c */
@@ -519,7 +528,7 @@ static void *ora_worker(void *arg)
             j->status = -1;
             break;
         }
-        ora_frame_weights(j->weight, dst, npix, j->n_x, counts, w);
+        ora_frame_weights(j->weight, j->alpha, dst, npix, j->n_x, counts, w);
         ora_accumulate(j->rule, npix, dst, w, j->probs + (int64_t)i * npix * j->c, j->c, j->A, j->cnt);
     }
     free(idmap); free(w); free(counts);
@@ -534,7 +543,7 @@ static void *ora_worker(void *arg)
 int ora_fuse_sequence(const float *V, int64_t nV, const int32_t *faces, int64_t F, const int32_t *s,
                       const int32_t *origin, const int64_t *id_t, int64_t n_x, const double *K, const double *T,
                       const float *probs, int32_t N, int32_t H, int32_t W, int32_t c, int32_t rule, int32_t weight,
-                      int32_t nthreads, double *A, int64_t *cnt, int32_t *idmaps_out)
+                      double alpha, int32_t nthreads, double *A, int64_t *cnt, int32_t *idmaps_out)
 {
     if (nthreads < 1) nthreads = 1;
     if (nthreads > N && N > 0) nthreads = N;
@@ -549,7 +558,8 @@ int ora_fuse_sequence(const float *V, int64_t nV, const int32_t *faces, int64_t 
         ora_job *j = &jobs[t];
         j->V = V; j->nV = nV; j->faces = faces; j->F = F; j->s = s; j->origin = origin; j->id_t = id_t;
         j->n_x = n_x; j->K = K; j->T = T; j->probs = probs; j->N = N; j->H = H; j->W = W; j->c = c;
-        j->rule = rule; j->weight = weight; j->idmaps_out = idmaps_out; j->nthreads = nthreads; j->tid = t;
+        j->rule = rule; j->weight = weight; j->alpha = alpha; j->idmaps_out = idmaps_out; j->nthreads = nthreads;
+        j->tid = t;
         if (t == 0) {
             j->A = A;
             j->cnt = cnt;
@@ -635,4 +645,101 @@ int ora_render_sequence(const float *V, int64_t nV, const int32_t *faces, int64_
     free(jobs);
     free(th);
     return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Texel resolution from gamma (Sec. 3.1)                                   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    const float *V;
+    int64_t nV;
+    const int32_t *faces;
+    int64_t F;
+    const double *K, *T;
+    const int64_t *id_t; /* face mode: row f = triangle f */
+    int32_t N, H, W, nthreads, tid;
+    int64_t *area; /* this thread's F maxima */
+    int status;
+} ora_ajob;
+
+static void *ora_area_worker(void *arg)
+{
+    ora_ajob *j = (ora_ajob *)arg;
+    int64_t npix = (int64_t)j->H * j->W;
+    int32_t *idmap = (int32_t *)malloc(sizeof(int32_t) * (size_t)npix);
+    int64_t *count = (int64_t *)calloc((size_t)(j->F > 0 ? j->F : 1), sizeof(int64_t));
+    if (!idmap || !count) {
+        j->status = -1;
+        free(idmap); free(count);
+        return NULL;
+    }
+    for (int32_t i = j->tid; i < j->N; i += j->nthreads) {
+        /* face mode (one row per triangle): the row map holds the triangle */
+        if (ora_render_frame(j->V, j->nV, j->faces, j->F, NULL, NULL, j->id_t, j->K + 4 * (int64_t)i,
+                             j->T + 16 * (int64_t)i, j->H, j->W, idmap, NULL, NULL) < 0) {
+            j->status = -1;
+            break;
+        }
+        for (int64_t k = 0; k < npix; ++k)
+            if (idmap[k] >= 0) count[idmap[k]] += 1;
+        for (int64_t f = 0; f < j->F; ++f) {
+            if (count[f] > j->area[f]) j->area[f] = count[f];
+            count[f] = 0;
+        }
+    }
+    free(idmap); free(count);
+    return NULL;
+}
+
+/* a_t of Sec. 3.1 (read as above): for every triangle, the largest number of
+ * pixels on which it is the visible surface in any one of the N frames.
+ * area_out (F) is overwritten.  Frames are dealt to nthreads threads, whose
+ * maxima are combined.  Returns 0, or -1 on allocation failure. */
+int ora_visible_area(const float *V, int64_t nV, const int32_t *faces, int64_t F, const double *K, const double *T,
+                     int32_t N, int32_t H, int32_t W, int32_t nthreads, int64_t *area_out)
+{
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > N && N > 0) nthreads = N;
+    ora_ajob *jobs = (ora_ajob *)calloc((size_t)nthreads, sizeof(ora_ajob));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    int64_t *id_t = (int64_t *)malloc(sizeof(int64_t) * (size_t)(F + 1));
+    int rc = (jobs && th && id_t) ? 0 : -1;
+    if (id_t) ora_row_offsets(NULL, F, id_t);
+    for (int32_t t = 0; t < nthreads && rc == 0; ++t) {
+        ora_ajob *j = &jobs[t];
+        j->V = V; j->nV = nV; j->faces = faces; j->F = F; j->K = K; j->T = T; j->id_t = id_t;
+        j->N = N; j->H = H; j->W = W;
+        j->nthreads = nthreads; j->tid = t;
+        j->area = t == 0 ? area_out : (int64_t *)malloc(sizeof(int64_t) * (size_t)(F > 0 ? F : 1));
+        if (!j->area) rc = -1;
+        else memset(j->area, 0, sizeof(int64_t) * (size_t)F);
+    }
+    if (rc == 0) {
+        for (int32_t t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, ora_area_worker, &jobs[t]);
+        ora_area_worker(&jobs[0]);
+        for (int32_t t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
+        for (int32_t t = 0; t < nthreads; ++t)
+            if (jobs[t].status) rc = -1;
+        for (int32_t t = 1; t < nthreads && rc == 0; ++t)
+            for (int64_t f = 0; f < F; ++f)
+                if (jobs[t].area[f] > area_out[f]) area_out[f] = jobs[t].area[f];
+    }
+    for (int32_t t = 1; jobs && t < nthreads; ++t) free(jobs[t].area);
+    free(jobs);
+    free(th);
+    free(id_t);
+    return rc;
+}
+
+/* s_t = max(1, ceil(gamma * sqrt(a_t))) (Sec. 3.1), evaluated in binary32
+ * (sqrt and product correctly rounded), the precision of the kernel that
+ * takes the same integer decision. */
+void ora_texel_res_from_gamma(const int64_t *area, int64_t F, float gamma, int32_t *s_out)
+{
+    for (int64_t f = 0; f < F; ++f) {
+        const float g = gamma * sqrtf((float)area[f]);
+        const float c = ceilf(g);
+        s_out[f] = c < 1.0f ? 1 : (int32_t)c;
+    }
 }
