@@ -184,6 +184,35 @@ sm_status sm_fuse_render_host(sm_mesh *m, const void *h_probs, sm_dtype dtype, c
                               const sm_intrinsics *h_K, const double *h_cam_to_world, int32_t N, int32_t H, int32_t W,
                               uint8_t *h_labels_out, void *stream);
 
+/* Image-weight mix (Fig. 5a): for a mesh uploaded with SM_WEIGHT_IMAGE, every
+ * later fusion weighs a pixel whose row holds n pixels of its frame by
+ * (1 - alpha) + alpha / n, evaluated in binary32.  alpha = 1 (the default) is
+ * w^(I) of Sec. 3.2.2, alpha = 0 gives weight 1 as w^(P); the paper plots the
+ * interpolation without printing its form, and this linear mix is the
+ * project's reading.  Host-side setting, nothing is enqueued.
+ * Errors: SM_ERR_INVALID_ARG (NULL mesh, a w^(P) mesh, alpha outside [0, 1]). */
+sm_status sm_set_weight_mix(sm_mesh *m, float alpha);
+
+/* Texel steps from gamma (Sec. 3.1): s_t = max(1, ceil(gamma sqrt(a_t))), with
+ * a_t read as the largest number of pixels on which triangle t is the visible
+ * surface in any one of the N frames (the paper's "area in pixels" does not
+ * say over which views).  A visibility pre-pass over the frames (the same
+ * raster as sm_fuse_frames) gives a_t; the square root and product are
+ * evaluated in binary32, correctly rounded.  m must have been uploaded
+ * without texel steps (one row per triangle); the result feeds the
+ * d_texel_res argument of a second sm_mesh_upload.
+ *
+ *   d_K, d_cam_to_world  N frames, as for sm_fuse_frames (device).
+ *   gamma                in [0, 64]; 0 gives s_t = 1 everywhere.
+ *   d_area_out           F int32 a_t, or NULL.
+ *   d_texel_res_out      F int32 s_t (device, required).
+ * Leaves the mesh's accumulators untouched.
+ * Errors: SM_ERR_INVALID_ARG, SM_ERR_STATE (a texel-mode mesh), SM_ERR_OOM,
+ * SM_ERR_CUDA. */
+sm_status sm_texel_res_from_gamma(sm_mesh *m, const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N,
+                                  int32_t H, int32_t W, float gamma, int32_t *d_area_out, int32_t *d_texel_res_out,
+                                  void *stream);
+
 /* Page-locked host memory for the host buffers of sm_fuse_render_host (the
  * paper has no counterpart: this is plumbing of the host path).  Memory from
  * here is copied to the device at the host link's full rate in one piece,

@@ -375,10 +375,10 @@ sm_status sm_fuse_frames(sm_mesh *m, const void *d_probs, sm_dtype dtype, const 
             if (tma)
                 lf::launch_scatter_tma(m->rule, dtype, probs, scale, from_keys ? keys : nullptr,
                                        from_keys ? nullptr : idm, from_keys ? idm : nullptr, npix * nb, npix, m->c,
-                                       fcnt, m->n_x, m->acc, m->cnt, m->err, s);
+                                       fcnt, m->alpha, m->n_x, m->acc, m->cnt, m->err, s);
             else
-                lf::launch_scatter(m->rule, dtype, probs, scale, idm, npix, nb, m->c, fcnt, m->n_x, m->acc, m->cnt,
-                                   m->err, s);
+                lf::launch_scatter(m->rule, dtype, probs, scale, idm, npix, nb, m->c, fcnt, m->alpha, m->n_x, m->acc,
+                                   m->cnt, m->err, s);
         }
         LF_LAUNCHED("scatter");
         if (image_w) {
@@ -448,6 +448,51 @@ sm_status sm_render_idmap(sm_mesh *m, const int32_t *d_idmap, int64_t n_pixels, 
         lf::launch_render(d_idmap, n_pixels, m->labels8, m->n_x, d_labels_out, s);
     }
     LF_LAUNCHED("render");
+    return SM_OK;
+}
+
+sm_status sm_set_weight_mix(sm_mesh *m, float alpha)
+{
+    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
+    if (m->weight != SM_WEIGHT_IMAGE) return fail(SM_ERR_INVALID_ARG, "the weight mix needs a w^(I) mesh");
+    if (!(alpha >= 0.0f && alpha <= 1.0f)) return fail(SM_ERR_INVALID_ARG, "alpha %g outside [0, 1]", (double)alpha);
+    m->alpha = alpha;
+    return SM_OK;
+}
+
+sm_status sm_texel_res_from_gamma(sm_mesh *m, const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N,
+                                  int32_t H, int32_t W, float gamma, int32_t *d_area_out, int32_t *d_texel_res_out,
+                                  void *stream)
+{
+    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
+    if (m->texel_mode) return fail(SM_ERR_STATE, "the visible-area pre-pass needs a mesh uploaded without texels");
+    sm_status st = check_image(N, H, W);
+    if (st != SM_OK) return st;
+    if (!(gamma >= 0.0f && gamma <= 64.0f)) return fail(SM_ERR_INVALID_ARG, "gamma %g outside [0, 64]", (double)gamma);
+    if (!d_texel_res_out || (N > 0 && (!d_K || !d_cam_to_world))) return fail(SM_ERR_INVALID_ARG, "NULL pointer");
+    DeviceGuard g(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t F = m->F, npix = (int64_t)H * W;
+    if ((st = grow(&m->area, &m->area_cap, F > 0 ? F : 1, s, -1, "area buffer")) != SM_OK) return st;
+    LF_CUDA(cudaMemsetAsync(m->area, 0, (size_t)(F > 0 ? F : 1) * sizeof(int32_t), s), "area buffer");
+    if (N > 0 && F > 0) {
+        const int B = batch_frames(m, npix, N);
+        if ((st = prepare_frames(m, d_K, d_cam_to_world, N, npix, B, false, s)) != SM_OK) return st;
+        // per-frame counts share the w^(I) histogram buffer (zero between uses)
+        if ((st = grow(&m->fcnt, &m->fcnt_cap, (int64_t)B * F, s, 0, "per-frame counts")) != SM_OK) return st;
+        for (int f0 = 0; f0 < N; f0 += B) {
+            const int nb = (N - f0 < B) ? N - f0 : B;
+            if ((st = raster_only(m, f0, nb, H, W, m->keys, s)) != SM_OK) return st;
+            lf::launch_area_count(m->keys, npix, nb, m->fcnt, F, s);
+            lf::launch_area_max(m->fcnt, nb, F, m->area, s);
+            LF_LAUNCHED("visible-area pre-pass");
+        }
+    }
+    lf::launch_texel_res(m->area, F, gamma, d_texel_res_out, s);
+    LF_LAUNCHED("texel steps");
+    if (d_area_out && F > 0)
+        LF_CUDA(cudaMemcpyAsync(d_area_out, m->area, (size_t)F * sizeof(int32_t), cudaMemcpyDeviceToDevice, s),
+                "copy areas");
     return SM_OK;
 }
 
@@ -615,7 +660,7 @@ sm_status sm_mesh_free(sm_mesh *m)
         cudaDeviceSynchronize();
         void *bufs[] = {m->verts, m->faces,  m->row0,   m->texinfo, m->acc,     m->cnt,    m->labels8,
                         m->err,   m->cams,   m->keys,   m->idbuf,   m->fcnt,    m->bounds, m->hstage,
-                        m->hids,  m->hlabels, m->hcam,  m->clist,   m->ccount};
+                        m->hids,  m->hlabels, m->hcam,  m->clist,   m->ccount, m->area};
         for (void *b : bufs)
             if (b) cudaFree(b);
         if (m->rstream) cudaStreamDestroy(m->rstream);

@@ -65,6 +65,49 @@ __global__ void k_count_reset(const int32_t *__restrict__ idmap, int64_t total, 
     if (row >= 0 && row < n_x) fcnt[(p / npix) * n_x + row] = 0u;
 }
 
+// Visible-area pre-pass of the texel steps (Sec. 3.1; a_t read as the most
+// pixels a triangle is visible on in one frame).  One thread per pixel of a
+// batch's z-buffers: the winning triangle's per-frame count + 1, and the key
+// re-armed for the next batch.
+__global__ void k_area_count(unsigned long long *__restrict__ keys, int64_t total, int64_t npix,
+                             uint32_t *__restrict__ fcnt, int64_t F)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= total) return;
+    const unsigned long long key = keys[p];
+    if (key == kEmptyKey) return;
+    keys[p] = kEmptyKey;
+    const int64_t f = (int64_t)(unsigned int)key;
+    if (f < F) atomicAdd(fcnt + (p / npix) * F + f, 1u);
+}
+
+// One thread per triangle: the largest of its nb per-frame counts folded into
+// area[f]; the counts are zeroed for the next batch.
+__global__ void k_area_max(uint32_t *__restrict__ fcnt, int nb, int64_t F, int32_t *__restrict__ area)
+{
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F) return;
+    uint32_t m = (uint32_t)area[f];
+    for (int b = 0; b < nb; ++b) {
+        const uint32_t v = fcnt[(int64_t)b * F + f];
+        if (v) {
+            m = v > m ? v : m;
+            fcnt[(int64_t)b * F + f] = 0u;
+        }
+    }
+    area[f] = (int32_t)m;
+}
+
+// s_t = max(1, ceil(gamma sqrt(a_t))) in binary32 with correctly rounded
+// square root and product (Sec. 3.1).
+__global__ void k_texel_res(const int32_t *__restrict__ area, int64_t F, float gamma, int32_t *__restrict__ s_out)
+{
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F) return;
+    const float c = ceilf(__fmul_rn(gamma, __fsqrt_rn((float)area[f])));
+    s_out[f] = c < 1.0f ? 1 : (int32_t)c;
+}
+
 // One thread per pixel: phi(p) of the pixel's prediction, times its weight,
 // added into its row with float atomics; the row's observation count + 1.
 //   sum    phi = p
@@ -74,7 +117,7 @@ __global__ void k_count_reset(const int32_t *__restrict__ idmap, int64_t total, 
 template <int RULE, int DT>
 __global__ void __launch_bounds__(256)
     k_scatter(const void *__restrict__ probs, const float *__restrict__ scale, const int32_t *__restrict__ idmap,
-              int64_t total, int64_t npix, int c, const uint32_t *__restrict__ fcnt, int64_t n_x,
+              int64_t total, int64_t npix, int c, const uint32_t *__restrict__ fcnt, float alpha, int64_t n_x,
               float *__restrict__ acc, uint32_t *__restrict__ cnt, int32_t *__restrict__ err)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -86,7 +129,7 @@ __global__ void __launch_bounds__(256)
         return;
     }
     float w = 1.0f;
-    if (fcnt) w = __fdiv_rn(1.0f, (float)fcnt[(p / npix) * n_x + row]);
+    if (fcnt) w = image_weight(alpha, fcnt[(p / npix) * n_x + row]);
     const float sc = (DT == SM_F32) ? 1.0f : scale[p];
     float *a = acc + (int64_t)row * c;
     const int64_t base = p * c;
@@ -195,16 +238,18 @@ __global__ void k_render16(const int4 *__restrict__ idmap, int64_t n16, const ui
 
 template <int RULE>
 void scatter_dt(sm_dtype dt, dim3 g, cudaStream_t s, const void *probs, const float *scale, const int32_t *idmap,
-                int64_t total, int64_t npix, int c, const uint32_t *fcnt, int64_t n_x, float *acc, uint32_t *cnt,
-                int32_t *err)
+                int64_t total, int64_t npix, int c, const uint32_t *fcnt, float alpha, int64_t n_x, float *acc,
+                uint32_t *cnt, int32_t *err)
 {
     if (dt == SM_F32)
-        k_scatter<RULE, SM_F32><<<g, 256, 0, s>>>(probs, scale, idmap, total, npix, c, fcnt, n_x, acc, cnt, err);
+        k_scatter<RULE, SM_F32>
+            <<<g, 256, 0, s>>>(probs, scale, idmap, total, npix, c, fcnt, alpha, n_x, acc, cnt, err);
     else if (dt == SM_BF16)
-        k_scatter<RULE, SM_BF16><<<g, 256, 0, s>>>(probs, scale, idmap, total, npix, c, fcnt, n_x, acc, cnt, err);
+        k_scatter<RULE, SM_BF16>
+            <<<g, 256, 0, s>>>(probs, scale, idmap, total, npix, c, fcnt, alpha, n_x, acc, cnt, err);
     else
-        k_scatter<RULE, SM_FP8_E4M3><<<g, 256, 0, s>>>(probs, scale, idmap, total, npix, c, fcnt, n_x, acc, cnt,
-                                                        err);
+        k_scatter<RULE, SM_FP8_E4M3>
+            <<<g, 256, 0, s>>>(probs, scale, idmap, total, npix, c, fcnt, alpha, n_x, acc, cnt, err);
 }
 
 }  // namespace
@@ -217,6 +262,25 @@ void launch_count(const int32_t *idmap, const unsigned long long *keys, int64_t 
     k_count<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(idmap, keys, total, npix, fcnt, n_x);
 }
 
+void launch_area_count(unsigned long long *keys, int64_t npix, int nb, uint32_t *fcnt, int64_t F, cudaStream_t s)
+{
+    const int64_t total = npix * nb;
+    if (total <= 0) return;
+    k_area_count<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(keys, total, npix, fcnt, F);
+}
+
+void launch_area_max(uint32_t *fcnt, int nb, int64_t F, int32_t *area, cudaStream_t s)
+{
+    if (F <= 0 || nb <= 0) return;
+    k_area_max<<<(unsigned)((F + 255) / 256), 256, 0, s>>>(fcnt, nb, F, area);
+}
+
+void launch_texel_res(const int32_t *area, int64_t F, float gamma, int32_t *s_out, cudaStream_t s)
+{
+    if (F <= 0) return;
+    k_texel_res<<<(unsigned)((F + 255) / 256), 256, 0, s>>>(area, F, gamma, s_out);
+}
+
 void launch_count_reset(const int32_t *idmap, int64_t npix, int nb, uint32_t *fcnt, int64_t n_x, cudaStream_t s)
 {
     const int64_t total = npix * nb;
@@ -225,24 +289,24 @@ void launch_count_reset(const int32_t *idmap, int64_t npix, int nb, uint32_t *fc
 }
 
 void launch_scatter(sm_rule rule, sm_dtype dtype, const void *probs, const float *scale, const int32_t *idmap,
-                    int64_t npix, int nb, int c, const uint32_t *fcnt, int64_t n_x, float *acc, uint32_t *cnt,
-                    int32_t *err, cudaStream_t s)
+                    int64_t npix, int nb, int c, const uint32_t *fcnt, float alpha, int64_t n_x, float *acc,
+                    uint32_t *cnt, int32_t *err, cudaStream_t s)
 {
     const int64_t total = npix * nb;
     if (total <= 0) return;
     dim3 g((unsigned)((total + 255) / 256));
     switch (rule) {
     case SM_RULE_SUM:
-        scatter_dt<SM_RULE_SUM>(dtype, g, s, probs, scale, idmap, total, npix, c, fcnt, n_x, acc, cnt, err);
+        scatter_dt<SM_RULE_SUM>(dtype, g, s, probs, scale, idmap, total, npix, c, fcnt, alpha, n_x, acc, cnt, err);
         break;
     case SM_RULE_LOGSUM:
-        scatter_dt<SM_RULE_LOGSUM>(dtype, g, s, probs, scale, idmap, total, npix, c, fcnt, n_x, acc, cnt, err);
+        scatter_dt<SM_RULE_LOGSUM>(dtype, g, s, probs, scale, idmap, total, npix, c, fcnt, alpha, n_x, acc, cnt, err);
         break;
     case SM_RULE_MAXSUM:
-        scatter_dt<SM_RULE_MAXSUM>(dtype, g, s, probs, scale, idmap, total, npix, c, fcnt, n_x, acc, cnt, err);
+        scatter_dt<SM_RULE_MAXSUM>(dtype, g, s, probs, scale, idmap, total, npix, c, fcnt, alpha, n_x, acc, cnt, err);
         break;
     default:
-        scatter_dt<SM_RULE_VOTE>(dtype, g, s, probs, scale, idmap, total, npix, c, fcnt, n_x, acc, cnt, err);
+        scatter_dt<SM_RULE_VOTE>(dtype, g, s, probs, scale, idmap, total, npix, c, fcnt, alpha, n_x, acc, cnt, err);
         break;
     }
 }

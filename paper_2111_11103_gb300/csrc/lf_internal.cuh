@@ -37,6 +37,14 @@ void launch_project(const sm_intrinsics *K, const double *T, int N, Camera *out,
 // Faces are processed in clusters of 32 (one warp); bounds holds two float4
 // (min, max corner; min.w != 0 marks a cluster without valid faces) per cluster.
 constexpr int kClusterFaces = 32;
+
+// Image weight of a pixel whose row holds n pixels of its frame, mixed with
+// the pixel weight (Fig. 5a, read as a linear mix): (1 - alpha) + alpha / n in
+// binary32; alpha = 1 gives w^(I) = 1/n exactly, alpha = 0 gives 1.
+__device__ __forceinline__ float image_weight(float alpha, uint32_t n)
+{
+    return __fadd_rn(1.0f - alpha, __fmul_rn(alpha, __fdiv_rn(1.0f, (float)n)));
+}
 void launch_cluster_bounds(const float4 *V, const int4 *faces, int64_t F, float4 *bounds, cudaStream_t s);
 // Raster of frames [frame0, frame0 + nb) into keys (nb x H x W z-buffer
 // keys): a cluster cull pass writes per-frame lists of the clusters that may
@@ -60,8 +68,8 @@ void launch_count(const int32_t *idmap, const unsigned long long *keys, int64_t 
                   int64_t n_x, cudaStream_t s);
 void launch_count_reset(const int32_t *idmap, int64_t npix, int nb, uint32_t *fcnt, int64_t n_x, cudaStream_t s);
 void launch_scatter(sm_rule rule, sm_dtype dtype, const void *probs, const float *scale, const int32_t *idmap,
-                    int64_t npix, int nb, int c, const uint32_t *fcnt, int64_t n_x, float *acc, uint32_t *cnt,
-                    int32_t *err, cudaStream_t s);
+                    int64_t npix, int nb, int c, const uint32_t *fcnt, float alpha, int64_t n_x, float *acc,
+                    uint32_t *cnt, int32_t *err, cudaStream_t s);
 // Pipelined scatter (scatter.cu): TMA-streamed tiles, run-length
 // pre-reduction in registers, vector reductions into the rows.  Face mode
 // passes the z-buffer keys (read, re-armed, optionally written out as row
@@ -70,8 +78,14 @@ void launch_scatter(sm_rule rule, sm_dtype dtype, const void *probs, const float
 bool scatter_tma_supported(int c);
 void launch_scatter_tma(sm_rule rule, sm_dtype dtype, const void *probs, const float *scale,
                         unsigned long long *keys, const int32_t *ids_in, int32_t *ids_out, int64_t total_px,
-                        int64_t npix, int c, const uint32_t *fcnt, int64_t n_x, float *acc, uint32_t *cnt,
-                        int32_t *err, cudaStream_t s);
+                        int64_t npix, int c, const uint32_t *fcnt, float alpha, int64_t n_x, float *acc,
+                        uint32_t *cnt, int32_t *err, cudaStream_t s);
+// Visible-area pre-pass (fuse.cu): per-frame pixel counts of the triangles in
+// a batch's z-buffers (re-armed), folded into per-triangle maxima; texel
+// steps from the maxima.
+void launch_area_count(unsigned long long *keys, int64_t npix, int nb, uint32_t *fcnt, int64_t F, cudaStream_t s);
+void launch_area_max(uint32_t *fcnt, int nb, int64_t F, int32_t *area, cudaStream_t s);
+void launch_texel_res(const int32_t *area, int64_t F, float gamma, int32_t *s_out, cudaStream_t s);
 void launch_normalise(sm_rule rule, const float *acc, const uint32_t *cnt, int64_t n_x, int c, float *dist,
                       int32_t *labels, uint8_t *labels8, cudaStream_t s);
 void launch_render(const int32_t *idmap, int64_t npix, const uint8_t *labels8, int64_t n_x, uint8_t *out,
@@ -96,6 +110,7 @@ struct sm_mesh {
     int32_t c = 0;
     sm_rule rule = SM_RULE_SUM;
     sm_weight weight = SM_WEIGHT_PIXEL;
+    float alpha = 1.0f;  // image-weight mix (sm_set_weight_mix)
     bool texel_mode = false;
     bool normalised = false;
 
@@ -118,6 +133,8 @@ struct sm_mesh {
     int64_t clist_cap = 0;
     uint32_t *ccount = nullptr;  // their lengths
     int64_t ccount_cap = 0;
+    int32_t *area = nullptr;     // visible-area pre-pass: per-triangle maxima
+    int64_t area_cap = 0;
     int32_t *idbuf = nullptr;
     int64_t idbuf_cap = 0;
     uint32_t *fcnt = nullptr;

@@ -42,7 +42,7 @@ def to_dev(scene, cams, texel_res=None, dev="cuda"):
 
 
 def run_gpu(scene, cams, probs, rule, weight, texel_res=None, dtype="f32", scale=None, reraster=True,
-            n_classes=None):
+            n_classes=None, alpha=None):
     from paper_2111_11103_gb300 import labelfuse as lf
     dev = probs.device
     N, H, W = cams.K.shape[0], cams.H, cams.W
@@ -50,6 +50,8 @@ def run_gpu(scene, cams, probs, rule, weight, texel_res=None, dtype="f32", scale
     V, Fc, K, T, tr = to_dev(scene, cams, texel_res, dev)
     m = lf.sm_mesh_upload(V, Fc, tr, c, rule, weight)
     try:
+        if alpha is not None:
+            lf.sm_set_weight_mix(m, alpha)
         n_x = lf.sm_num_rows(m)
         idm = torch.full((N, H, W), -7, dtype=torch.int32, device=dev)
         lf.sm_fuse_frames(m, probs, dtype, scale, K, T, N, H, W, idm)
@@ -112,12 +114,12 @@ def assert_labels_match(rule, labels_gpu, A, cnt, dist_ora, labels_ora):
 
 
 def check_against_oracle(ora, scene, cams, probs_np, res: GpuResult, rule, weight, texel_res=None,
-                         nthreads=4):
+                         nthreads=4, alpha=1.0):
     """Full comparison on a case small enough for the oracle."""
     mesh = ora.Mesh(scene.vertices, scene.faces, texel_res=texel_res)
     assert mesh.n_x == res.n_x
     A, cnt, idm = ora.fuse_sequence(mesh, cams.K, cams.cam_to_world, probs_np, rule, weight, nthreads=nthreads,
-                                    want_idmaps=True)
+                                    want_idmaps=True, alpha=alpha)
     assert np.array_equal(res.idmaps, idm), f"{(res.idmaps != idm).sum()} row-map pixels differ"
     assert np.array_equal(res.cnt, cnt), "observation counts differ"
     assert_acc_close(res.acc, A)
