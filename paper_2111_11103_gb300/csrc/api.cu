@@ -109,7 +109,7 @@ size_t dtype_size(sm_dtype d) { return d == SM_F32 ? 4 : (d == SM_BF16 ? 2 : 1);
 // of the image weights stay within ~512 MB.
 int batch_frames(const sm_mesh *m, int64_t npix, int N)
 {
-    int64_t B = (int64_t)(48u << 20) / (npix * 8);
+    int64_t B = (m->tuned_B > 0 && m->tuned_npix == npix) ? m->tuned_B : (int64_t)(48u << 20) / (npix * 8);
     if (m->weight == SM_WEIGHT_IMAGE && m->n_x > 0) {
         const int64_t Bi = (int64_t)(512u << 20) / (m->n_x * 4);
         if (Bi < B) B = Bi;
@@ -493,6 +493,62 @@ sm_status sm_texel_res_from_gamma(sm_mesh *m, const sm_intrinsics *d_K, const do
     if (d_area_out && F > 0)
         LF_CUDA(cudaMemcpyAsync(d_area_out, m->area, (size_t)F * sizeof(int32_t), cudaMemcpyDeviceToDevice, s),
                 "copy areas");
+    return SM_OK;
+}
+
+sm_status sm_autotune_batch(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
+                            const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N, int32_t H, int32_t W,
+                            int32_t *best_out, void *stream)
+{
+    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
+    sm_status st = check_image(N, H, W);
+    if (st != SM_OK) return st;
+    if (N < 4) return fail(SM_ERR_INVALID_ARG, "the autotuner needs at least 4 frames (got %d)", N);
+    DeviceGuard g(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t npix = (int64_t)H * W;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    LF_CUDA(cudaEventCreate(&e0), "events");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(SM_ERR_CUDA, "events");
+    }
+    int best = 0;
+    float best_ms = 0.0f;
+    const int saved_B = m->tuned_B;
+    const int64_t saved_npix = m->tuned_npix;
+    // candidates: multiples of 4 frames whose two z-buffer slots stay within 512 MB
+    for (int B = 4; B <= 64 && B <= N && (int64_t)B * npix * 16 <= (512ll << 20); B += 4) {
+        m->tuned_B = B;
+        m->tuned_npix = npix;
+        const int n = (N / B) * B;  // whole launches only
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2 && st == SM_OK; ++rep) {  // the first pass grows the scratch
+            if ((st = sm_reset(m, stream)) != SM_OK) break;
+            if (cudaEventRecord(e0, s) != cudaSuccess) st = fail(SM_ERR_CUDA, "event");
+            if (st == SM_OK) st = sm_fuse_frames(m, d_probs, dtype, d_scale, d_K, d_cam_to_world, n, H, W, nullptr, stream);
+            if (st == SM_OK && cudaEventRecord(e1, s) != cudaSuccess) st = fail(SM_ERR_CUDA, "event");
+            if (st == SM_OK && cudaEventSynchronize(e1) != cudaSuccess) st = fail(SM_ERR_CUDA, "synchronise");
+            if (st == SM_OK) cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (st != SM_OK) break;
+        const float per_frame = ms / (float)n;
+        if (best == 0 || per_frame < best_ms) {
+            best = B;
+            best_ms = per_frame;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == SM_OK) st = sm_reset(m, stream);
+    if (st != SM_OK || best == 0) {
+        m->tuned_B = saved_B;
+        m->tuned_npix = saved_npix;
+        return st != SM_OK ? st : fail(SM_ERR_INTERNAL, "autotuner found no candidate");
+    }
+    m->tuned_B = best;
+    m->tuned_npix = npix;
+    if (best_out) *best_out = best;
     return SM_OK;
 }
 

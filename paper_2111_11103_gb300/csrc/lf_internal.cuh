@@ -111,6 +111,8 @@ struct sm_mesh {
     sm_rule rule = SM_RULE_SUM;
     sm_weight weight = SM_WEIGHT_PIXEL;
     float alpha = 1.0f;  // image-weight mix (sm_set_weight_mix)
+    int tuned_B = 0;          // frames per launch chosen by sm_autotune_batch ...
+    int64_t tuned_npix = 0;   // ... for frames of this many pixels
     bool texel_mode = false;
     bool normalised = false;
 

@@ -24,7 +24,8 @@ SM_MAX_CLASSES = 254
 SYMBOLS = ["sm_mesh_upload", "sm_fuse_frames", "sm_normalise", "sm_render_labels", "sm_render_idmap", "sm_reset",
            "sm_read_state", "sm_load_state", "sm_check", "sm_num_rows", "sm_num_classes", "sm_mesh_free",
            "sm_status_string", "sm_last_error", "sm_profile_enable", "sm_profile_read", "sm_render_rows_noalloc",
-           "sm_fuse_render_host", "sm_host_alloc", "sm_host_free", "sm_set_weight_mix", "sm_texel_res_from_gamma"]
+           "sm_fuse_render_host", "sm_host_alloc", "sm_host_free", "sm_set_weight_mix", "sm_texel_res_from_gamma",
+           "sm_autotune_batch"]
 SM_NOALLOC_MAX_PIXELS = 1572864
 SM_NOALLOC_MAX_FRAMES = 1024
 
@@ -65,6 +66,7 @@ def lib() -> ctypes.CDLL:
             "sm_host_free": [P],
             "sm_set_weight_mix": [P, ctypes.c_float],
             "sm_texel_res_from_gamma": [P, P, P, i32, i32, i32, ctypes.c_float, P, P, P],
+            "sm_autotune_batch": [P, P, i32, P, P, P, i32, i32, i32, ctypes.POINTER(i32), P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -154,6 +156,14 @@ def sm_texel_res_from_gamma(mesh: int, K, cam_to_world, N: int, H: int, W: int, 
                             area_out=None, stream=None):
     _check(lib().sm_texel_res_from_gamma(mesh, _ptr(K), _ptr(cam_to_world), int(N), int(H), int(W), float(gamma),
                                          _ptr(area_out), _ptr(texel_res_out), _stream(stream)))
+
+
+def sm_autotune_batch(mesh: int, probs, dtype, scale, K, cam_to_world, N: int, H: int, W: int, stream=None) -> int:
+    """Chooses the frames per launch for H x W frames by timing; returns it."""
+    best = ctypes.c_int32(0)
+    _check(lib().sm_autotune_batch(mesh, _ptr(probs), _enum(SM_DTYPE, dtype), _ptr(scale), _ptr(K),
+                                   _ptr(cam_to_world), int(N), int(H), int(W), ctypes.byref(best), _stream(stream)))
+    return best.value
 
 
 def sm_host_alloc(nbytes: int) -> int:

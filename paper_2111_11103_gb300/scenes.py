@@ -1,0 +1,55 @@
+"""Many independent scenes at once: each scene's fusion (its own mesh,
+accumulators and frames) is enqueued on one of a few CUDA streams, so small
+scenes that cannot fill the GPU alone run side by side.  Host-side
+orchestration of the C ABI only; every step runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import torch
+
+
+@dataclasses.dataclass
+class SceneJob:
+    mesh: int                    # handle from sm_mesh_upload
+    probs: torch.Tensor          # N x H x W x c on the device
+    K: torch.Tensor              # N x 4 intrinsics (float64)
+    cam_to_world: torch.Tensor   # N x 16 poses (float64)
+    H: int
+    W: int
+    dtype: str = "f32"
+    scale: torch.Tensor | None = None
+    idmap_out: torch.Tensor | None = None
+    dist_out: torch.Tensor | None = None
+    labels_out: torch.Tensor | None = None
+
+
+def fuse_scenes(jobs: list[SceneJob], streams: int = 4) -> None:
+    """Fuses (and, where an output is given, normalises) every scene; scene i
+    runs on stream i % streams.  The streams start after the work already on
+    the current stream and the current stream waits for all of them, so the
+    call orders like one sequence of calls on the current stream.  A mesh must
+    appear in one job only."""
+    from . import labelfuse as lf
+    if len({j.mesh for j in jobs}) != len(jobs):
+        raise ValueError("a mesh may appear in one job only")
+    if not jobs:
+        return
+    cur = torch.cuda.current_stream()
+    pool = [torch.cuda.Stream() for _ in range(max(1, min(streams, len(jobs))))]
+    for st in pool:
+        st.wait_stream(cur)
+    for i, j in enumerate(jobs):
+        st = pool[i % len(pool)]
+        n = int(j.K.shape[0])
+        lf.sm_fuse_frames(j.mesh, j.probs, j.dtype, j.scale, j.K, j.cam_to_world, n, j.H, j.W, j.idmap_out, st)
+        if j.dist_out is not None or j.labels_out is not None:
+            lf.sm_normalise(j.mesh, j.dist_out, j.labels_out, st)
+    for st in pool:
+        cur.wait_stream(st)
+    for j in jobs:  # the caller's tensors were used on the pool's streams
+        for t in (j.probs, j.K, j.cam_to_world, j.scale, j.idmap_out, j.dist_out, j.labels_out):
+            if t is not None:
+                for st in pool:
+                    t.record_stream(st)
