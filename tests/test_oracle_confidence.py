@@ -1,0 +1,82 @@
+"""Pins for the confidence oracle: gradients against central finite
+differences, closed-form forward passes, bfloat16 rounding against torch's
+own conversion, and features with closed forms (a fronto-parallel wall,
+uniform / one-hot predictions, hand-worked border distances)."""
+import numpy as np
+import torch
+
+from oracle import confidence as cf
+
+
+def _random_params(rng, scale=0.4):
+    return cf.bf16_round(rng.normal(0, scale, cf.N_PARAMS).astype(np.float32))
+
+
+def test_gradient_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    params = _random_params(rng)
+    X = rng.uniform(0, 1, (64, cf.N_FEAT))
+    y = (rng.uniform(size=64) < 0.6).astype(np.float64)
+    _, g = cf.loss_and_grad(params, X, y, rounding=False)
+    eps = 1e-6
+    idx = rng.choice(cf.N_PARAMS, 120, replace=False)
+    for i in idx:
+        d = np.zeros(cf.N_PARAMS)
+        d[i] = eps
+        lp, _ = cf.loss_and_grad(params + d, X, y, rounding=False)
+        lm, _ = cf.loss_and_grad(params - d, X, y, rounding=False)
+        fd = (lp - lm) / (2 * eps)
+        assert abs(fd - g[i]) <= 1e-7 + 1e-5 * abs(fd), (i, fd, g[i])
+
+
+def test_forward_closed_forms():
+    p = np.zeros(cf.N_PARAMS)
+    p[-1] = 0.75  # b3
+    _, w, _ = cf.forward(p, np.ones((3, cf.N_FEAT)))
+    assert np.allclose(w, 1 / (1 + np.exp(-0.75)), rtol=0, atol=1e-15)
+    # one path through: o = relu(relu(x0)) -> w = sigmoid(x0) for x0 >= 0, 0.5 for x0 < 0
+    W1, b1, W2, b2, w3, b3 = cf.unpack(np.zeros(cf.N_PARAMS))
+    q = np.zeros(cf.N_PARAMS)
+    q[0] = 1.0                                   # W1[0, 0]
+    q[cf.HID * cf.N_FEAT + cf.HID] = 1.0         # W2[0, 0]
+    q[cf.N_PARAMS - 1 - cf.HID] = 1.0            # w3[0]
+    X = np.array([[0.5, 9, 9, 9, 9], [-2.0, 1, 1, 1, 1]])
+    o, w, _ = cf.forward(q, X)
+    assert np.array_equal(o, [0.5, 0.0])
+
+
+def test_bf16_rounding_matches_torch():
+    rng = np.random.default_rng(1)
+    x = (rng.normal(0, 1, 20000) * np.exp(rng.uniform(-20, 20, 20000))).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(cf.bf16_round(x), ref)
+
+
+def test_features_fronto_parallel_wall(ora):
+    """Wall at z = 2 facing the camera (identity pose): depth feature 2/4,
+    |cos| = 1 / |((x-cx)/fx, (y-cy)/fy, 1)|, border distance by hand."""
+    V = np.array([[-1, -0.75, 2], [1, -0.75, 2], [1, 0.75, 2], [-1, 0.75, 2]], dtype=np.float64)
+    F = np.array([[0, 1, 2], [0, 2, 3]])
+    K = np.array([10.0, 10.0, 8.25, 6.25])
+    H, W, c = 14, 18, 4
+    probs = np.full((H, W, c), 0.25, dtype=np.float32)   # uniform: entropy 1, margin 0
+    probs[3, 4] = [1, 0, 0, 0]                           # one-hot: entropy 0, margin 1
+    X, face = cf.features(ora, V, F, K, np.eye(4), probs, H, W)
+    X = X.reshape(H, W, 5)
+    cov = face.reshape(H, W) >= 0
+    assert np.all(X[cov, 1] == 0.5)
+    ys, xs = np.mgrid[0:H, 0:W]
+    cos = 1 / np.sqrt(((xs - 8.25) / 10) ** 2 + ((ys - 6.25) / 10) ** 2 + 1)
+    np.testing.assert_allclose(X[cov, 0], cos[cov], rtol=1e-14)
+    assert X[3, 4, 2] == 0.0 and X[3, 4, 3] == 1.0
+    np.testing.assert_allclose(X[5, 5, 2], 1.0, rtol=1e-12)
+    assert X[5, 5, 3] == 0.0
+    assert X[3, 4, 4] == 3 / 7 and X[9, 13, 4] == 4 / 7  # min(4,3,13,10) = 3; min(13,9,4,4) = 4; / (14/2)
+    assert np.all(X[~cov] == 0)
+
+
+def test_targets_by_hand():
+    probs = np.array([[0.1, 0.7, 0.2], [0.5, 0.5, 0.0], [0.2, 0.3, 0.5], [0.6, 0.3, 0.1]])
+    rows = np.array([0, 1, 1, -1])
+    labels = np.array([1, 0])
+    assert list(cf.targets(probs, rows, labels)) == [1.0, 1.0, 0.0, 0.0]
