@@ -228,6 +228,54 @@ sm_status sm_autotune_batch(sm_mesh *m, const void *d_probs, sm_dtype dtype, con
                             const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N, int32_t H, int32_t W,
                             int32_t *best_out, void *stream);
 
+/* Fusion with explicit per-pixel weights: as sm_fuse_frames, but pixel k of
+ * the N frames weighs d_weights[k] (N x H x W float32, device) in the
+ * weighted rules (Sec. 3.2.2, Eqs. w-sum / w-mul / w-maxsum), replacing the
+ * mesh's own weight (w^(P) or w^(I)).  Used with the learned confidence below.
+ * Errors: as sm_fuse_frames, SM_ERR_INVALID_ARG for NULL weights. */
+sm_status sm_fuse_frames_weighted(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
+                                  const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N, int32_t H,
+                                  int32_t W, const float *d_weights, int32_t *d_idmap_out, void *stream);
+
+/* Learned per-observation confidence: the weight of an observation predicted
+ * by a small network (an extension of the weights of Sec. 3.2.2; the paper's
+ * weights are fixed).
+ *
+ * Features (SM_CONF_FEATURES per pixel, float32): |cos| between the visible
+ * triangle's normal and the pixel's viewing ray; depth of the visible surface
+ * (1 / interpolated 1/z) / 4 m; prediction entropy -sum p ln max(p, 2^-30) /
+ * ln c; top-2 margin p(1) - p(2); distance to the nearest image border /
+ * (min(H, W) / 2).  Background pixels get zeros.
+ * Network: 5 -> 32 -> 32 -> 1, ReLU, w = sigmoid(o); SM_CONF_PARAMS float32
+ * parameters in the order W1 (32 x 5, row = output), b1, W2 (32 x 32), b2,
+ * w3 (32), b3, used rounded to bfloat16 with float32 accumulation.
+ * Training: mean binary cross-entropy against targets y in {0, 1}. */
+#define SM_CONF_FEATURES 5
+#define SM_CONF_PARAMS 1281
+
+/* Renders the N frames and writes every pixel's features (d_feat_out,
+ * N x H x W x SM_CONF_FEATURES) and row (d_rows_out, N x H x W, -1 for
+ * background).  Leaves the accumulators untouched. */
+sm_status sm_conf_features(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
+                           const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N, int32_t H, int32_t W,
+                           float *d_feat_out, int32_t *d_rows_out, void *stream);
+
+/* Training targets: d_target_out[k] = 1 where pixel k's first arg max equals
+ * the fused label of its row d_rows[k], else 0 (background, unseen rows).
+ * Requires an earlier sm_normalise (else SM_ERR_STATE). */
+sm_status sm_conf_targets(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
+                          const int32_t *d_rows, int64_t n_pixels, float *d_target_out, void *stream);
+
+/* Inference: d_w_out[i] = sigmoid(MLP(d_feat[i])) for n observations. */
+sm_status sm_conf_forward(const float *d_params, const float *d_feat, int64_t n, float *d_w_out, void *stream);
+
+/* One gradient-descent step on the mean binary cross-entropy of n
+ * observations: d_grad_out (SM_CONF_PARAMS, required) receives the gradient
+ * with respect to the bfloat16-rounded parameters, d_loss_out (1 float,
+ * required) the loss before the step, and d_params -= lr * gradient. */
+sm_status sm_conf_train_step(float *d_params, const float *d_feat, const float *d_target, int64_t n, float lr,
+                             float *d_grad_out, float *d_loss_out, void *stream);
+
 /* Page-locked host memory for the host buffers of sm_fuse_render_host (the
  * paper has no counterpart: this is plumbing of the host path).  Memory from
  * here is copied to the device at the host link's full rate in one piece,

@@ -188,6 +188,83 @@ sm_status prepare_frames(sm_mesh *m, const sm_intrinsics *d_K, const double *d_T
     return SM_OK;
 }
 
+// Fusion of N frames (sm_fuse_frames; d_weights: explicit per-pixel weights, or null).
+sm_status fuse_impl(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale, const sm_intrinsics *d_K,
+                    const double *d_cam_to_world, int32_t N, int32_t H, int32_t W, const float *d_weights,
+                    int32_t *d_idmap_out, void *stream)
+{
+    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
+    sm_status st = check_image(N, H, W);
+    if (st != SM_OK) return st;
+    if ((int)dtype < 0 || (int)dtype > 2) return fail(SM_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
+    if (dtype == SM_F32 && d_scale) return fail(SM_ERR_INVALID_ARG, "F32 probabilities take no scale");
+    if (dtype != SM_F32 && !d_scale && N > 0) return fail(SM_ERR_INVALID_ARG, "BF16/FP8 need a per-pixel scale");
+    if (N == 0) return SM_OK;
+    if (!d_probs || !d_K || !d_cam_to_world) return fail(SM_ERR_INVALID_ARG, "NULL input pointer");
+    if (((uintptr_t)d_probs & 15) != 0) return fail(SM_ERR_INVALID_ARG, "probabilities not 16-byte aligned");
+    DeviceGuard g(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t npix = (int64_t)H * W;
+    const int B = batch_frames(m, npix, N);
+    const bool image_w = m->weight == SM_WEIGHT_IMAGE && !d_weights;  // explicit weights replace w^(I)
+    const bool tma = lf::scatter_tma_supported(m->c);
+    // face mode with the pipelined scatter: the scatter reads the z-buffer
+    // keys itself; otherwise a resolve pass writes the row map first
+    const bool from_keys = tma && !m->texel_mode;
+    const bool need_ids = !from_keys || image_w;
+    // the pipelined scatter reads its row map from the library's aligned buffer
+    const bool ids_internal = need_ids && (!d_idmap_out || (tma && !from_keys));
+    if ((st = prepare_frames(m, d_K, d_cam_to_world, N, npix, B, ids_internal, s)) != SM_OK) return st;
+    if (image_w && (st = grow(&m->fcnt, &m->fcnt_cap, (int64_t)B * m->n_x, s, 0, "row histograms")) != SM_OK)
+        return st;
+    const size_t esz = dtype_size(dtype);
+    cudaStream_t r = m->rstream;
+    LF_CUDA(cudaEventRecord(m->ev_start, s), "event");
+    LF_CUDA(cudaStreamWaitEvent(r, m->ev_start, 0), "event");
+    for (int b = 0, f0 = 0; f0 < N; ++b, f0 += B) {
+        const int nb = (N - f0 < B) ? N - f0 : B;
+        const int slot = b & 1;
+        unsigned long long *keys = m->keys + (int64_t)slot * slot_stride(B, npix);
+        int32_t *user_idm = d_idmap_out ? d_idmap_out + (int64_t)f0 * npix : nullptr;
+        int32_t *idm = ids_internal ? m->idbuf : user_idm;
+        // raster of this batch on the raster stream, once the scatter that
+        // last used this z-buffer slot has re-armed it
+        if (b >= 2) LF_CUDA(cudaStreamWaitEvent(r, m->ev_scat[slot], 0), "event");
+        if ((st = raster_only(m, f0, nb, H, W, keys, r)) != SM_OK) return st;
+        LF_CUDA(cudaEventRecord(m->ev_rast[slot], r), "event");
+        LF_CUDA(cudaStreamWaitEvent(s, m->ev_rast[slot], 0), "event");
+        if (!from_keys &&
+            (st = resolve_only(m, f0, nb, H, W, keys, idm, s, idm != user_idm ? user_idm : nullptr)) != SM_OK)
+            return st;
+        if (image_w) {
+            ProfScope p(m, SM_K_COUNT, s);
+            lf::launch_count(from_keys ? nullptr : idm, keys, npix, nb, m->fcnt, m->n_x, s);
+        }
+        {
+            ProfScope p(m, SM_K_SCATTER, s);
+            const char *probs = static_cast<const char *>(d_probs) + (size_t)f0 * npix * m->c * esz;
+            const float *scale = d_scale ? d_scale + (size_t)f0 * npix : nullptr;
+            const uint32_t *fcnt = image_w ? m->fcnt : nullptr;
+            const float *wpix = d_weights ? d_weights + (size_t)f0 * npix : nullptr;
+            if (tma)
+                lf::launch_scatter_tma(m->rule, dtype, probs, scale, from_keys ? keys : nullptr,
+                                       from_keys ? nullptr : idm, from_keys ? idm : nullptr, npix * nb, npix, m->c,
+                                       fcnt, m->alpha, wpix, m->n_x, m->acc, m->cnt, m->err, s);
+            else
+                lf::launch_scatter(m->rule, dtype, probs, scale, idm, npix, nb, m->c, fcnt, m->alpha, wpix, m->n_x,
+                                   m->acc, m->cnt, m->err, s);
+        }
+        LF_LAUNCHED("scatter");
+        if (image_w) {
+            ProfScope p(m, SM_K_COUNT, s);
+            lf::launch_count_reset(idm, npix, nb, m->fcnt, m->n_x, s);
+        }
+        LF_LAUNCHED("histogram reset");
+        LF_CUDA(cudaEventRecord(m->ev_scat[slot], s), "event");
+    }
+    m->normalised = false;
+    return SM_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -320,76 +397,15 @@ sm_status sm_fuse_frames(sm_mesh *m, const void *d_probs, sm_dtype dtype, const 
                          const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N, int32_t H, int32_t W,
                          int32_t *d_idmap_out, void *stream)
 {
-    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
-    sm_status st = check_image(N, H, W);
-    if (st != SM_OK) return st;
-    if ((int)dtype < 0 || (int)dtype > 2) return fail(SM_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
-    if (dtype == SM_F32 && d_scale) return fail(SM_ERR_INVALID_ARG, "F32 probabilities take no scale");
-    if (dtype != SM_F32 && !d_scale && N > 0) return fail(SM_ERR_INVALID_ARG, "BF16/FP8 need a per-pixel scale");
-    if (N == 0) return SM_OK;
-    if (!d_probs || !d_K || !d_cam_to_world) return fail(SM_ERR_INVALID_ARG, "NULL input pointer");
-    if (((uintptr_t)d_probs & 15) != 0) return fail(SM_ERR_INVALID_ARG, "probabilities not 16-byte aligned");
-    DeviceGuard g(m->device);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int64_t npix = (int64_t)H * W;
-    const int B = batch_frames(m, npix, N);
-    const bool image_w = m->weight == SM_WEIGHT_IMAGE;
-    const bool tma = lf::scatter_tma_supported(m->c);
-    // face mode with the pipelined scatter: the scatter reads the z-buffer
-    // keys itself; otherwise a resolve pass writes the row map first
-    const bool from_keys = tma && !m->texel_mode;
-    const bool need_ids = !from_keys || image_w;
-    // the pipelined scatter reads its row map from the library's aligned buffer
-    const bool ids_internal = need_ids && (!d_idmap_out || (tma && !from_keys));
-    if ((st = prepare_frames(m, d_K, d_cam_to_world, N, npix, B, ids_internal, s)) != SM_OK) return st;
-    if (image_w && (st = grow(&m->fcnt, &m->fcnt_cap, (int64_t)B * m->n_x, s, 0, "row histograms")) != SM_OK)
-        return st;
-    const size_t esz = dtype_size(dtype);
-    cudaStream_t r = m->rstream;
-    LF_CUDA(cudaEventRecord(m->ev_start, s), "event");
-    LF_CUDA(cudaStreamWaitEvent(r, m->ev_start, 0), "event");
-    for (int b = 0, f0 = 0; f0 < N; ++b, f0 += B) {
-        const int nb = (N - f0 < B) ? N - f0 : B;
-        const int slot = b & 1;
-        unsigned long long *keys = m->keys + (int64_t)slot * slot_stride(B, npix);
-        int32_t *user_idm = d_idmap_out ? d_idmap_out + (int64_t)f0 * npix : nullptr;
-        int32_t *idm = ids_internal ? m->idbuf : user_idm;
-        // raster of this batch on the raster stream, once the scatter that
-        // last used this z-buffer slot has re-armed it
-        if (b >= 2) LF_CUDA(cudaStreamWaitEvent(r, m->ev_scat[slot], 0), "event");
-        if ((st = raster_only(m, f0, nb, H, W, keys, r)) != SM_OK) return st;
-        LF_CUDA(cudaEventRecord(m->ev_rast[slot], r), "event");
-        LF_CUDA(cudaStreamWaitEvent(s, m->ev_rast[slot], 0), "event");
-        if (!from_keys &&
-            (st = resolve_only(m, f0, nb, H, W, keys, idm, s, idm != user_idm ? user_idm : nullptr)) != SM_OK)
-            return st;
-        if (image_w) {
-            ProfScope p(m, SM_K_COUNT, s);
-            lf::launch_count(from_keys ? nullptr : idm, keys, npix, nb, m->fcnt, m->n_x, s);
-        }
-        {
-            ProfScope p(m, SM_K_SCATTER, s);
-            const char *probs = static_cast<const char *>(d_probs) + (size_t)f0 * npix * m->c * esz;
-            const float *scale = d_scale ? d_scale + (size_t)f0 * npix : nullptr;
-            const uint32_t *fcnt = image_w ? m->fcnt : nullptr;
-            if (tma)
-                lf::launch_scatter_tma(m->rule, dtype, probs, scale, from_keys ? keys : nullptr,
-                                       from_keys ? nullptr : idm, from_keys ? idm : nullptr, npix * nb, npix, m->c,
-                                       fcnt, m->alpha, m->n_x, m->acc, m->cnt, m->err, s);
-            else
-                lf::launch_scatter(m->rule, dtype, probs, scale, idm, npix, nb, m->c, fcnt, m->alpha, m->n_x, m->acc,
-                                   m->cnt, m->err, s);
-        }
-        LF_LAUNCHED("scatter");
-        if (image_w) {
-            ProfScope p(m, SM_K_COUNT, s);
-            lf::launch_count_reset(idm, npix, nb, m->fcnt, m->n_x, s);
-        }
-        LF_LAUNCHED("histogram reset");
-        LF_CUDA(cudaEventRecord(m->ev_scat[slot], s), "event");
-    }
-    m->normalised = false;
-    return SM_OK;
+    return fuse_impl(m, d_probs, dtype, d_scale, d_K, d_cam_to_world, N, H, W, nullptr, d_idmap_out, stream);
+}
+
+sm_status sm_fuse_frames_weighted(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
+                                  const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N, int32_t H,
+                                  int32_t W, const float *d_weights, int32_t *d_idmap_out, void *stream)
+{
+    if (N > 0 && !d_weights) return fail(SM_ERR_INVALID_ARG, "weights are NULL");
+    return fuse_impl(m, d_probs, dtype, d_scale, d_K, d_cam_to_world, N, H, W, d_weights, d_idmap_out, stream);
 }
 
 sm_status sm_normalise(sm_mesh *m, float *d_dist, int32_t *d_labels, void *stream)
@@ -549,6 +565,80 @@ sm_status sm_autotune_batch(sm_mesh *m, const void *d_probs, sm_dtype dtype, con
     m->tuned_B = best;
     m->tuned_npix = npix;
     if (best_out) *best_out = best;
+    return SM_OK;
+}
+
+sm_status sm_conf_features(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
+                           const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N, int32_t H, int32_t W,
+                           float *d_feat_out, int32_t *d_rows_out, void *stream)
+{
+    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
+    sm_status st = check_image(N, H, W);
+    if (st != SM_OK) return st;
+    if ((int)dtype < 0 || (int)dtype > 2) return fail(SM_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
+    if ((dtype == SM_F32) != (d_scale == nullptr) && N > 0) return fail(SM_ERR_INVALID_ARG, "scale given iff BF16/FP8");
+    if (N == 0) return SM_OK;
+    if (!d_probs || !d_K || !d_cam_to_world || !d_feat_out || !d_rows_out)
+        return fail(SM_ERR_INVALID_ARG, "NULL pointer");
+    DeviceGuard g(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t npix = (int64_t)H * W;
+    const int B = batch_frames(m, npix, N);
+    if ((st = prepare_frames(m, d_K, d_cam_to_world, N, npix, B, false, s)) != SM_OK) return st;
+    const size_t esz = dtype_size(dtype);
+    for (int f0 = 0; f0 < N; f0 += B) {
+        const int nb = (N - f0 < B) ? N - f0 : B;
+        if ((st = raster_only(m, f0, nb, H, W, m->keys, s)) != SM_OK) return st;
+        lf::launch_conf_features(m->keys, npix * nb, H, W, m->verts, m->faces, m->F, d_K + f0,
+                                 d_cam_to_world + 16 * (int64_t)f0,
+                                 static_cast<const char *>(d_probs) + (size_t)f0 * npix * m->c * esz, dtype,
+                                 d_scale ? d_scale + (size_t)f0 * npix : nullptr, m->c,
+                                 d_feat_out + (size_t)f0 * npix * SM_CONF_FEATURES, s);
+        LF_LAUNCHED("confidence features");
+        // row map of the batch (re-arms the z-buffer)
+        if ((st = resolve_only(m, f0, nb, H, W, m->keys, d_rows_out + (int64_t)f0 * npix, s, nullptr)) != SM_OK)
+            return st;
+    }
+    return SM_OK;
+}
+
+sm_status sm_conf_targets(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
+                          const int32_t *d_rows, int64_t n_pixels, float *d_target_out, void *stream)
+{
+    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
+    if (!m->normalised) return fail(SM_ERR_STATE, "sm_conf_targets before sm_normalise");
+    if (n_pixels < 0) return fail(SM_ERR_INVALID_ARG, "n_pixels < 0");
+    if ((int)dtype < 0 || (int)dtype > 2) return fail(SM_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
+    if (n_pixels == 0) return SM_OK;
+    if (!d_probs || !d_rows || !d_target_out || ((dtype != SM_F32) && !d_scale))
+        return fail(SM_ERR_INVALID_ARG, "NULL pointer");
+    DeviceGuard g(m->device);
+    lf::launch_conf_targets(d_probs, dtype, d_scale, m->c, d_rows, n_pixels, m->labels8, m->n_x, d_target_out,
+                            static_cast<cudaStream_t>(stream));
+    LF_LAUNCHED("confidence targets");
+    return SM_OK;
+}
+
+sm_status sm_conf_forward(const float *d_params, const float *d_feat, int64_t n, float *d_w_out, void *stream)
+{
+    if (n < 0) return fail(SM_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return SM_OK;
+    if (!d_params || !d_feat || !d_w_out) return fail(SM_ERR_INVALID_ARG, "NULL pointer");
+    lf::launch_conf_forward(d_params, d_feat, n, d_w_out, static_cast<cudaStream_t>(stream));
+    LF_LAUNCHED("confidence forward");
+    return SM_OK;
+}
+
+sm_status sm_conf_train_step(float *d_params, const float *d_feat, const float *d_target, int64_t n, float lr,
+                             float *d_grad_out, float *d_loss_out, void *stream)
+{
+    if (n < 0) return fail(SM_ERR_INVALID_ARG, "n < 0");
+    if (!(lr >= 0.0f && lr < 1.0e6f)) return fail(SM_ERR_INVALID_ARG, "learning rate %g", (double)lr);
+    if (!d_params || !d_grad_out || !d_loss_out || (n > 0 && (!d_feat || !d_target)))
+        return fail(SM_ERR_INVALID_ARG, "NULL pointer");
+    lf::launch_conf_train_step(d_params, d_feat, d_target, n, lr, d_grad_out, d_loss_out,
+                               static_cast<cudaStream_t>(stream));
+    LF_LAUNCHED("confidence training step");
     return SM_OK;
 }
 

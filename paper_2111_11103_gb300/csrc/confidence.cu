@@ -1,0 +1,275 @@
+// Learned per-observation confidence: an extension of the weighted fusion
+// rules (Sec. 3.2.2, Eqs. w-sum / w-mul / w-maxsum), where the weight of an
+// observation comes from a small network instead of being 1 or
+// 1/|K_i ∩ K_x|.
+//
+//  * k_conf_features: per pixel of a rasterised batch, five features -- |cos|
+//    between the visible triangle's normal and the pixel's viewing ray, depth
+//    (1 / interpolated 1/z, / 4 m), prediction entropy (/ ln c), top-2
+//    margin, distance to the image border (/ half the smaller side).
+//  * k_conf_forward: 5 -> 32 -> 32 -> 1 MLP, ReLU, sigmoid output, the
+//    parameters rounded to bfloat16, float32 accumulation.
+//  * k_conf_grad + k_conf_update: one step of gradient descent on the mean
+//    binary cross-entropy; each block reduces its observations' gradients in
+//    shared memory before one atomic add per parameter.
+//  * k_conf_targets: 1 where a pixel's arg max equals its row's fused label.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "lf_internal.cuh"
+
+namespace lf {
+namespace {
+
+constexpr int kF = SM_CONF_FEATURES;  // 5
+constexpr int kH = 32;                 // hidden width
+// parameter offsets: W1 (kH x kF, row = output), b1, W2 (kH x kH), b2, w3, b3
+constexpr int kW1 = 0, kB1 = kW1 + kH * kF, kW2 = kB1 + kH, kB2 = kW2 + kH * kH, kW3 = kB2 + kH, kB3 = kW3 + kH;
+static_assert(kB3 + 1 == SM_CONF_PARAMS, "parameter layout");
+constexpr float kPMin = 9.313225746154785e-10f;  // 2^-30
+
+__device__ __forceinline__ float load_p(const void *probs, sm_dtype dt, int64_t i, float sc)
+{
+    if (dt == SM_F32) return static_cast<const float *>(probs)[i];
+    if (dt == SM_BF16) {
+        const unsigned short u = static_cast<const unsigned short *>(probs)[i];
+        return __fmul_rn(__uint_as_float((unsigned)u << 16), sc);
+    }
+    __half_raw h = __nv_cvt_fp8_to_halfraw(static_cast<const __nv_fp8_storage_t *>(probs)[i], __NV_E4M3);
+    return __fmul_rn(__half2float(*reinterpret_cast<__half *>(&h)), sc);
+}
+
+__global__ void __launch_bounds__(256)
+    k_conf_features(const unsigned long long *__restrict__ keys, int64_t total, int H, int W,
+                    const float4 *__restrict__ V, const int4 *__restrict__ faces, int64_t F,
+                    const sm_intrinsics *__restrict__ K, const double *__restrict__ T, const void *__restrict__ probs,
+                    sm_dtype dt, const float *__restrict__ scale, int c, float *__restrict__ feat)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= total) return;
+    const int64_t npix = (int64_t)H * W;
+    const int b = (int)(p / npix);
+    const int64_t q = p - (int64_t)b * npix;
+    const int y = (int)(q / W), x = (int)(q - (int64_t)y * W);
+    float *out = feat + p * kF;
+    const unsigned long long key = keys[p];
+    const int64_t f = (int64_t)(unsigned int)key;
+    if (key == kEmptyKey || f >= F) {
+        for (int k = 0; k < kF; ++k) out[k] = 0.0f;
+        return;
+    }
+    // viewing ray in world coordinates: R_cw ((x - cx) / fx, (y - cy) / fy, 1)
+    const sm_intrinsics Kb = K[b];
+    const double *Tb = T + 16 * (int64_t)b;
+    const float dx = ((float)x - (float)Kb.cx) / (float)Kb.fx, dy = ((float)y - (float)Kb.cy) / (float)Kb.fy;
+    float ray[3];
+    for (int r = 0; r < 3; ++r) ray[r] = (float)Tb[4 * r] * dx + (float)Tb[4 * r + 1] * dy + (float)Tb[4 * r + 2];
+    const int4 fc = faces[f];
+    const float4 a = V[fc.x], bb = V[fc.y], cc = V[fc.z];
+    const float e1[3] = {bb.x - a.x, bb.y - a.y, bb.z - a.z}, e2[3] = {cc.x - a.x, cc.y - a.y, cc.z - a.z};
+    const float n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    const float dot = n[0] * ray[0] + n[1] * ray[1] + n[2] * ray[2];
+    const float nn = sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    const float rr = sqrtf(ray[0] * ray[0] + ray[1] * ray[1] + ray[2] * ray[2]);
+    out[0] = nn > 0.0f ? fabsf(dot) / (nn * rr) : 0.0f;
+    const float inv_z = __uint_as_float(0xFFFFFFFFu - (unsigned int)(key >> 32));
+    out[1] = inv_z > 0.0f ? 0.25f / inv_z : 0.0f;
+    // entropy and top-2 margin of the prediction
+    const float sc = (dt == SM_F32) ? 1.0f : scale[p];
+    float ent = 0.0f, m1 = -INFINITY, m2 = -INFINITY;
+    for (int j = 0; j < c; ++j) {
+        const float v = load_p(probs, dt, p * c + j, sc);
+        ent -= v * logf(fmaxf(v, kPMin));
+        if (v > m1) {
+            m2 = m1;
+            m1 = v;
+        } else if (v > m2) {
+            m2 = v;
+        }
+    }
+    out[2] = c > 1 ? ent / logf((float)c) : 0.0f;
+    out[3] = c > 1 ? m1 - m2 : m1;
+    const int d = min(min(x, y), min(W - 1 - x, H - 1 - y));
+    out[4] = (float)d / (0.5f * (float)min(W, H));
+}
+
+// Parameters rounded to bfloat16, in shared memory.
+__device__ __forceinline__ void load_params(const float *__restrict__ params, float *s)
+{
+    for (int i = threadIdx.x; i < SM_CONF_PARAMS; i += blockDim.x)
+        s[i] = __bfloat162float(__float2bfloat16_rn(params[i]));
+    __syncthreads();
+}
+
+// Forward pass of one observation; z1, z2: pre-activations.
+__device__ __forceinline__ float mlp_forward(const float *s, const float *x, float *z1, float *z2)
+{
+    float h1[kH];
+#pragma unroll
+    for (int i = 0; i < kH; ++i) {
+        float acc = s[kB1 + i];
+#pragma unroll
+        for (int k = 0; k < kF; ++k) acc = fmaf(s[kW1 + i * kF + k], x[k], acc);
+        z1[i] = acc;
+        h1[i] = fmaxf(acc, 0.0f);
+    }
+    float o = s[kB3];
+#pragma unroll 4
+    for (int j = 0; j < kH; ++j) {
+        float acc = s[kB2 + j];
+#pragma unroll
+        for (int i = 0; i < kH; ++i) acc = fmaf(s[kW2 + j * kH + i], h1[i], acc);
+        z2[j] = acc;
+        o = fmaf(s[kW3 + j], fmaxf(acc, 0.0f), o);
+    }
+    return o;
+}
+
+__global__ void __launch_bounds__(256)
+    k_conf_forward(const float *__restrict__ params, const float *__restrict__ feat, int64_t n, float *__restrict__ w)
+{
+    __shared__ float s[SM_CONF_PARAMS];
+    load_params(params, s);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float x[kF], z1[kH], z2[kH];
+#pragma unroll
+    for (int k = 0; k < kF; ++k) x[k] = feat[i * kF + k];
+    const float o = mlp_forward(s, x, z1, z2);
+    w[i] = 1.0f / (1.0f + expf(-o));
+}
+
+constexpr int kObs = 128;  // observations per block in the gradient kernel
+// per-observation vectors kept for the block's reduction: x, h1, d_z1, h2, d_z2, d_o
+constexpr int kRow = kF + 4 * kH + 1;
+
+__global__ void __launch_bounds__(kObs)
+    k_conf_grad(const float *__restrict__ params, const float *__restrict__ feat, const float *__restrict__ target,
+                int64_t n, float *__restrict__ grad, float *__restrict__ loss)
+{
+    extern __shared__ float sm[];
+    float *s = sm;                          // SM_CONF_PARAMS (bf16-rounded)
+    float *rows = sm + SM_CONF_PARAMS + 3;  // kObs x kRow
+    load_params(params, s);
+    const int64_t i = (int64_t)blockIdx.x * kObs + threadIdx.x;
+    float *r = rows + threadIdx.x * kRow;
+    float l = 0.0f;
+    if (i < n) {
+        float x[kF], z1[kH], z2[kH];
+#pragma unroll
+        for (int k = 0; k < kF; ++k) x[k] = feat[i * kF + k];
+        const float o = mlp_forward(s, x, z1, z2);
+        const float y = target[i];
+        l = (fmaxf(o, 0.0f) + log1pf(expf(-fabsf(o))) - y * o) / (float)n;  // softplus(o) - y o
+        const float d_o = (1.0f / (1.0f + expf(-o)) - y) / (float)n;
+        for (int k = 0; k < kF; ++k) r[k] = x[k];
+        for (int j = 0; j < kH; ++j) {
+            r[kF + 2 * kH + j] = fmaxf(z2[j], 0.0f);                          // h2
+            r[kF + 3 * kH + j] = z2[j] > 0.0f ? d_o * s[kW3 + j] : 0.0f;      // d_z2
+        }
+        for (int a = 0; a < kH; ++a) {
+            float acc = 0.0f;
+            for (int j = 0; j < kH; ++j) acc = fmaf(r[kF + 3 * kH + j], s[kW2 + j * kH + a], acc);
+            r[kF + a] = fmaxf(z1[a], 0.0f);                  // h1
+            r[kF + kH + a] = z1[a] > 0.0f ? acc : 0.0f;      // d_z1
+        }
+        r[kF + 4 * kH] = d_o;
+    } else {
+        for (int k = 0; k < kRow; ++k) r[k] = 0.0f;
+    }
+    // block sum of the loss
+    for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, l);
+    __syncthreads();
+    // each thread sums some parameters' gradients over the block's observations
+    for (int q = threadIdx.x; q < SM_CONF_PARAMS; q += blockDim.x) {
+        float g = 0.0f;
+        for (int t = 0; t < kObs; ++t) {
+            const float *rt = rows + t * kRow;
+            float v;
+            if (q < kB1) v = rt[kF + kH + q / kF] * rt[q % kF];                              // W1: d_z1 x
+            else if (q < kW2) v = rt[kF + kH + (q - kB1)];                                    // b1
+            else if (q < kB2) v = rt[kF + 3 * kH + (q - kW2) / kH] * rt[kF + (q - kW2) % kH];  // W2: d_z2 h1
+            else if (q < kW3) v = rt[kF + 3 * kH + (q - kB2)];                                // b2
+            else if (q < kB3) v = rt[kF + 4 * kH] * rt[kF + 2 * kH + (q - kW3)];              // w3: d_o h2
+            else v = rt[kF + 4 * kH];                                                          // b3
+            g += v;
+        }
+        atomicAdd(grad + q, g);
+    }
+}
+
+__global__ void k_conf_update(float *__restrict__ params, const float *__restrict__ grad, float lr)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < SM_CONF_PARAMS) params[q] -= lr * grad[q];
+}
+
+__global__ void __launch_bounds__(256)
+    k_conf_targets(const void *__restrict__ probs, sm_dtype dt, const float *__restrict__ scale, int c,
+                   const int32_t *__restrict__ rows, int64_t n, const uint8_t *__restrict__ labels8, int64_t n_x,
+                   float *__restrict__ y)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int32_t row = rows[p];
+    float t = 0.0f;
+    if (row >= 0 && row < n_x) {
+        const float sc = (dt == SM_F32) ? 1.0f : scale[p];
+        float m = -INFINITY;
+        int am = 0;
+        for (int j = 0; j < c; ++j) {
+            const float v = load_p(probs, dt, p * c + j, sc);
+            if (v > m) {
+                m = v;
+                am = j;
+            }
+        }
+        t = (labels8[row] != 255 && am == labels8[row]) ? 1.0f : 0.0f;
+    }
+    y[p] = t;
+}
+
+}  // namespace
+
+void launch_conf_features(const unsigned long long *keys, int64_t total, int H, int W, const float4 *V,
+                          const int4 *faces, int64_t F, const sm_intrinsics *K, const double *T, const void *probs,
+                          sm_dtype dt, const float *scale, int c, float *feat, cudaStream_t s)
+{
+    if (total <= 0) return;
+    k_conf_features<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(keys, total, H, W, V, faces, F, K, T, probs, dt,
+                                                                    scale, c, feat);
+}
+
+void launch_conf_forward(const float *params, const float *feat, int64_t n, float *w, cudaStream_t s)
+{
+    if (n <= 0) return;
+    k_conf_forward<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(params, feat, n, w);
+}
+
+void launch_conf_train_step(float *params, const float *feat, const float *target, int64_t n, float lr, float *grad,
+                            float *loss, cudaStream_t s)
+{
+    cudaMemsetAsync(grad, 0, SM_CONF_PARAMS * sizeof(float), s);
+    cudaMemsetAsync(loss, 0, sizeof(float), s);
+    if (n > 0) {
+        const size_t smem = (SM_CONF_PARAMS + 3 + (size_t)kObs * kRow) * sizeof(float);
+        static bool configured = false;
+        if (!configured) {
+            cudaFuncSetAttribute(k_conf_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            configured = true;
+        }
+        k_conf_grad<<<(unsigned)((n + kObs - 1) / kObs), kObs, smem, s>>>(params, feat, target, n, grad, loss);
+    }
+    k_conf_update<<<(SM_CONF_PARAMS + 255) / 256, 256, 0, s>>>(params, grad, lr);
+}
+
+void launch_conf_targets(const void *probs, sm_dtype dt, const float *scale, int c, const int32_t *rows, int64_t n,
+                         const uint8_t *labels8, int64_t n_x, float *y, cudaStream_t s)
+{
+    if (n <= 0) return;
+    k_conf_targets<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(probs, dt, scale, c, rows, n, labels8, n_x, y);
+}
+
+}  // namespace lf

@@ -117,7 +117,8 @@ __global__ void k_texel_res(const int32_t *__restrict__ area, int64_t F, float g
 template <int RULE, int DT>
 __global__ void __launch_bounds__(256)
     k_scatter(const void *__restrict__ probs, const float *__restrict__ scale, const int32_t *__restrict__ idmap,
-              int64_t total, int64_t npix, int c, const uint32_t *__restrict__ fcnt, float alpha, int64_t n_x,
+              int64_t total, int64_t npix, int c, const uint32_t *__restrict__ fcnt, float alpha,
+              const float *__restrict__ wpix, int64_t n_x,
               float *__restrict__ acc, uint32_t *__restrict__ cnt, int32_t *__restrict__ err)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -129,7 +130,8 @@ __global__ void __launch_bounds__(256)
         return;
     }
     float w = 1.0f;
-    if (fcnt) w = image_weight(alpha, fcnt[(p / npix) * n_x + row]);
+    if (wpix) w = wpix[p];
+    else if (fcnt) w = image_weight(alpha, fcnt[(p / npix) * n_x + row]);
     const float sc = (DT == SM_F32) ? 1.0f : scale[p];
     float *a = acc + (int64_t)row * c;
     const int64_t base = p * c;
@@ -238,18 +240,18 @@ __global__ void k_render16(const int4 *__restrict__ idmap, int64_t n16, const ui
 
 template <int RULE>
 void scatter_dt(sm_dtype dt, dim3 g, cudaStream_t s, const void *probs, const float *scale, const int32_t *idmap,
-                int64_t total, int64_t npix, int c, const uint32_t *fcnt, float alpha, int64_t n_x, float *acc,
+                int64_t total, int64_t npix, int c, const uint32_t *fcnt, float alpha, const float *wpix, int64_t n_x, float *acc,
                 uint32_t *cnt, int32_t *err)
 {
     if (dt == SM_F32)
         k_scatter<RULE, SM_F32>
-            <<<g, 256, 0, s>>>(probs, scale, idmap, total, npix, c, fcnt, alpha, n_x, acc, cnt, err);
+            <<<g, 256, 0, s>>>(probs, scale, idmap, total, npix, c, fcnt, alpha, wpix, n_x, acc, cnt, err);
     else if (dt == SM_BF16)
         k_scatter<RULE, SM_BF16>
-            <<<g, 256, 0, s>>>(probs, scale, idmap, total, npix, c, fcnt, alpha, n_x, acc, cnt, err);
+            <<<g, 256, 0, s>>>(probs, scale, idmap, total, npix, c, fcnt, alpha, wpix, n_x, acc, cnt, err);
     else
         k_scatter<RULE, SM_FP8_E4M3>
-            <<<g, 256, 0, s>>>(probs, scale, idmap, total, npix, c, fcnt, alpha, n_x, acc, cnt, err);
+            <<<g, 256, 0, s>>>(probs, scale, idmap, total, npix, c, fcnt, alpha, wpix, n_x, acc, cnt, err);
 }
 
 }  // namespace
@@ -289,7 +291,7 @@ void launch_count_reset(const int32_t *idmap, int64_t npix, int nb, uint32_t *fc
 }
 
 void launch_scatter(sm_rule rule, sm_dtype dtype, const void *probs, const float *scale, const int32_t *idmap,
-                    int64_t npix, int nb, int c, const uint32_t *fcnt, float alpha, int64_t n_x, float *acc,
+                    int64_t npix, int nb, int c, const uint32_t *fcnt, float alpha, const float *wpix, int64_t n_x, float *acc,
                     uint32_t *cnt, int32_t *err, cudaStream_t s)
 {
     const int64_t total = npix * nb;
@@ -297,16 +299,16 @@ void launch_scatter(sm_rule rule, sm_dtype dtype, const void *probs, const float
     dim3 g((unsigned)((total + 255) / 256));
     switch (rule) {
     case SM_RULE_SUM:
-        scatter_dt<SM_RULE_SUM>(dtype, g, s, probs, scale, idmap, total, npix, c, fcnt, alpha, n_x, acc, cnt, err);
+        scatter_dt<SM_RULE_SUM>(dtype, g, s, probs, scale, idmap, total, npix, c, fcnt, alpha, wpix, n_x, acc, cnt, err);
         break;
     case SM_RULE_LOGSUM:
-        scatter_dt<SM_RULE_LOGSUM>(dtype, g, s, probs, scale, idmap, total, npix, c, fcnt, alpha, n_x, acc, cnt, err);
+        scatter_dt<SM_RULE_LOGSUM>(dtype, g, s, probs, scale, idmap, total, npix, c, fcnt, alpha, wpix, n_x, acc, cnt, err);
         break;
     case SM_RULE_MAXSUM:
-        scatter_dt<SM_RULE_MAXSUM>(dtype, g, s, probs, scale, idmap, total, npix, c, fcnt, alpha, n_x, acc, cnt, err);
+        scatter_dt<SM_RULE_MAXSUM>(dtype, g, s, probs, scale, idmap, total, npix, c, fcnt, alpha, wpix, n_x, acc, cnt, err);
         break;
     default:
-        scatter_dt<SM_RULE_VOTE>(dtype, g, s, probs, scale, idmap, total, npix, c, fcnt, alpha, n_x, acc, cnt, err);
+        scatter_dt<SM_RULE_VOTE>(dtype, g, s, probs, scale, idmap, total, npix, c, fcnt, alpha, wpix, n_x, acc, cnt, err);
         break;
     }
 }

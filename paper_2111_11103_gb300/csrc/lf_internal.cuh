@@ -68,8 +68,8 @@ void launch_count(const int32_t *idmap, const unsigned long long *keys, int64_t 
                   int64_t n_x, cudaStream_t s);
 void launch_count_reset(const int32_t *idmap, int64_t npix, int nb, uint32_t *fcnt, int64_t n_x, cudaStream_t s);
 void launch_scatter(sm_rule rule, sm_dtype dtype, const void *probs, const float *scale, const int32_t *idmap,
-                    int64_t npix, int nb, int c, const uint32_t *fcnt, float alpha, int64_t n_x, float *acc,
-                    uint32_t *cnt, int32_t *err, cudaStream_t s);
+                    int64_t npix, int nb, int c, const uint32_t *fcnt, float alpha, const float *wpix, int64_t n_x,
+                    float *acc, uint32_t *cnt, int32_t *err, cudaStream_t s);
 // Pipelined scatter (scatter.cu): TMA-streamed tiles, run-length
 // pre-reduction in registers, vector reductions into the rows.  Face mode
 // passes the z-buffer keys (read, re-armed, optionally written out as row
@@ -78,14 +78,23 @@ void launch_scatter(sm_rule rule, sm_dtype dtype, const void *probs, const float
 bool scatter_tma_supported(int c);
 void launch_scatter_tma(sm_rule rule, sm_dtype dtype, const void *probs, const float *scale,
                         unsigned long long *keys, const int32_t *ids_in, int32_t *ids_out, int64_t total_px,
-                        int64_t npix, int c, const uint32_t *fcnt, float alpha, int64_t n_x, float *acc,
-                        uint32_t *cnt, int32_t *err, cudaStream_t s);
+                        int64_t npix, int c, const uint32_t *fcnt, float alpha, const float *wpix, int64_t n_x,
+                        float *acc, uint32_t *cnt, int32_t *err, cudaStream_t s);
 // Visible-area pre-pass (fuse.cu): per-frame pixel counts of the triangles in
 // a batch's z-buffers (re-armed), folded into per-triangle maxima; texel
 // steps from the maxima.
 void launch_area_count(unsigned long long *keys, int64_t npix, int nb, uint32_t *fcnt, int64_t F, cudaStream_t s);
 void launch_area_max(uint32_t *fcnt, int nb, int64_t F, int32_t *area, cudaStream_t s);
 void launch_texel_res(const int32_t *area, int64_t F, float gamma, int32_t *s_out, cudaStream_t s);
+// Learned per-observation confidence (confidence.cu).
+void launch_conf_features(const unsigned long long *keys, int64_t total, int H, int W, const float4 *V,
+                          const int4 *faces, int64_t F, const sm_intrinsics *K, const double *T, const void *probs,
+                          sm_dtype dt, const float *scale, int c, float *feat, cudaStream_t s);
+void launch_conf_forward(const float *params, const float *feat, int64_t n, float *w, cudaStream_t s);
+void launch_conf_train_step(float *params, const float *feat, const float *target, int64_t n, float lr, float *grad,
+                            float *loss, cudaStream_t s);
+void launch_conf_targets(const void *probs, sm_dtype dt, const float *scale, int c, const int32_t *rows, int64_t n,
+                         const uint8_t *labels8, int64_t n_x, float *y, cudaStream_t s);
 void launch_normalise(sm_rule rule, const float *acc, const uint32_t *cnt, int64_t n_x, int c, float *dist,
                       int32_t *labels, uint8_t *labels8, cudaStream_t s);
 void launch_render(const int32_t *idmap, int64_t npix, const uint8_t *labels8, int64_t n_x, uint8_t *out,

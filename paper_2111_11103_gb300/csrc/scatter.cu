@@ -91,6 +91,7 @@ struct Args {
     int c;
     const uint32_t *fcnt;      // per-frame row histogram (image weights) or null
     float alpha;               // image-weight mix (1: w^(I))
+    const float *wpix;         // explicit per-pixel weights (replace the histogram), or null
     int64_t n_x;
     float *acc;
     uint32_t *cnt;
@@ -138,7 +139,7 @@ __device__ __forceinline__ void pixel_info(const Args &a, int64_t p, int i, cons
         atomicCAS(a.err, 0, (int32_t)kErrRowRange);
         row = -1;
     }
-    if (IMAGE && row >= 0) w = image_weight(a.alpha, a.fcnt[(p / a.npix) * a.n_x + row]);
+    if (IMAGE && row >= 0) w = a.wpix ? a.wpix[p] : image_weight(a.alpha, a.fcnt[(p / a.npix) * a.n_x + row]);
     if (DT != SM_F32) sc = sscale ? sscale[i] : a.scale[p];
 }
 
@@ -669,7 +670,7 @@ void launch_dt(sm_dtype dt, const Args &a, cudaStream_t s)
 template <int RULE>
 void launch_rule(sm_dtype dt, const Args &a, cudaStream_t s)
 {
-    if (a.fcnt) launch_dt<RULE, true>(dt, a, s);
+    if (a.fcnt || a.wpix) launch_dt<RULE, true>(dt, a, s);
     else launch_dt<RULE, false>(dt, a, s);
 }
 
@@ -679,12 +680,12 @@ bool scatter_tma_supported(int c) { return c % 4 == 0 && c >= 4 && c <= 128; }
 
 void launch_scatter_tma(sm_rule rule, sm_dtype dtype, const void *probs, const float *scale,
                         unsigned long long *keys, const int32_t *ids_in, int32_t *ids_out, int64_t total_px,
-                        int64_t npix, int c, const uint32_t *fcnt, float alpha, int64_t n_x, float *acc,
-                        uint32_t *cnt, int32_t *err, cudaStream_t s)
+                        int64_t npix, int c, const uint32_t *fcnt, float alpha, const float *wpix, int64_t n_x,
+                        float *acc, uint32_t *cnt, int32_t *err, cudaStream_t s)
 {
     if (total_px <= 0) return;
-    Args a{static_cast<const uint8_t *>(probs), scale, keys, ids_in, ids_out, total_px, npix, c, fcnt, alpha, n_x, acc,
-           cnt, err, scale != nullptr && ((uintptr_t)scale & 15) == 0};
+    Args a{static_cast<const uint8_t *>(probs), scale, keys, ids_in, ids_out, total_px, npix, c, fcnt, alpha, wpix,
+           n_x, acc, cnt, err, scale != nullptr && ((uintptr_t)scale & 15) == 0};
     switch (rule) {
     case SM_RULE_SUM: launch_rule<SM_RULE_SUM>(dtype, a, s); break;
     case SM_RULE_LOGSUM: launch_rule<SM_RULE_LOGSUM>(dtype, a, s); break;

@@ -25,7 +25,10 @@ SYMBOLS = ["sm_mesh_upload", "sm_fuse_frames", "sm_normalise", "sm_render_labels
            "sm_read_state", "sm_load_state", "sm_check", "sm_num_rows", "sm_num_classes", "sm_mesh_free",
            "sm_status_string", "sm_last_error", "sm_profile_enable", "sm_profile_read", "sm_render_rows_noalloc",
            "sm_fuse_render_host", "sm_host_alloc", "sm_host_free", "sm_set_weight_mix", "sm_texel_res_from_gamma",
-           "sm_autotune_batch"]
+           "sm_autotune_batch", "sm_fuse_frames_weighted", "sm_conf_features", "sm_conf_targets", "sm_conf_forward",
+           "sm_conf_train_step"]
+SM_CONF_FEATURES = 5
+SM_CONF_PARAMS = 1281
 SM_NOALLOC_MAX_PIXELS = 1572864
 SM_NOALLOC_MAX_FRAMES = 1024
 
@@ -67,6 +70,11 @@ def lib() -> ctypes.CDLL:
             "sm_set_weight_mix": [P, ctypes.c_float],
             "sm_texel_res_from_gamma": [P, P, P, i32, i32, i32, ctypes.c_float, P, P, P],
             "sm_autotune_batch": [P, P, i32, P, P, P, i32, i32, i32, ctypes.POINTER(i32), P],
+            "sm_fuse_frames_weighted": [P, P, i32, P, P, P, i32, i32, i32, P, P, P],
+            "sm_conf_features": [P, P, i32, P, P, P, i32, i32, i32, P, P, P],
+            "sm_conf_targets": [P, P, i32, P, P, i64, P, P],
+            "sm_conf_forward": [P, P, i64, P, P],
+            "sm_conf_train_step": [P, P, P, i64, ctypes.c_float, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -164,6 +172,34 @@ def sm_autotune_batch(mesh: int, probs, dtype, scale, K, cam_to_world, N: int, H
     _check(lib().sm_autotune_batch(mesh, _ptr(probs), _enum(SM_DTYPE, dtype), _ptr(scale), _ptr(K),
                                    _ptr(cam_to_world), int(N), int(H), int(W), ctypes.byref(best), _stream(stream)))
     return best.value
+
+
+def sm_fuse_frames_weighted(mesh: int, probs, dtype, scale, K, cam_to_world, N: int, H: int, W: int, weights,
+                            idmap_out=None, stream=None):
+    _check(lib().sm_fuse_frames_weighted(mesh, _ptr(probs), _enum(SM_DTYPE, dtype), _ptr(scale), _ptr(K),
+                                         _ptr(cam_to_world), int(N), int(H), int(W), _ptr(weights), _ptr(idmap_out),
+                                         _stream(stream)))
+
+
+def sm_conf_features(mesh: int, probs, dtype, scale, K, cam_to_world, N: int, H: int, W: int, feat_out, rows_out,
+                     stream=None):
+    _check(lib().sm_conf_features(mesh, _ptr(probs), _enum(SM_DTYPE, dtype), _ptr(scale), _ptr(K),
+                                  _ptr(cam_to_world), int(N), int(H), int(W), _ptr(feat_out), _ptr(rows_out),
+                                  _stream(stream)))
+
+
+def sm_conf_targets(mesh: int, probs, dtype, scale, rows, n_pixels: int, target_out, stream=None):
+    _check(lib().sm_conf_targets(mesh, _ptr(probs), _enum(SM_DTYPE, dtype), _ptr(scale), _ptr(rows),
+                                 int(n_pixels), _ptr(target_out), _stream(stream)))
+
+
+def sm_conf_forward(params, feat, n: int, w_out, stream=None):
+    _check(lib().sm_conf_forward(_ptr(params), _ptr(feat), int(n), _ptr(w_out), _stream(stream)))
+
+
+def sm_conf_train_step(params, feat, target, n: int, lr: float, grad_out, loss_out, stream=None):
+    _check(lib().sm_conf_train_step(_ptr(params), _ptr(feat), _ptr(target), int(n), float(lr), _ptr(grad_out),
+                                    _ptr(loss_out), _stream(stream)))
 
 
 def sm_host_alloc(nbytes: int) -> int:

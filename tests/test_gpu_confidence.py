@@ -1,0 +1,148 @@
+"""GPU parity of the learned confidence against its binary64 oracle:
+features, the bfloat16 network's outputs, the training gradient and loss,
+the agreement targets, fusion with the predicted per-pixel weights (every
+rule), and a short training run lowering the loss."""
+import numpy as np
+import pytest
+import torch
+
+import scenegen as sg
+from gpu_common import assert_acc_close, to_dev
+from oracle import confidence as cf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2111_11103_gb300 import labelfuse as lf
+    lf.lib()
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def tiny(dev):
+    scene, cams = sg.tiny_room(), sg.circle_poses()
+    return scene, cams, sg.predictions(scene, cams, "tiny", device=dev)
+
+
+@pytest.fixture(scope="module")
+def medium(dev):
+    scene = sg.paper_room(target_faces=60_000)
+    cams = sg.random_walk_poses(12, H=151, W=203, fx=183.0, fy=183.0, cx=101.0, cy=75.0)
+    return scene, cams, sg.predictions(scene, cams, "paper", device=dev)
+
+
+def gpu_features(scene, cams, probs, dev):
+    from paper_2111_11103_gb300 import labelfuse as lf
+    N, H, W, c = cams.K.shape[0], cams.H, cams.W, scene.n_classes
+    V, Fc, K, T, _ = to_dev(scene, cams, None, dev)
+    m = lf.sm_mesh_upload(V, Fc, None, c, "sum", "pixel")
+    try:
+        feat = torch.full((N, H, W, 5), -3.0, device=dev)
+        rows = torch.full((N, H, W), -7, dtype=torch.int32, device=dev)
+        lf.sm_conf_features(m, probs, "f32", None, K, T, N, H, W, feat, rows)
+        lf.sm_check(m)
+    finally:
+        lf.sm_mesh_free(m)
+    return feat, rows
+
+
+def _params(seed, scale=0.5):
+    rng = np.random.default_rng(seed)
+    return rng.normal(0, scale, cf.N_PARAMS).astype(np.float32)
+
+
+@pytest.mark.parametrize("which", ["tiny", "medium"])
+def test_features_match_oracle(ora, dev, tiny, medium, which):
+    scene, cams, probs = tiny if which == "tiny" else medium
+    feat, rows = gpu_features(scene, cams, probs, dev)
+    feat, rows = feat.cpu().numpy(), rows.cpu().numpy()
+    P = probs.cpu().numpy()
+    for i in range(cams.K.shape[0]):
+        X, face = cf.features(ora, scene.vertices, scene.faces, cams.K[i], cams.cam_to_world[i], P[i], cams.H, cams.W)
+        assert np.array_equal(rows[i].ravel(), face)  # face mode: row = triangle
+        np.testing.assert_allclose(feat[i].reshape(-1, 5), X, rtol=0, atol=3e-6)
+
+
+def test_forward_and_gradient_match_oracle(dev, medium):
+    from paper_2111_11103_gb300 import labelfuse as lf
+    scene, cams, probs = medium
+    feat, rows = gpu_features(scene, cams, probs, dev)
+    X = feat.reshape(-1, 5)[rows.reshape(-1) >= 0][:5000].contiguous()
+    n = X.shape[0]
+    y = (torch.arange(n, device=dev) % 3 == 0).float()
+    params = torch.as_tensor(_params(3), device=dev)
+    w = torch.empty(n, device=dev)
+    lf.sm_conf_forward(params, X, n, w)
+    _, w_ora, _ = cf.forward(params.cpu().numpy(), X.cpu().numpy())
+    np.testing.assert_allclose(w.cpu().numpy(), w_ora, rtol=0, atol=2e-6)
+    grad, loss = torch.empty(cf.N_PARAMS, device=dev), torch.empty(1, device=dev)
+    p0 = params.clone()
+    lf.sm_conf_train_step(params, X, y, n, 0.0, grad, loss)
+    torch.cuda.synchronize()
+    assert torch.equal(params, p0)  # lr = 0
+    l_ora, g_ora = cf.loss_and_grad(p0.cpu().numpy(), X.cpu().numpy(), y.cpu().numpy())
+    assert abs(float(loss) - l_ora) <= 1e-5 * abs(l_ora)
+    np.testing.assert_allclose(grad.cpu().numpy(), g_ora, rtol=0, atol=1e-5 * np.abs(g_ora).max())
+    lf.sm_conf_train_step(params, X, y, n, 0.5, grad, loss)  # the update is params - lr * grad
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(params.cpu().numpy(), p0.cpu().numpy() - 0.5 * grad.cpu().numpy(), rtol=0, atol=1e-7)
+
+
+@pytest.mark.parametrize("rule", ["sum", "logsum", "maxsum", "vote"])
+def test_fusion_with_predicted_weights(ora, dev, tiny, rule):
+    from paper_2111_11103_gb300 import labelfuse as lf
+    scene, cams, probs = tiny
+    N, H, W, c = cams.K.shape[0], cams.H, cams.W, scene.n_classes
+    feat, rows = gpu_features(scene, cams, probs, dev)
+    params = torch.as_tensor(_params(4), device=dev)
+    w = torch.empty((N, H, W), device=dev)
+    lf.sm_conf_forward(params, feat, N * H * W, w)
+    V, Fc, K, T, _ = to_dev(scene, cams, None, dev)
+    m = lf.sm_mesh_upload(V, Fc, None, c, rule, "pixel")
+    try:
+        lf.sm_fuse_frames_weighted(m, probs, "f32", None, K, T, N, H, W, w)
+        acc = torch.empty((len(scene.faces), c), device=dev)
+        cnt = torch.empty(len(scene.faces), dtype=torch.int32, device=dev)
+        lf.sm_read_state(m, acc, cnt)
+        lf.sm_check(m)
+        with pytest.raises(lf.LabelFuseError):
+            lf.sm_fuse_frames_weighted(m, probs, "f32", None, K, T, N, H, W, None)
+    finally:
+        lf.sm_mesh_free(m)
+    A, cnt_o = ora.accumulate(rule, rows.cpu().numpy().ravel(), probs.cpu().numpy().reshape(-1, c), len(scene.faces),
+                              weights=w.cpu().numpy().ravel().astype(np.float64))
+    assert np.array_equal(cnt.cpu().numpy().astype(np.int64), cnt_o)
+    assert_acc_close(acc.cpu().numpy(), A)
+
+
+def test_targets_and_training_lower_the_loss(ora, dev, medium):
+    from paper_2111_11103_gb300 import labelfuse as lf
+    scene, cams, probs = medium
+    N, H, W, c = cams.K.shape[0], cams.H, cams.W, scene.n_classes
+    feat, rows = gpu_features(scene, cams, probs, dev)
+    V, Fc, K, T, _ = to_dev(scene, cams, None, dev)
+    m = lf.sm_mesh_upload(V, Fc, None, c, "logsum", "pixel")
+    try:
+        lf.sm_fuse_frames(m, probs, "f32", None, K, T, N, H, W)
+        labels = torch.empty(len(scene.faces), dtype=torch.int32, device=dev)
+        lf.sm_normalise(m, None, labels)
+        y = torch.empty((N, H, W), device=dev)
+        lf.sm_conf_targets(m, probs, "f32", None, rows, N * H * W, y)
+        lf.sm_check(m)
+    finally:
+        lf.sm_mesh_free(m)
+    y_ora = cf.targets(probs.cpu().numpy().reshape(-1, c), rows.cpu().numpy().ravel(), labels.cpu().numpy())
+    assert np.array_equal(y.cpu().numpy().ravel(), y_ora)
+    sel = rows.reshape(-1) >= 0
+    X, Y = feat.reshape(-1, 5)[sel].contiguous(), y.reshape(-1)[sel].contiguous()
+    params = torch.as_tensor(_params(5, 0.2), device=dev)
+    grad, loss = torch.empty(cf.N_PARAMS, device=dev), torch.empty(1, device=dev)
+    losses = []
+    for _ in range(150):
+        lf.sm_conf_train_step(params, X, Y, X.shape[0], 1.0, grad, loss)
+        losses.append(float(loss))
+    assert losses[-1] < 0.9 * losses[0]
+    assert np.isfinite(losses).all()
