@@ -107,9 +107,9 @@ size_t dtype_size(sm_dtype d) { return d == SM_F32 ? 4 : (d == SM_BF16 ? 2 : 1);
 // the streaming scatter launches long enough to fill the GPU, which matters
 // more than keeping both z-buffer slots in L2; the per-frame row histograms
 // of the image weights stay within ~512 MB.
-int batch_frames(const sm_mesh *m, int64_t npix, int N)
+int batch_frames(const sm_mesh *m, int64_t npix, int N, bool tuned = true)
 {
-    int64_t B = (m->tuned_B > 0 && m->tuned_npix == npix) ? m->tuned_B : (int64_t)(48u << 20) / (npix * 8);
+    int64_t B = (tuned && m->tuned_B > 0 && m->tuned_npix == npix) ? m->tuned_B : (int64_t)(48u << 20) / (npix * 8);
     if (m->weight == SM_WEIGHT_IMAGE && m->n_x > 0) {
         const int64_t Bi = (int64_t)(512u << 20) / (m->n_x * 4);
         if (Bi < B) B = Bi;
@@ -678,7 +678,7 @@ sm_status sm_fuse_render_host(sm_mesh *m, const void *h_probs, sm_dtype dtype, c
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     constexpr int NC = sm_mesh::kCopyStreams;
     const int64_t npix = (int64_t)H * W;
-    const int B = batch_frames(m, npix, N);
+    const int B = batch_frames(m, npix, N, false);  // small batches keep copies and fusion overlapped
     const size_t frame_bytes = (size_t)npix * m->c * dtype_size(dtype);
     const size_t probs_slot = ((size_t)B * frame_bytes + 255) & ~(size_t)255;
     const size_t slot_bytes = probs_slot + (dtype != SM_F32 ? (((size_t)B * npix * 4 + 255) & ~(size_t)255) : 0);
