@@ -39,6 +39,7 @@ import scenegen as sg  # noqa: E402
 
 METRIC = "frames/s fuse+render (640x480, c=40) & HBM roofline %, plain vs BF16/FP8"
 WORKLOAD = "paper-shaped room: 500k triangles, 1000 frames 640x480, c=40"
+WORKLOAD_HIRES = "paper-shaped room: 500k triangles, 250 frames 1296x968 fused 4x, c=40"
 
 
 def parse():
@@ -57,6 +58,8 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the BF16 / FP8 storage forms")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay timing")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default frames per launch")
+    ap.add_argument("--hires", action="store_true",
+                    help="1296 x 968 frames (fx = fy = 1170): a 250-frame ring fused and rendered 4 times per step")
     return ap.parse_args()
 
 
@@ -153,7 +156,10 @@ def dist_env():
 
 def make_workload(args, dev):
     scene = sg.paper_room(target_faces=args.faces)
-    cams = sg.random_walk_poses(args.frames)
+    if args.hires:
+        cams = sg.random_walk_poses(args.frames, H=968, W=1296, fx=1170.0, fy=1170.0, cx=647.5, cy=483.5)
+    else:
+        cams = sg.random_walk_poses(args.frames)
     N, H, W, c = args.frames, cams.H, cams.W, scene.n_classes
     probs = torch.empty((N, H, W, c), dtype=torch.float32, device=dev)
     for a in range(0, N, 25):
@@ -224,6 +230,12 @@ def run_ours(args):
     from paper_2111_11103_gb300 import labelfuse as lf
     from paper_2111_11103_gb300 import shard
     lf.lib()
+    # the e2e leg's page-locked input, allocated before anything else touches
+    # host memory (a 49 GB block allocated late, in a process that has already
+    # churned host memory, copied markedly slower in probes)
+    h_probs = None
+    if not args.no_e2e and rank == 0 and ws == 1 and not args.hires:
+        h_probs = lf.pinned_empty((args.frames, 480, 640, 40), torch.float32)
 
     scene, cams, probs = make_workload(args, dev)
     N, H, W, c = probs.shape
@@ -241,6 +253,7 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
+    ring = 4 if args.hires else 1
     # frames of this rank: all of them on one GPU; on several, a contiguous
     # share, fused locally and completed by one all-reduce of the state
     fa, fb = shard.frame_range(N, rank, ws)
@@ -252,12 +265,15 @@ def run_ours(args):
         (max over ranks) and the per-kernel event totals of the timed region."""
         def step():
             lf.sm_reset(m, stream)
-            if ws > 1:
-                shard.fuse_sharded(m, x, dtype, scale, K, T, H, W, rank, ws, idmap_out=idmaps[fa:fb], state=state)
-            else:
-                lf.sm_fuse_frames(m, x, dtype, scale, K, T, N, H, W, idmaps, stream)
+            for _ in range(ring):  # the frames fused (and rendered) `ring` times per step
+                if ws > 1:
+                    shard.fuse_sharded(m, x, dtype, scale, K, T, H, W, rank, ws, idmap_out=idmaps[fa:fb],
+                                       state=state)
+                else:
+                    lf.sm_fuse_frames(m, x, dtype, scale, K, T, N, H, W, idmaps, stream)
             lf.sm_normalise(m, None, None, stream)
-            lf.sm_render_idmap(m, idmaps[fa:fb], (fb - fa) * H * W, images[fa:fb], stream)
+            for _ in range(ring):
+                lf.sm_render_idmap(m, idmaps[fa:fb], (fb - fa) * H * W, images[fa:fb], stream)
 
         for _ in range(max(args.warmup, 3)):
             step()
@@ -288,7 +304,7 @@ def run_ours(args):
         one launch processes, over the launch's average event time."""
         n_sc, ms_sc = prof["scatter"]
         per_frame = H * W * c * elem_bytes + H * W * 4 + (H * W * 4 if scaled else 0)
-        fpl = (fb - fa) * args.steps / max(n_sc, 1)
+        fpl = ring * (fb - fa) * args.steps / max(n_sc, 1)
         achieved = per_frame * fpl / (ms_sc / max(n_sc, 1) / 1e3) / 1e9
         return achieved, per_frame, fpl
 
@@ -323,7 +339,7 @@ def run_ours(args):
 
     ms_step, prof, clocks = timed("f32", probs, None)
     launches = sum(n for n, _ in prof.values())
-    value = N / (ms_step / 1e3)  # the whole 1,000-frame sequence, split over the ranks
+    value = ring * N / (ms_step / 1e3)  # the whole sequence (x ring), split over the ranks
     achieved, bytes_per_frame_scatter, frames_per_launch = scatter_roofline(prof, 4, False)
     peak, peak_kind = peaks()
     kernels = {k: {"launches": n, "ms_per_step": t / args.steps} for k, (n, t) in prof.items() if n}
@@ -333,9 +349,10 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "faces": int(scene.faces.shape[0]), "frames": N, "H": H, "W": W,
+            "config": {"workload": WORKLOAD_HIRES if args.hires else WORKLOAD, "faces": int(scene.faces.shape[0]),
+                       "frames": N, "ring": ring, "H": H, "W": W,
                        "classes": c, "rule": args.rule, "weight": args.weight, "probs": "f32 HWC",
-                       "l2": "inputs (49 GB) larger than L2, no flush",
+                       "l2": "inputs larger than L2 (49-50 GB), no flush",
                        "parallelism": f"frames{ws}" if ws > 1 else "single", "frames_per_launch": tuned_B},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": "scatter",
@@ -345,16 +362,16 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clocks}
     # step-level HBM fraction on the algorithmic bytes of the whole path
-    algo_step = (fb - fa) * (H * W * c * 4 + 2 * H * W * 4 + H * W) + 2 * sg_rows(m, lf) * c * 4
+    algo_step = ring * (fb - fa) * (H * W * c * 4 + 2 * H * W * 4 + H * W) + 2 * sg_rows(m, lf) * c * 4
     line["step_hbm_frac"] = algo_step / (ms_step / 1e3) / 1e9 / peak
 
-    if ws == 1 and not args.no_graph:
+    if ws == 1 and not args.no_graph and not args.hires:
         line["graph"] = graph_timing()
     if not args.no_forms:
-        line["forms"] = storage_forms(probs, timed, scatter_roofline, peak, N, args.steps)
-    if not args.no_e2e and rank == 0 and ws == 1:
+        line["forms"] = storage_forms(probs, timed, scatter_roofline, peak, ring * N, args.steps)
+    if not args.no_e2e and rank == 0 and ws == 1 and not args.hires:
         try:
-            line["e2e"] = e2e(args, lf, m, probs, K, T, dev, stream)
+            line["e2e"] = e2e(args, lf, m, probs, K, T, dev, stream, h_probs)
         except (RuntimeError, MemoryError) as exc:  # e.g. pinned host memory unavailable
             line["e2e"] = {"value": None, "unit": "frames/s", "error": str(exc)[:200]}
     if not args.no_cpu and rank == 0:
@@ -408,7 +425,7 @@ def sg_rows(m, lf):
     return lf.sm_num_rows(m)
 
 
-def e2e(args, lf, m, probs, K, T, dev, stream):
+def e2e(args, lf, m, probs, K, T, dev, stream, h_probs=None):
     """Same metric end to end through the C ABI with HOST buffers: one
     sm_fuse_render_host call per step streams the predictions and cameras
     host -> device (page-locked memory from sm_host_alloc), fuses, normalises,
@@ -418,7 +435,8 @@ def e2e(args, lf, m, probs, K, T, dev, stream):
     # page-locked host buffers from the library (one block each), written by
     # the CPU as a data loader would (staged through pageable memory: pages
     # that the GPU itself wrote by DMA stream back markedly slower here)
-    h_probs = lf.pinned_empty(probs.shape, probs.dtype)
+    if h_probs is None or tuple(h_probs.shape) != tuple(probs.shape):
+        h_probs = lf.pinned_empty(probs.shape, probs.dtype)
     tmp = torch.empty((50,) + tuple(probs.shape[1:]), dtype=probs.dtype)
     for a in range(0, N, 50):
         n = min(50, N - a)
@@ -448,6 +466,8 @@ def e2e(args, lf, m, probs, K, T, dev, stream):
 
 def main():
     args = parse()
+    if args.hires and args.frames == 1000:
+        args.frames = 250  # the ring of the high-resolution workload (50 GB of FP32 predictions)
     if args.impl == "reference":
         run_reference(args)
     else:
