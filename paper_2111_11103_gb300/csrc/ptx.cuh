@@ -82,13 +82,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
-// Bulk prefetch of [src, src + bytes) into L2 (no shared memory, no
-// completion tracking).  src 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes)
-{
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-
 // Hardware base-2 logarithm (MUFU), flushing subnormal inputs to zero; only
 // used on values clamped to >= 2^-30, where it needs no denormal handling.
 __device__ __forceinline__ float lg2_ftz(float x)

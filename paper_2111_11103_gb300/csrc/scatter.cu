@@ -12,15 +12,16 @@
 //    per-pixel metadata: the z-buffer keys left by the raster (face mode; row
 //    = triangle of the nearest surface) or the resolved row map, and the
 //    per-pixel scales of BF16/FP8 storage;
-//  * 8 consumer warps, 32 pixels each.  A warp splits into groups of c/4
-//    lanes; each lane owns four classes and each group walks a contiguous run
-//    of pixels, four pixels per software-pipelined step, keeping the running
-//    sum of phi(p) for the current row in registers.  Only when the row (or
-//    the pixel weight) changes is the run flushed: the group's lanes together
-//    add one contiguous row of P with 16-byte vector reductions (L2
-//    evict-last, so the rows a trajectory keeps revisiting stay in L2 while
-//    the prediction stream passes through), plus the run length into the
-//    observation count;
+//  * 8 consumer warps, 32 pixels each.  For c = 40 and c = 20 (compile-time
+//    class count) a pixel is split over 5 lanes and the warp runs 6 groups in
+//    lock step over contiguous pixel ranges (warp_tile_q): a few ballots per
+//    tile give the entry layout (an entry = a run of one row and weight
+//    within a group), the steps build each entry in registers and store it
+//    to its slot, and the whole warp then adds all entries into P with
+//    16-byte vector reductions (L2 evict-last, so the rows a trajectory
+//    keeps revisiting stay in L2 while the prediction stream passes through)
+//    plus their lengths into the observation counts.  Other c take a generic
+//    walk (warp_tile) with groups of c/4 lanes that flush each run as it ends;
 //  * log-sum multiplies up to four clamped probabilities (>= 2^-30 each, so
 //    no underflow) before one hardware log2 per class: sum_k log p_k =
 //    log prod_k p_k, up to rounding;
