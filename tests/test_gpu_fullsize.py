@@ -83,3 +83,25 @@ def test_paper_workload_full_size(ora):
     del probs
     torch.cuda.empty_cache()
     assert np.array_equal(ora.render_labels(idm_o, lab_g), img.cpu().numpy())
+
+
+@pytest.mark.parametrize("kind", ["f32", "fp8_e4m3"])
+def test_high_resolution_frames(ora, kind):
+    """The high-resolution configuration's frames (1296 x 968, fx = fy = 1170,
+    the full paper-shaped mesh): 6 frames against the oracle, FP32 and the
+    FP8 storage form (the oracle fed the dequantised values)."""
+    from gpu_common import check_against_oracle, run_gpu
+    dev = torch.device("cuda:0")
+    scene = sg.paper_room()
+    cams = sg.random_walk_poses(6, H=968, W=1296, fx=1170.0, fy=1170.0, cx=647.5, cy=483.5)
+    probs = sg.predictions(scene, cams, "paper", device=dev)
+    if kind == "f32":
+        res = run_gpu(scene, cams, probs, "logsum", "pixel", reraster=True)
+        check_against_oracle(ora, scene, cams, probs.cpu().numpy(), res, "logsum", "pixel", nthreads=8)
+    else:
+        scale = probs.amax(-1) / 448.0
+        q = (probs / scale[..., None]).to(torch.float8_e4m3fn).contiguous()
+        deq = (q.float() * scale[..., None]).cpu().numpy()
+        res = run_gpu(scene, cams, q, "sum", "pixel", dtype=kind, scale=scale.contiguous(), reraster=False)
+        check_against_oracle(ora, scene, cams, deq, res, "sum", "pixel", nthreads=8)
+    assert (res.idmaps >= 0).mean() > 0.99
