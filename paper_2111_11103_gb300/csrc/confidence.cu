@@ -255,11 +255,9 @@ void launch_conf_train_step(float *params, const float *feat, const float *targe
     cudaMemsetAsync(loss, 0, sizeof(float), s);
     if (n > 0) {
         const size_t smem = (SM_CONF_PARAMS + 3 + (size_t)kObs * kRow) * sizeof(float);
-        static bool configured = false;
-        if (!configured) {
+        static PerDeviceOnce configured;
+        if (configured.first(current_device()))
             cudaFuncSetAttribute(k_conf_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            configured = true;
-        }
         k_conf_grad<<<(unsigned)((n + kObs - 1) / kObs), kObs, smem, s>>>(params, feat, target, n, grad, loss);
     }
     k_conf_update<<<(SM_CONF_PARAMS + 255) / 256, 256, 0, s>>>(params, grad, lr);

@@ -1,6 +1,8 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <atomic>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -37,6 +39,23 @@ void launch_project(const sm_intrinsics *K, const double *T, int N, Camera *out,
 // Faces are processed in clusters of 32 (one warp); bounds holds two float4
 // (min, max corner; min.w != 0 marks a cluster without valid faces) per cluster.
 constexpr int kClusterFaces = 32;
+
+// Remembers, per device ordinal (< 64), that a per-device setting of a kernel
+// (cudaFuncSetAttribute applies to the current device) has been made.
+struct PerDeviceOnce {
+    std::atomic<uint64_t> done{0};
+    bool first(int dev)
+    {
+        const uint64_t bit = 1ull << (dev & 63);
+        return !(done.fetch_or(bit) & bit);
+    }
+};
+__host__ inline int current_device()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return dev;
+}
 
 // Image weight of a pixel whose row holds n pixels of its frame, mixed with
 // the pixel weight (Fig. 5a, read as a linear mix): (1 - alpha) + alpha / n in

@@ -608,43 +608,49 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
     }
 }
 
-int g_num_sms = 0;
-uint32_t g_cta_smem = 0;  // shared memory one CTA may take so that two fit on an SM
+// SM count and the shared memory one CTA may take so that two fit on an SM,
+// per device ordinal (< 64).
+struct DevInfo {
+    int sms;
+    uint32_t cta_smem;
+};
 
-void ensure_num_sms()
+DevInfo dev_info()
 {
-    if (g_num_sms == 0) {
-        int dev = 0, per_sm = 0, reserved = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    static std::atomic<uint64_t> known{0};
+    static DevInfo info[64];
+    const int dev = current_device() & 63;
+    if (!(known.load() & (1ull << dev))) {
+        int sms = 0, per_sm = 0, reserved = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
         cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-        if (g_num_sms <= 0) g_num_sms = 1;
         const int cta = per_sm / 2 - reserved;
-        g_cta_smem = cta > (96 << 10) ? (uint32_t)cta : (96u << 10);
+        info[dev] = DevInfo{sms > 0 ? sms : 1, cta > (96 << 10) ? (uint32_t)cta : (96u << 10)};
+        known.fetch_or(1ull << dev);
     }
+    return info[dev];
 }
 
 template <int RULE, int DT, bool IMAGE, int C>
 void launch_one(const Args &a, cudaStream_t s)
 {
-    static bool configured = false;
-    ensure_num_sms();
+    static PerDeviceOnce configured;
+    const DevInfo di = dev_info();
     // as many stages (up to 4) as fit beside the entry arrays with two CTAs per SM
     const StageLayout L = stage_layout<DT>(a);
-    int stages = (int)((g_cta_smem - 128u - QueueLayout<C, DT>::bytes) / L.stride);
+    int stages = (int)((di.cta_smem - 128u - QueueLayout<C, DT>::bytes) / L.stride);
     stages = stages < 1 ? 1 : (stages > 4 ? 4 : stages);
     const size_t smem = 128 + QueueLayout<C, DT>::bytes + (size_t)stages * L.stride;
-    if (!configured) {
+    if (configured.first(current_device())) {
         cudaFuncSetAttribute(k_scatter_tma<RULE, DT, IMAGE, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 << 10);
         // the whole unified L1 as shared memory, so that two CTAs fit
         cudaFuncSetAttribute(k_scatter_tma<RULE, DT, IMAGE, C>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
-        configured = true;
     }
     const int64_t ntiles = (a.total_px + kTile - 1) / kTile;
-    int64_t grid = 2LL * g_num_sms;
+    int64_t grid = 2LL * di.sms;
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
     k_scatter_tma<RULE, DT, IMAGE, C><<<(unsigned)grid, kThreads, smem, s>>>(a, stages);
