@@ -365,15 +365,15 @@ def run_ours(args):
     algo_step = ring * (fb - fa) * (H * W * c * 4 + 2 * H * W * 4 + H * W) + 2 * sg_rows(m, lf) * c * 4
     line["step_hbm_frac"] = algo_step / (ms_step / 1e3) / 1e9 / peak
 
+    if not args.no_e2e and rank == 0 and ws == 1 and not args.hires:
+        try:
+            line["e2e"] = e2e(args, lf, scene, probs, K, T, dev, stream, h_probs)
+        except (RuntimeError, MemoryError) as exc:  # e.g. pinned host memory unavailable
+            line["e2e"] = {"value": None, "unit": "frames/s", "error": str(exc)[:200]}
     if ws == 1 and not args.no_graph and not args.hires:
         line["graph"] = graph_timing()
     if not args.no_forms:
         line["forms"] = storage_forms(probs, timed, scatter_roofline, peak, ring * N, args.steps)
-    if not args.no_e2e and rank == 0 and ws == 1 and not args.hires:
-        try:
-            line["e2e"] = e2e(args, lf, m, probs, K, T, dev, stream, h_probs)
-        except (RuntimeError, MemoryError) as exc:  # e.g. pinned host memory unavailable
-            line["e2e"] = {"value": None, "unit": "frames/s", "error": str(exc)[:200]}
     if not args.no_cpu and rank == 0:
         line["cpu_baseline"] = cpu_baseline(scene, cams, probs, args, min(args.cpu_frames, N))
     lf.sm_mesh_free(m)
@@ -425,13 +425,15 @@ def sg_rows(m, lf):
     return lf.sm_num_rows(m)
 
 
-def e2e(args, lf, m, probs, K, T, dev, stream, h_probs=None):
+def e2e(args, lf, scene, probs, K, T, dev, stream, h_probs=None):
     """Same metric end to end through the C ABI with HOST buffers: one
     sm_fuse_render_host call per step streams the predictions and cameras
     host -> device (page-locked memory from sm_host_alloc), fuses, normalises,
     renders every frame and copies the label images back, all inside the
-    timed region."""
+    timed region.  A mesh of its own, uploaded here."""
     N, H, W, c = probs.shape
+    m = lf.sm_mesh_upload(torch.as_tensor(scene.vertices, device=dev), torch.as_tensor(scene.faces, device=dev),
+                          None, c, args.rule, args.weight)
     # page-locked host buffers from the library (one block each), written by
     # the CPU as a data loader would (staged through pageable memory: pages
     # that the GPU itself wrote by DMA stream back markedly slower here)
@@ -459,6 +461,7 @@ def e2e(args, lf, m, probs, K, T, dev, stream, h_probs=None):
         step()
     torch.cuda.synchronize(dev)
     dt = (time.perf_counter() - t0) / steps
+    lf.sm_mesh_free(m)
     hb = h_probs.numel() * h_probs.element_size() + h_K.numel() * 8 + h_T.numel() * 8
     return {"value": N / dt, "unit": "frames/s", "h2d_bytes_per_step": hb, "d2h_bytes_per_step": N * H * W,
             "steps": steps, "call": "sm_fuse_render_host"}
