@@ -308,8 +308,8 @@ def run_ours(args):
         achieved = per_frame * fpl / (ms_sc / max(n_sc, 1) / 1e3) / 1e9
         return achieved, per_frame, fpl
 
-    # frames per launch: the library's autotuner on a 128-frame sample
-    n_tune = min(128, N)
+    # frames per launch: the library's autotuner on a 256-frame sample
+    n_tune = min(256, N)
     tuned_B = lf.sm_autotune_batch(m, probs[:n_tune], "f32", None, K[:n_tune], T[:n_tune], n_tune, H, W) \
         if n_tune >= 4 and not args.no_autotune else None
 

@@ -215,14 +215,14 @@ sm_status sm_texel_res_from_gamma(sm_mesh *m, const sm_intrinsics *d_K, const do
 
 /* Autotuner of the frames per launch (the paper has no counterpart: a
  * throughput setting of this implementation).  Fuses the given frames once per
- * candidate batch size (multiples of 4 up to 64 frames, both z-buffer slots
- * within 512 MB), times each on `stream` with CUDA events, and keeps the
+ * candidate batch size (multiples of 4 up to 128 frames, both z-buffer slots
+ * within 1 GB), times each on `stream` with CUDA events, and keeps the
  * fastest per-frame time for frames of H x W pixels: later calls on this mesh
  * with that frame size launch that many frames at a time (results do not
  * depend on it).  Synchronises `stream`; resets the accumulators (P and
  * counts are zero afterwards).  *best_out, if not NULL, receives the choice.
  *   d_probs ...  N >= 4 frames as for sm_fuse_frames (a representative
- *                sample: 2-4 x 64 frames is plenty).
+ *                sample: 2-4 x 128 frames is plenty).
  * Errors: SM_ERR_INVALID_ARG, SM_ERR_OOM, SM_ERR_CUDA. */
 sm_status sm_autotune_batch(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
                             const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N, int32_t H, int32_t W,

@@ -115,7 +115,7 @@ int batch_frames(const sm_mesh *m, int64_t npix, int N, bool tuned = true)
         if (Bi < B) B = Bi;
     }
     if (B < 1) B = 1;
-    if (B > 64) B = 64;
+    if (B > 128) B = 128;
     // multiples of 4 frames keep every batch's probability, scale and row-map
     // base 16-byte aligned for the bulk copies (4 H W c bytes is a multiple
     // of 16 for c % 4 == 0)
@@ -533,8 +533,8 @@ sm_status sm_autotune_batch(sm_mesh *m, const void *d_probs, sm_dtype dtype, con
     float best_ms = 0.0f;
     const int saved_B = m->tuned_B;
     const int64_t saved_npix = m->tuned_npix;
-    // candidates: multiples of 4 frames whose two z-buffer slots stay within 512 MB
-    for (int B = 4; B <= 64 && B <= N && (int64_t)B * npix * 16 <= (512ll << 20); B += 4) {
+    // candidates: multiples of 4 frames whose two z-buffer slots stay within 1 GB
+    for (int B = 4; B <= 128 && B <= N && (int64_t)B * npix * 16 <= (1024ll << 20); B += 4) {
         m->tuned_B = B;
         m->tuned_npix = npix;
         const int n = (N / B) * B;  // whole launches only
