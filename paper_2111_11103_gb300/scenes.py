@@ -25,19 +25,32 @@ class SceneJob:
     labels_out: torch.Tensor | None = None
 
 
+_POOLS: dict = {}
+
+
+def _pool(n: int) -> list:
+    """n streams of the current device, created once and reused (so that a
+    call can be captured into a CUDA graph after a first eager call)."""
+    key = (torch.cuda.current_device(), n)
+    if key not in _POOLS:
+        _POOLS[key] = [torch.cuda.Stream() for _ in range(n)]
+    return _POOLS[key]
+
+
 def fuse_scenes(jobs: list[SceneJob], streams: int = 4) -> None:
     """Fuses (and, where an output is given, normalises) every scene; scene i
     runs on stream i % streams.  The streams start after the work already on
     the current stream and the current stream waits for all of them, so the
-    call orders like one sequence of calls on the current stream.  A mesh must
-    appear in one job only."""
+    call orders like one sequence of calls on the current stream, and it can
+    be captured into a CUDA graph (after one eager call that creates the
+    streams).  A mesh must appear in one job only."""
     from . import labelfuse as lf
     if len({j.mesh for j in jobs}) != len(jobs):
         raise ValueError("a mesh may appear in one job only")
     if not jobs:
         return
     cur = torch.cuda.current_stream()
-    pool = [torch.cuda.Stream() for _ in range(max(1, min(streams, len(jobs))))]
+    pool = _pool(max(1, min(streams, len(jobs))))
     for st in pool:
         st.wait_stream(cur)
     for i, j in enumerate(jobs):
@@ -48,6 +61,8 @@ def fuse_scenes(jobs: list[SceneJob], streams: int = 4) -> None:
             lf.sm_normalise(j.mesh, j.dist_out, j.labels_out, st)
     for st in pool:
         cur.wait_stream(st)
+    if torch.cuda.is_current_stream_capturing():
+        return  # a graph keeps its tensors alive itself
     for j in jobs:  # the caller's tensors were used on the pool's streams
         for t in (j.probs, j.K, j.cam_to_world, j.scale, j.idmap_out, j.dist_out, j.labels_out):
             if t is not None:

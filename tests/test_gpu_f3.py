@@ -133,6 +133,20 @@ def test_scenes_side_by_side_match_one_by_one(dev):
             assert_acc_close(acc, ref.acc.astype(np.float64))
         with pytest.raises(ValueError):
             fuse_scenes([jobs[0], jobs[0]])
+        # the same multi-stream submission captured into one CUDA graph and replayed
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for j in jobs:
+                lf.sm_reset(j.mesh)
+            fuse_scenes(jobs, streams=3)
+        for _ in range(2):
+            g.replay()
+        torch.cuda.synchronize()
+        for j, ref, (scene, _) in zip(jobs, refs, specs):
+            acc, cnt = _state(lf, j.mesh, ref.n_x, scene.n_classes, dev)
+            lf.sm_check(j.mesh)
+            assert np.array_equal(cnt.astype(np.int64), ref.cnt)
+            assert_acc_close(acc, ref.acc.astype(np.float64))
     finally:
         for m in meshes:
             lf.sm_mesh_free(m)
