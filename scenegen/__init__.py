@@ -76,8 +76,10 @@ def _grid_rect(rect: Rect, nu: int, nv: int, v_base: int):
     v11 = idx[1:, 1:].ravel()
     tris = np.stack([np.stack([v00, v10, v11], 1), np.stack([v00, v11, v01], 1)], 1).reshape(-1, 3)
     pu, pv = rect.classes.shape
-    qa = np.arange(nu) // (nu // pu)
-    qb = np.arange(nv) // (nv // pv)
+    # the class of the patch under each quad's centre (the same as quad // (nu / pu)
+    # when the grid refines the patches; a grid that ignores them cuts across patches)
+    qa = np.minimum(((np.arange(nu) + 0.5) * pu / nu).astype(np.int64), pu - 1)
+    qb = np.minimum(((np.arange(nv) + 0.5) * pv / nv).astype(np.int64), pv - 1)
     cls = rect.classes[qa[:, None], qb[None, :]].ravel()
     gt = np.repeat(cls, 2)
     return verts, tris, gt
@@ -115,8 +117,11 @@ def _zipf_classes(rng, shape, n_classes):
 
 
 def paper_room(seed: int = BASE_SEED + 1, target_faces: int = 500_000, n_boxes: int = 20,
-               n_classes: int = 40, size=(6.0, 5.0, 3.0)) -> Scene:
-    """Procedural room with box furniture, ~target_faces triangles (+-1 %)."""
+               n_classes: int = 40, size=(6.0, 5.0, 3.0), aligned: bool = True) -> Scene:
+    """Procedural room with box furniture, ~target_faces triangles (+-1 %).
+    aligned=False grids every rectangle without regard to its class patches
+    (as a simplified reconstruction would): coarse grids then have triangles
+    that straddle class boundaries (about +-3 % of target_faces)."""
     rng = np.random.default_rng(seed)
     Lx, Ly, Lz = size
     o = np.array
@@ -150,6 +155,9 @@ def paper_room(seed: int = BASE_SEED + 1, target_faces: int = 500_000, n_boxes: 
         out = []
         for r in rects:
             pu, pv = r.classes.shape
+            if not aligned:
+                out.append((max(1, int(round(np.linalg.norm(r.eu) / hq))), max(1, int(round(np.linalg.norm(r.ev) / hq)))))
+                continue
             qu = max(1, int(round(np.linalg.norm(r.eu) / pu / hq)))
             qv = max(1, int(round(np.linalg.norm(r.ev) / pv / hq)))
             out.append((pu * qu, pv * qv))
@@ -167,6 +175,8 @@ def paper_room(seed: int = BASE_SEED + 1, target_faces: int = 500_000, n_boxes: 
         else:
             hi = mid
     hq = min((lo, hi), key=lambda q: abs(nfaces(q) - target_faces))
+    if not aligned:
+        return _build(rects, quads_for(hq), n_classes)
     per = [[nu // r.classes.shape[0], nv // r.classes.shape[1]] for r, (nu, nv) in zip(rects, quads_for(hq))]
 
     def total():
