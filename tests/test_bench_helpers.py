@@ -1,0 +1,40 @@
+"""Host helpers of the benchmark: the storage-form quantiser (per-pixel scale,
+BF16 / E4M3 codes) and the lookup of the committed scatter profile."""
+import importlib.util
+import os
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_quantise_scales_and_codes():
+    b = _bench()
+    g = torch.Generator().manual_seed(0)
+    probs = torch.softmax(torch.randn((3, 5, 7, 40), generator=g), -1)
+    for kind, top in (("bf16", 1.0), ("fp8_e4m3", 448.0)):
+        q, scale = b.quantise(probs, kind)
+        assert q.shape == probs.shape and scale.shape == probs.shape[:-1]
+        np.testing.assert_allclose(scale.numpy(), probs.amax(-1).numpy() / top, rtol=1e-7)
+        deq = (q.float() * scale[..., None]).numpy()
+        p, s = probs.numpy(), scale[..., None].numpy()
+        if kind == "bf16":  # 8 significant bits: half an ulp is 2^-8 relative
+            bound = 2.0 ** -8 * p + 1e-12
+        else:  # E4M3: 4 significant bits (2^-4 relative), subnormal step 2^-9 of the scale
+            bound = 2.0 ** -4 * p + 2.0 ** -10 * s + 1e-12
+        assert np.all(np.abs(deq - p) <= bound)
+        assert float(q.float().amax()) == top  # the largest class maps to the top code exactly
+
+
+def test_scatter_traffic_lookup_follows_the_source_hash():
+    b = _bench()
+    tpf = b.scatter_traffic_per_frame()
+    assert tpf is not None and 5.0e7 < tpf < 6.0e7  # bytes per 640 x 480 x 40 frame
