@@ -50,6 +50,12 @@ def test_bf16_rounding_matches_torch():
     x = (rng.normal(0, 1, 20000) * np.exp(rng.uniform(-20, 20, 20000))).astype(np.float32)
     ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(cf.bf16_round(x), ref)
+    # exact ties (low half 0x8000) go to the even neighbour; 0x7FFF / 0x8001 round down / up
+    hi = rng.integers(0x0080, 0x7F00, 4000, dtype=np.uint32) << 16
+    for low in (0x8000, 0x7FFF, 0x8001):
+        t = (hi | np.uint32(low)).view(np.float32)
+        ref = torch.from_numpy(t.copy()).to(torch.bfloat16).to(torch.float64).numpy()
+        assert np.array_equal(cf.bf16_round(t), ref)
 
 
 def test_features_fronto_parallel_wall(ora):
@@ -73,6 +79,9 @@ def test_features_fronto_parallel_wall(ora):
     assert X[5, 5, 3] == 0.0
     assert X[3, 4, 4] == 3 / 7 and X[9, 13, 4] == 4 / 7  # min(4,3,13,10) = 3; min(13,9,4,4) = 4; / (14/2)
     assert np.all(X[~cov] == 0)
+    # the view-angle feature does not depend on the winding (the sign of the normal)
+    X2, face2 = cf.features(ora, V, F[:, [0, 2, 1]], K, np.eye(4), probs, H, W)
+    assert np.array_equal(face2, face) and np.array_equal(X2.reshape(H, W, 5), X)
 
 
 def test_targets_by_hand():

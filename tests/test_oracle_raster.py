@@ -60,6 +60,38 @@ def test_hand_counted_pixels_exact(ora):
     assert np.array_equal(idmap >= 0, (xs + ys < 8))
 
 
+@pytest.mark.parametrize("frac,expect_le", [(0.6, True), (0.4, False)])
+def test_snap_rounds_to_nearest(ora, frac, expect_le):
+    """Vertices snap to the nearest 1/256 pixel (Sec. 3.3.1 reading).  The legs
+    of the right triangle (0,0), (a,0), (0,a) are a = 5 + frac/256 pixels:
+    frac = 0.6 snaps the hypotenuse to 1281/256, so the six centres with
+    x + y = 5 are inside (21 pixels); frac = 0.4 snaps it onto them (1280/256),
+    where the bottom-right edge excludes them (15 pixels)."""
+    a = 5 + frac / 256
+    V = np.array([[0, 0, 1], [a, 0, 1], [0, a, 1]], dtype=np.float64)
+    K, T = _pixel_camera()
+    idmap = ora.render_frame(ora.Mesh(V, [[0, 1, 2]]), K, T, 10, 10)
+    ys, xs = np.mgrid[0:10, 0:10]
+    expect = (xs + ys <= 5) if expect_le else (xs + ys < 5)
+    assert int(expect.sum()) == (21 if expect_le else 15)
+    assert np.array_equal(idmap >= 0, expect)
+
+
+def test_sequence_render_matches_frames(ora):
+    """The threaded row-map renderer gives every frame's own row map, for one
+    and for several threads."""
+    import scenegen as sg
+    sc = sg.tiny_room()
+    cams = sg.circle_poses()
+    mesh = ora.Mesh(sc.vertices, sc.faces)
+    one = np.stack([ora.render_frame(mesh, cams.K[i], cams.cam_to_world[i], cams.H, cams.W)
+                    for i in range(cams.K.shape[0])])
+    assert len({one[i].tobytes() for i in range(len(one))}) == len(one)  # the views differ
+    for nthreads in (1, 3):
+        seq = ora.render_sequence(mesh, cams.K, cams.cam_to_world, cams.H, cams.W, nthreads=nthreads)
+        assert np.array_equal(seq, one)
+
+
 def test_closed_form_wall(ora):
     """A fronto-parallel wall at depth 2: the covered rectangle follows from the
     intrinsics (edges at x = 3.25, 13.25 and y = 2.5, 10.0; the bottom edge is
@@ -189,12 +221,17 @@ def test_brute_force_ray_cast(ora, seed):
     assert (best >= 0).sum() > 50  # the scene is actually visible
 
 
-def test_texel_rows_on_subdivided_triangle(ora):
-    """A large triangle with s = 6 seen head-on: every one of its 21 texels is
-    hit (Fig. 3), the rows stay inside [id_t, id_t + 21), and each pixel's texel
-    is the cell of its uv coordinates computed independently in binary64."""
+@pytest.mark.parametrize("flip", [False, True])
+def test_texel_rows_on_subdivided_triangle(ora, flip):
+    """A large triangle with s = 6 seen head-on, in both windings (one of them
+    goes through the renderer's orientation fix-up): every one of its 21
+    texels is hit (Fig. 3), the rows stay inside [id_t, id_t + 21), and each
+    pixel's texel is the cell of its uv coordinates computed independently in
+    binary64 from the face's own vertex order (u toward its second vertex
+    after the uv origin, v toward its third)."""
     V = np.array([[0, 0, 1.0], [60, 0, 1.0], [0, 60, 1.0], [70, 70, 1.0], [75, 70, 1.0], [70, 75, 1.0]])
-    faces = np.array([[3, 4, 5], [0, 1, 2]])
+    tri = [0, 2, 1] if flip else [0, 1, 2]
+    faces = np.array([[3, 4, 5], tri])
     s = np.array([1, 6], dtype=np.int32)
     mesh = ora.Mesh(V, faces, texel_res=s)
     assert mesh.n_x == 22 and list(mesh.id_t) == [0, 1, 22]
@@ -203,18 +240,19 @@ def test_texel_rows_on_subdivided_triangle(ora):
     rows = idmap[fmap == 1]
     assert set(rows.tolist()) == set(range(1, 22))
     o = mesh.origin[1]
-    assert o == 0  # right angle at vertex 0
+    assert o == 0  # right angle at the face's first vertex (V0) in both windings
     ys, xs = np.nonzero(fmap == 1)
     # barycentric coordinates in binary64 (affine: all depths equal)
-    P0, P1, P2 = V[0, :2], V[1, :2], V[2, :2]
+    P0, P1, P2 = (V[tri[(o + k) % 3], :2] for k in range(3))
     M = np.stack([P1 - P0, P2 - P0], 1)
-    uv = np.linalg.solve(M, (np.stack([xs, ys], 1) - P0).T).T   # weights of vertex 1 and 2
+    uv = np.linalg.solve(M, (np.stack([xs, ys], 1) - P0).T).T   # weights of the 2nd and 3rd vertex
     u, v = uv[:, 0], uv[:, 1]
     i = np.minimum(np.floor(6 * u), 5).astype(int)
     j = np.minimum(np.floor(6 * v), 5 - i).astype(int)
     near_border = (np.abs(6 * u - np.round(6 * u)) < 1e-4) | (np.abs(6 * v - np.round(6 * v)) < 1e-4)
     expect = 1 + (i + j) * (i + j + 1) // 2 + j
     assert np.all((idmap[ys, xs] == expect) | near_border)
+    assert (~near_border).sum() > 1000
 
 
 def test_s1_equals_face_mode(ora):
