@@ -65,3 +65,77 @@ def test_no_cpu_fallback_in_binding():
     for f in os.listdir(os.path.join(ROOT, "paper_2111_11103_gb300")):
         if f.endswith(".py"):
             assert "import oracle" not in open(os.path.join(ROOT, "paper_2111_11103_gb300", f)).read()
+
+
+def _mesh_functions():
+    """Entry points whose first parameter is the mesh handle."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return sorted(set(re.findall(r"\b(sm_[a-z_0-9]+)\s*\(\s*(?:const\s+)?sm_mesh\s*\*", src)))
+
+
+def test_every_mesh_call_rejects_a_null_handle(libpath):
+    """Each call that takes a mesh answers SM_ERR_INVALID_ARG for a NULL one,
+    on the host, before any CUDA call (so this runs without a GPU)."""
+    from paper_2111_11103_gb300 import labelfuse as lf
+    L = lf.lib()
+    n64, ms, b = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int32()
+    calls = {
+        "sm_fuse_frames": (None, None, 0, None, None, None, 1, 4, 4, None, None),
+        "sm_fuse_frames_weighted": (None, None, 0, None, None, None, 0, 4, 4, None, None, None),
+        "sm_normalise": (None, None, None, None),
+        "sm_render_labels": (None, None, None, 1, 4, 4, None, None, None),
+        "sm_render_idmap": (None, None, 16, None, None),
+        "sm_reset": (None, None),
+        "sm_read_state": (None, None, None, None),
+        "sm_load_state": (None, None, None, None),
+        "sm_check": (None, None),
+        "sm_profile_enable": (None, 1),
+        "sm_profile_read": (None, 0, ctypes.byref(n64), ctypes.byref(ms)),
+        "sm_fuse_render_host": (None, None, 0, None, None, None, 1, 4, 4, None, None),
+        "sm_set_weight_mix": (None, 0.5),
+        "sm_texel_res_from_gamma": (None, None, None, 1, 4, 4, 0.5, None, None, None),
+        "sm_autotune_batch": (None, None, 0, None, None, None, 1, 4, 4, ctypes.byref(b), None),
+        "sm_conf_features": (None, None, 0, None, None, None, 1, 4, 4, None, None, None),
+        "sm_conf_targets": (None, None, 0, None, None, 16, None, None),
+    }
+    queries = {"sm_num_rows", "sm_num_classes", "sm_mesh_free"}  # -1, -1 and a no-op for NULL
+    assert sorted(set(calls) | queries) == _mesh_functions()
+    for name, args in calls.items():
+        assert getattr(L, name)(*args) == 1, name
+        assert "NULL" in lf.sm_last_error(), (name, lf.sm_last_error())
+
+
+def test_argument_ranges_rejected_on_host(libpath):
+    """Sizes, enums and rates outside the documented ranges are rejected before
+    any CUDA call; empty work returns SM_OK without touching the device."""
+    from paper_2111_11103_gb300 import labelfuse as lf
+    L = lf.lib()
+    h = ctypes.c_void_p()
+    P = ctypes.c_void_p(16)  # never dereferenced: validation fails first
+    up = L.sm_mesh_upload
+    assert up(None, 3, None, 1, None, 4, 0, 0, None, None) == 1                 # out NULL
+    assert up(None, -1, None, 0, None, 4, 0, 0, None, ctypes.byref(h)) == 1     # V < 0
+    assert up(None, 3, None, 1, None, 4, 0, 0, None, ctypes.byref(h)) == 1      # F > 0, NULL arrays
+    assert up(P, 3, P, 1 << 31, None, 4, 0, 0, None, ctypes.byref(h)) == 1      # F >= 2^31
+    assert up(P, 3, P, 1, None, 0, 0, 0, None, ctypes.byref(h)) == 1            # c = 0
+    assert up(P, 3, P, 1, None, 4, -1, 0, None, ctypes.byref(h)) == 1           # rule
+    assert up(P, 3, P, 1, None, 4, 0, 2, None, ctypes.byref(h)) == 1            # weight
+    assert not h.value
+    nr = L.sm_render_rows_noalloc
+    assert nr(P, 3, P, 1, P, P, -1, 4, 4, P, None) == 1                         # N < 0
+    assert nr(P, 3, P, 1, P, P, 1, 0, 4, P, None) == 1                          # H = 0
+    assert nr(P, 3, P, 1, P, P, 1, 4, 16385, P, None) == 1                      # W > 16384
+    assert nr(P, 3, P, 1, P, P, 1, 1296, 1297, P, None) == 1                    # > 1.5 Mi pixels
+    assert nr(P, 3, P, 1, P, P, 1025, 4, 4, P, None) == 1                       # > 1024 frames
+    assert nr(P, -3, P, 1, P, P, 1, 4, 4, P, None) == 1                         # V < 0
+    assert nr(P, 3, P, 1, None, P, 1, 4, 4, P, None) == 1                       # K NULL
+    assert nr(None, 0, None, 0, None, None, 0, 4, 4, None, None) == 0           # N = 0: nothing to do
+    assert L.sm_conf_forward(P, P, -1, P, None) == 1
+    assert L.sm_conf_forward(None, None, 0, None, None) == 0                    # n = 0: nothing to do
+    assert L.sm_conf_forward(None, P, 5, P, None) == 1
+    assert L.sm_conf_train_step(P, P, P, -1, 0.1, P, P, None) == 1
+    assert L.sm_conf_train_step(P, P, P, 4, float("nan"), P, P, None) == 1
+    assert L.sm_conf_train_step(P, P, P, 4, -0.5, P, P, None) == 1
+    assert L.sm_conf_train_step(P, None, P, 4, 0.1, P, P, None) == 1
+    assert L.sm_host_alloc(0, ctypes.byref(h)) == 1
+    assert L.sm_host_free(None) == 0
