@@ -214,9 +214,10 @@ sm_status sm_texel_res_from_gamma(sm_mesh *m, const sm_intrinsics *d_K, const do
                                   void *stream);
 
 /* Autotuner of the frames per launch (the paper has no counterpart: a
- * throughput setting of this implementation).  Fuses the given frames once per
+ * throughput setting of this implementation).  Fuses the given frames twice per
  * candidate batch size (multiples of 4 up to 128 frames, both z-buffer slots
- * within 1 GB), times each on `stream` with CUDA events, and keeps the
+ * within 1 GB; the first pass sizes the scratch buffers), times the second on
+ * `stream` with CUDA events, and keeps the
  * fastest per-frame time for frames of H x W pixels: later calls on this mesh
  * with that frame size launch that many frames at a time (results do not
  * depend on it).  Synchronises `stream`; resets the accumulators (P and

@@ -102,8 +102,8 @@ sm_status grow(T **buf, int64_t *cap, int64_t need, cudaStream_t s, int fill, co
 
 size_t dtype_size(sm_dtype d) { return d == SM_F32 ? 4 : (d == SM_BF16 ? 2 : 1); }
 
-// Frames per batch: a batch's 64-bit z-buffers take up to ~48 MB (16 frames
-// of 640 x 480).  Longer batches keep the mostly-culled raster launches and
+// Frames per batch: a batch's 64-bit z-buffers take up to ~48 MB (20 frames
+// of 640 x 480) unless the autotuner chose another length.  Longer batches keep the mostly-culled raster launches and
 // the streaming scatter launches long enough to fill the GPU, which matters
 // more than keeping both z-buffer slots in L2; the per-frame row histograms
 // of the image weights stay within ~512 MB.
