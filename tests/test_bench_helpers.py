@@ -38,3 +38,9 @@ def test_scatter_traffic_lookup_follows_the_source_hash():
     b = _bench()
     tpf = b.scatter_traffic_per_frame()
     assert tpf is not None and 5.0e7 < tpf < 6.0e7  # bytes per 640 x 480 x 40 frame
+
+
+def test_l2_note_states_the_resident_size():
+    import bench
+    assert bench.l2_note(49_152_000_000).startswith("inputs larger than L2 (49.2 GB")
+    assert "NOT larger than L2" in bench.l2_note(100 << 20)
