@@ -6,6 +6,14 @@ integer addresses), the stream as a ``torch.cuda.Stream`` (default: the
 current stream).  A non-OK status raises :class:`LabelFuseError` carrying
 ``sm_last_error()``.  There is no fallback: if the library is missing or was
 not built, :func:`lib` raises.
+
+A C entry point cannot see how large a buffer behind a pointer is, so the
+binding checks every tensor argument before the call: contiguous, on the side
+the call reads it from (CUDA, or host memory for ``sm_fuse_render_host``), and
+at least as many bytes as the call reads or writes through it.  A violation
+raises :class:`LabelFuseError` with ``SM_ERR_INVALID_ARG`` and nothing is
+enqueued, so a wrong shape cannot make a kernel touch memory outside the
+tensor.  Raw integer addresses are passed through unchecked.
 """
 from __future__ import annotations
 
@@ -20,6 +28,7 @@ SM_WEIGHT = {"pixel": 0, "image": 1}
 SM_DTYPE = {"f32": 0, "bf16": 1, "fp8_e4m3": 2}
 SM_KERNEL = {"project": 0, "raster": 1, "resolve": 2, "count": 3, "scatter": 4, "normalise": 5, "render": 6}
 SM_OK = 0
+SM_ERR_INVALID_ARG = 1
 SM_MAX_CLASSES = 254
 SYMBOLS = ["sm_mesh_upload", "sm_fuse_frames", "sm_normalise", "sm_render_labels", "sm_render_idmap", "sm_reset",
            "sm_read_state", "sm_load_state", "sm_check", "sm_num_rows", "sm_num_classes", "sm_mesh_free",
@@ -97,13 +106,37 @@ def _check(status: int):
         raise LabelFuseError(status, lib().sm_last_error().decode() or lib().sm_status_string(status).decode())
 
 
-def _ptr(t):
-    """Device address of a tensor (or passes an int / None through)."""
-    if t is None:
-        return None
-    if isinstance(t, int):
+def _arg(t, name: str, nbytes: int = 0, host: bool = False):
+    """Address of a buffer argument after the checks described above: a
+    tensor must be contiguous, a CUDA tensor (a CPU tensor if host), and hold
+    at least nbytes.  None and raw integer addresses pass through."""
+    if t is None or isinstance(t, int):
         return t
+    if not t.is_contiguous():
+        raise LabelFuseError(SM_ERR_INVALID_ARG, f"{name} is not contiguous")
+    if bool(t.is_cuda) == host:
+        raise LabelFuseError(SM_ERR_INVALID_ARG, f"{name} must be a {'host (CPU)' if host else 'CUDA'} tensor")
+    have = t.numel() * t.element_size()
+    if have < nbytes:
+        raise LabelFuseError(SM_ERR_INVALID_ARG, f"{name} holds {have} bytes; the call needs {nbytes}")
     return t.data_ptr()
+
+
+_ESIZE = {0: 4, 1: 2, 2: 1}  # bytes per stored probability: F32, BF16, FP8 E4M3
+
+
+def _classes(mesh) -> int:
+    """Classes of the mesh (0 for a NULL handle: the library rejects it)."""
+    return max(0, int(lib().sm_num_classes(mesh))) if mesh else 0
+
+
+def _frames_args(mesh, probs, dt: int, scale, K, cam_to_world, N: int, H: int, W: int, host: bool = False):
+    """Checked addresses of the predictions, scales and cameras of N frames."""
+    n, npix = max(0, int(N)), max(0, int(H)) * max(0, int(W))
+    return (_arg(probs, "probs", n * npix * _classes(mesh) * _ESIZE.get(dt, 1), host),
+            _arg(scale, "scale", 4 * n * npix, host),
+            _arg(K, "K", 32 * n, host),
+            _arg(cam_to_world, "cam_to_world", 128 * n, host))
 
 
 def _stream(stream):
@@ -125,35 +158,46 @@ def sm_mesh_upload(vertices, faces, texel_res, n_classes: int, rule="sum", weigh
     h = ctypes.c_void_p()
     V = int(vertices.shape[0]) if vertices is not None else 0
     F = int(faces.shape[0]) if faces is not None else 0
-    _check(lib().sm_mesh_upload(_ptr(vertices), V, _ptr(faces), F, _ptr(texel_res), int(n_classes),
+    _check(lib().sm_mesh_upload(_arg(vertices, "vertices", 12 * V), V, _arg(faces, "faces", 12 * F),
+                                F, _arg(texel_res, "texel_res", 4 * F), int(n_classes),
                                 _enum(SM_RULE, rule), _enum(SM_WEIGHT, weight), _stream(stream), ctypes.byref(h)))
     return h.value
 
 
 def sm_fuse_frames(mesh: int, probs, dtype, scale, K, cam_to_world, N: int, H: int, W: int, idmap_out=None,
                    stream=None):
-    _check(lib().sm_fuse_frames(mesh, _ptr(probs), _enum(SM_DTYPE, dtype), _ptr(scale), _ptr(K), _ptr(cam_to_world),
-                                int(N), int(H), int(W), _ptr(idmap_out), _stream(stream)))
+    dt = _enum(SM_DTYPE, dtype)
+    p, sc, k, t = _frames_args(mesh, probs, dt, scale, K, cam_to_world, N, H, W)
+    _check(lib().sm_fuse_frames(mesh, p, dt, sc, k, t, int(N), int(H), int(W),
+                                _arg(idmap_out, "idmap_out", 4 * max(0, N * H * W)), _stream(stream)))
 
 
 def sm_normalise(mesh: int, dist_out=None, labels_out=None, stream=None):
-    _check(lib().sm_normalise(mesh, _ptr(dist_out), _ptr(labels_out), _stream(stream)))
+    n_x = max(0, sm_num_rows(mesh)) if mesh else 0
+    _check(lib().sm_normalise(mesh, _arg(dist_out, "dist_out", 4 * n_x * _classes(mesh)),
+                              _arg(labels_out, "labels_out", 4 * n_x), _stream(stream)))
 
 
 def sm_render_labels(mesh: int, K, cam_to_world, N: int, H: int, W: int, labels_out, idmap_out=None, stream=None):
-    _check(lib().sm_render_labels(mesh, _ptr(K), _ptr(cam_to_world), int(N), int(H), int(W), _ptr(labels_out),
-                                  _ptr(idmap_out), _stream(stream)))
+    n = max(0, N * H * W)
+    _check(lib().sm_render_labels(mesh, _arg(K, "K", 32 * max(0, N)), _arg(cam_to_world, "cam_to_world", 128 * max(0, N)),
+                                  int(N), int(H), int(W), _arg(labels_out, "labels_out", n),
+                                  _arg(idmap_out, "idmap_out", 4 * n), _stream(stream)))
 
 
 def sm_render_idmap(mesh: int, idmap, n_pixels: int, labels_out, stream=None):
-    _check(lib().sm_render_idmap(mesh, _ptr(idmap), int(n_pixels), _ptr(labels_out), _stream(stream)))
+    n = max(0, int(n_pixels))
+    _check(lib().sm_render_idmap(mesh, _arg(idmap, "idmap", 4 * n), int(n_pixels), _arg(labels_out, "labels_out", n),
+                                 _stream(stream)))
 
 
 def sm_fuse_render_host(mesh: int, probs, dtype, scale, K, cam_to_world, N: int, H: int, W: int, labels_out,
                         stream=None):
     """Fuse + normalise + render with HOST tensors (pin them for overlap)."""
-    _check(lib().sm_fuse_render_host(mesh, _ptr(probs), _enum(SM_DTYPE, dtype), _ptr(scale), _ptr(K),
-                                     _ptr(cam_to_world), int(N), int(H), int(W), _ptr(labels_out), _stream(stream)))
+    dt = _enum(SM_DTYPE, dtype)
+    p, sc, k, t = _frames_args(mesh, probs, dt, scale, K, cam_to_world, N, H, W, host=True)
+    _check(lib().sm_fuse_render_host(mesh, p, dt, sc, k, t, int(N), int(H), int(W),
+                                     _arg(labels_out, "labels_out", max(0, N * H * W), host=True), _stream(stream)))
 
 
 def sm_set_weight_mix(mesh: int, alpha: float):
@@ -162,44 +206,64 @@ def sm_set_weight_mix(mesh: int, alpha: float):
 
 def sm_texel_res_from_gamma(mesh: int, K, cam_to_world, N: int, H: int, W: int, gamma: float, texel_res_out,
                             area_out=None, stream=None):
-    _check(lib().sm_texel_res_from_gamma(mesh, _ptr(K), _ptr(cam_to_world), int(N), int(H), int(W), float(gamma),
-                                         _ptr(area_out), _ptr(texel_res_out), _stream(stream)))
+    # the outputs hold one value per triangle; the triangle count is not
+    # visible through the handle, so only their placement is checked
+    _check(lib().sm_texel_res_from_gamma(mesh, _arg(K, "K", 32 * max(0, N)),
+                                         _arg(cam_to_world, "cam_to_world", 128 * max(0, N)), int(N), int(H), int(W),
+                                         float(gamma), _arg(area_out, "area_out"), _arg(texel_res_out, "texel_res_out"),
+                                         _stream(stream)))
 
 
 def sm_autotune_batch(mesh: int, probs, dtype, scale, K, cam_to_world, N: int, H: int, W: int, stream=None) -> int:
     """Chooses the frames per launch for H x W frames by timing; returns it."""
     best = ctypes.c_int32(0)
-    _check(lib().sm_autotune_batch(mesh, _ptr(probs), _enum(SM_DTYPE, dtype), _ptr(scale), _ptr(K),
-                                   _ptr(cam_to_world), int(N), int(H), int(W), ctypes.byref(best), _stream(stream)))
+    dt = _enum(SM_DTYPE, dtype)
+    p, sc, k, t = _frames_args(mesh, probs, dt, scale, K, cam_to_world, N, H, W)
+    _check(lib().sm_autotune_batch(mesh, p, dt, sc, k, t, int(N), int(H), int(W), ctypes.byref(best),
+                                   _stream(stream)))
     return best.value
 
 
 def sm_fuse_frames_weighted(mesh: int, probs, dtype, scale, K, cam_to_world, N: int, H: int, W: int, weights,
                             idmap_out=None, stream=None):
-    _check(lib().sm_fuse_frames_weighted(mesh, _ptr(probs), _enum(SM_DTYPE, dtype), _ptr(scale), _ptr(K),
-                                         _ptr(cam_to_world), int(N), int(H), int(W), _ptr(weights), _ptr(idmap_out),
+    dt = _enum(SM_DTYPE, dtype)
+    p, sc, k, t = _frames_args(mesh, probs, dt, scale, K, cam_to_world, N, H, W)
+    n = max(0, N * H * W)
+    _check(lib().sm_fuse_frames_weighted(mesh, p, dt, sc, k, t, int(N), int(H), int(W),
+                                         _arg(weights, "weights", 4 * n), _arg(idmap_out, "idmap_out", 4 * n),
                                          _stream(stream)))
 
 
 def sm_conf_features(mesh: int, probs, dtype, scale, K, cam_to_world, N: int, H: int, W: int, feat_out, rows_out,
                      stream=None):
-    _check(lib().sm_conf_features(mesh, _ptr(probs), _enum(SM_DTYPE, dtype), _ptr(scale), _ptr(K),
-                                  _ptr(cam_to_world), int(N), int(H), int(W), _ptr(feat_out), _ptr(rows_out),
+    dt = _enum(SM_DTYPE, dtype)
+    p, sc, k, t = _frames_args(mesh, probs, dt, scale, K, cam_to_world, N, H, W)
+    n = max(0, N * H * W)
+    _check(lib().sm_conf_features(mesh, p, dt, sc, k, t, int(N), int(H), int(W),
+                                  _arg(feat_out, "feat_out", 4 * SM_CONF_FEATURES * n), _arg(rows_out, "rows_out", 4 * n),
                                   _stream(stream)))
 
 
 def sm_conf_targets(mesh: int, probs, dtype, scale, rows, n_pixels: int, target_out, stream=None):
-    _check(lib().sm_conf_targets(mesh, _ptr(probs), _enum(SM_DTYPE, dtype), _ptr(scale), _ptr(rows),
-                                 int(n_pixels), _ptr(target_out), _stream(stream)))
+    dt = _enum(SM_DTYPE, dtype)
+    n = max(0, int(n_pixels))
+    _check(lib().sm_conf_targets(mesh, _arg(probs, "probs", n * _classes(mesh) * _ESIZE.get(dt, 1)), dt,
+                                 _arg(scale, "scale", 4 * n), _arg(rows, "rows", 4 * n), int(n_pixels),
+                                 _arg(target_out, "target_out", 4 * n), _stream(stream)))
 
 
 def sm_conf_forward(params, feat, n: int, w_out, stream=None):
-    _check(lib().sm_conf_forward(_ptr(params), _ptr(feat), int(n), _ptr(w_out), _stream(stream)))
+    m = max(0, int(n))
+    _check(lib().sm_conf_forward(_arg(params, "params", 4 * SM_CONF_PARAMS), _arg(feat, "feat", 4 * SM_CONF_FEATURES * m),
+                                 int(n), _arg(w_out, "w_out", 4 * m), _stream(stream)))
 
 
 def sm_conf_train_step(params, feat, target, n: int, lr: float, grad_out, loss_out, stream=None):
-    _check(lib().sm_conf_train_step(_ptr(params), _ptr(feat), _ptr(target), int(n), float(lr), _ptr(grad_out),
-                                    _ptr(loss_out), _stream(stream)))
+    m = max(0, int(n))
+    _check(lib().sm_conf_train_step(_arg(params, "params", 4 * SM_CONF_PARAMS),
+                                    _arg(feat, "feat", 4 * SM_CONF_FEATURES * m), _arg(target, "target", 4 * m), int(n),
+                                    float(lr), _arg(grad_out, "grad_out", 4 * SM_CONF_PARAMS),
+                                    _arg(loss_out, "loss_out", 4), _stream(stream)))
 
 
 def sm_host_alloc(nbytes: int) -> int:
@@ -244,11 +308,15 @@ def sm_reset(mesh: int, stream=None):
 
 
 def sm_read_state(mesh: int, acc_out=None, cnt_out=None, stream=None):
-    _check(lib().sm_read_state(mesh, _ptr(acc_out), _ptr(cnt_out), _stream(stream)))
+    n_x = max(0, sm_num_rows(mesh)) if mesh else 0
+    _check(lib().sm_read_state(mesh, _arg(acc_out, "acc_out", 4 * n_x * _classes(mesh)),
+                               _arg(cnt_out, "cnt_out", 4 * n_x), _stream(stream)))
 
 
 def sm_load_state(mesh: int, acc, cnt, stream=None):
-    _check(lib().sm_load_state(mesh, _ptr(acc), _ptr(cnt), _stream(stream)))
+    n_x = max(0, sm_num_rows(mesh)) if mesh else 0
+    _check(lib().sm_load_state(mesh, _arg(acc, "acc", 4 * n_x * _classes(mesh)), _arg(cnt, "cnt", 4 * n_x),
+                               _stream(stream)))
 
 
 def sm_check(mesh: int, stream=None):
@@ -280,8 +348,11 @@ def sm_render_rows_noalloc(vertices, faces, K, cam_to_world, N: int, H: int, W: 
     for callers whose device memory is owned elsewhere (see labelfuse.h)."""
     V = int(vertices.shape[0]) if vertices is not None else 0
     F = int(faces.shape[0]) if faces is not None else 0
-    _check(lib().sm_render_rows_noalloc(_ptr(vertices), V, _ptr(faces), F, _ptr(K), _ptr(cam_to_world), int(N),
-                                        int(H), int(W), _ptr(idmap_out), _stream(stream)))
+    n = max(0, int(N))
+    _check(lib().sm_render_rows_noalloc(_arg(vertices, "vertices", 12 * V), V, _arg(faces, "faces", 12 * F), F,
+                                        _arg(K, "K", 32 * n), _arg(cam_to_world, "cam_to_world", 128 * n), int(N),
+                                        int(H), int(W), _arg(idmap_out, "idmap_out", 4 * max(0, N * H * W)),
+                                        _stream(stream)))
 
 
 def sm_profile_enable(mesh: int, on: bool = True):

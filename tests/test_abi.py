@@ -139,3 +139,39 @@ def test_argument_ranges_rejected_on_host(libpath):
     assert L.sm_conf_train_step(P, None, P, 4, 0.1, P, P, None) == 1
     assert L.sm_host_alloc(0, ctypes.byref(h)) == 1
     assert L.sm_host_free(None) == 0
+
+
+def test_binding_checks_buffers_before_the_call(libpath):
+    """The binding refuses a tensor that is on the wrong side, not contiguous
+    or smaller than what the call reads or writes, with SM_ERR_INVALID_ARG
+    and before the library is called; raw addresses pass through."""
+    import torch
+    from paper_2111_11103_gb300 import labelfuse as lf
+    host = torch.zeros(4 * lf.SM_CONF_PARAMS, dtype=torch.float32)
+    with pytest.raises(lf.LabelFuseError) as e:          # device entry point, host tensor
+        lf.sm_conf_forward(host, host, 4, host, stream=0)
+    assert e.value.status == 1 and "CUDA tensor" in str(e.value)
+    K = torch.zeros((2, 4), dtype=torch.float64)
+    T = torch.zeros((2, 16), dtype=torch.float64)
+    img = torch.zeros((2, 4, 4), dtype=torch.uint8)
+    with pytest.raises(lf.LabelFuseError, match="K holds 64 bytes; the call needs 96"):
+        lf.sm_fuse_render_host(None, None, "f32", None, K, T, 3, 4, 4, img, stream=0)
+    with pytest.raises(lf.LabelFuseError, match="labels_out holds 32 bytes; the call needs 40"):
+        lf.sm_fuse_render_host(None, None, "f32", None, K, T, 2, 4, 5, img, stream=0)
+    with pytest.raises(lf.LabelFuseError, match="cam_to_world is not contiguous"):
+        lf.sm_fuse_render_host(None, None, "f32", None, K, torch.zeros((16, 2), dtype=torch.float64).t(), 2, 4, 4,
+                               img, stream=0)
+    with pytest.raises(lf.LabelFuseError, match="scale holds"):
+        lf.sm_fuse_render_host(None, None, "bf16", torch.zeros(31), K, T, 2, 4, 4, img, stream=0)
+    # within bounds the call reaches the library, which rejects the NULL mesh
+    with pytest.raises(lf.LabelFuseError, match="NULL"):
+        lf.sm_fuse_render_host(None, None, "f32", None, K, T, 2, 4, 4, img, stream=0)
+    # the host entry point refuses what the device entry points need, and vice versa
+    assert lf._arg(img, "x", img.numel(), host=True) == img.data_ptr()
+    with pytest.raises(lf.LabelFuseError, match="must be a CUDA tensor"):
+        lf._arg(img, "x", 1)
+    assert lf._arg(1234, "raw", 1 << 40) == 1234 and lf._arg(None, "x", 8) is None
+    # the byte count follows the element size (an FP8 buffer viewed as uint8 is fine)
+    assert lf._arg(torch.zeros(10, dtype=torch.uint8), "probs", 10, host=True)
+    with pytest.raises(lf.LabelFuseError):
+        lf._arg(torch.zeros(10, dtype=torch.uint8), "probs", 11, host=True)
