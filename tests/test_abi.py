@@ -175,3 +175,42 @@ def test_binding_checks_buffers_before_the_call(libpath):
     assert lf._arg(torch.zeros(10, dtype=torch.uint8), "probs", 10, host=True)
     with pytest.raises(lf.LabelFuseError):
         lf._arg(torch.zeros(10, dtype=torch.uint8), "probs", 11, host=True)
+
+
+def test_header_is_plain_c_and_a_c_client_links(libpath, tmp_path):
+    """include/labelfuse.h compiles as strict C99 and C++17 on its own, and a
+    plain C program (no Python, no PyTorch) links against the library and gets
+    its host-side answers (status strings, NULL-handle queries, validation)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(ROOT, "include")
+    for lang, std in (("c", "-std=c99"), ("c++", "-std=c++17")):
+        r = subprocess.run([gcc if lang == "c" else (shutil.which("g++") or gcc), std, "-Wall", "-Wextra",
+                            "-pedantic", "-Werror", "-fsyntax-only", "-x", lang, HEADER], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+    src = tmp_path / "client.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include "labelfuse.h"
+int main(void)
+{
+    sm_mesh *m = 0;
+    sm_status st = sm_mesh_upload(0, 0, 0, 0, 0, 0, SM_RULE_SUM, SM_WEIGHT_PIXEL, 0, &m);
+    printf("%d|%s|%s|%lld|%d\n", (int)st, sm_status_string(st), sm_last_error(), (long long)sm_num_rows(0),
+           (int)sm_mesh_free(0));
+    return (st == SM_ERR_INVALID_ARG && m == 0) ? 0 : 1;
+}
+""")
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(libpath)
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-I", inc, str(src), "-o", str(exe), "-L", libdir, "-llabelfuse",
+                        "-Wl,-rpath," + libdir], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stdout + r.stderr
+    code, text, reason, rows, freed = r.stdout.strip().split("|")
+    assert (code, text, rows, freed) == ("1", "invalid argument", "-1", "0")
+    assert "n_classes" in reason
