@@ -370,6 +370,18 @@ def run_ours(args):
     # step-level HBM fraction on the algorithmic bytes of the whole path
     algo_step = ring * (fb - fa) * (H * W * c * 4 + 2 * H * W * 4 + H * W) + 2 * sg_rows(m, lf) * c * 4
     line["step_hbm_frac"] = algo_step / (ms_step / 1e3) / 1e9 / peak
+    # face updates (one covered pixel added to a row, all c classes): the
+    # observation counts of the last timed step, read back after the timing
+    try:
+        cnt = torch.zeros(max(sg_rows(m, lf), 1), dtype=torch.int32, device=dev)
+        lf.sm_read_state(m, None, cnt, stream)
+        stream.synchronize()
+        updates = int(cnt.to(torch.int64).sum())
+        line["face_updates_per_step"] = updates
+        line["face_updates_per_s"] = updates / (ms_step / 1e3)
+    except Exception as exc:  # an optional figure: never costs the benchmark its line
+        line["face_updates_per_s"] = None
+        line["face_updates_error"] = str(exc)[:200]
 
     if not args.no_e2e and rank == 0 and ws == 1 and not args.hires:
         try:
