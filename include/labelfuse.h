@@ -255,25 +255,38 @@ sm_status sm_fuse_frames_weighted(sm_mesh *m, const void *d_probs, sm_dtype dtyp
 #define SM_CONF_PARAMS 1281
 
 /* Renders the N frames and writes every pixel's features (d_feat_out,
- * N x H x W x SM_CONF_FEATURES) and row (d_rows_out, N x H x W, -1 for
- * background).  Leaves the accumulators untouched. */
+ * N x H x W x SM_CONF_FEATURES float32) and row (d_rows_out, N x H x W int32,
+ * -1 for background).  Inputs as for sm_fuse_frames; both outputs are
+ * caller-owned device buffers.  Leaves the accumulators untouched.
+ * Errors: SM_ERR_INVALID_ARG (NULL mesh or pointer, sizes, a scale given for
+ * F32 or missing for BF16/FP8), SM_ERR_OOM, SM_ERR_CUDA. */
 sm_status sm_conf_features(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
                            const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N, int32_t H, int32_t W,
                            float *d_feat_out, int32_t *d_rows_out, void *stream);
 
 /* Training targets: d_target_out[k] = 1 where pixel k's first arg max equals
  * the fused label of its row d_rows[k], else 0 (background, unseen rows).
- * Requires an earlier sm_normalise (else SM_ERR_STATE). */
+ * d_probs n_pixels x c in `dtype` (+ d_scale n_pixels float32 for BF16/FP8),
+ * d_rows n_pixels int32, d_target_out n_pixels float32, all device.
+ * Requires an earlier sm_normalise.
+ * Errors: SM_ERR_INVALID_ARG (NULL mesh or pointer, n_pixels < 0, dtype),
+ * SM_ERR_STATE (no sm_normalise since the last fusion), SM_ERR_CUDA. */
 sm_status sm_conf_targets(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
                           const int32_t *d_rows, int64_t n_pixels, float *d_target_out, void *stream);
 
-/* Inference: d_w_out[i] = sigmoid(MLP(d_feat[i])) for n observations. */
+/* Inference: d_w_out[i] = sigmoid(MLP(d_feat[i])) for n observations.
+ * d_params SM_CONF_PARAMS float32, d_feat n x SM_CONF_FEATURES float32,
+ * d_w_out n float32, all device; n == 0 is a no-op.
+ * Errors: SM_ERR_INVALID_ARG (n < 0, NULL pointer), SM_ERR_CUDA. */
 sm_status sm_conf_forward(const float *d_params, const float *d_feat, int64_t n, float *d_w_out, void *stream);
 
 /* One gradient-descent step on the mean binary cross-entropy of n
  * observations: d_grad_out (SM_CONF_PARAMS, required) receives the gradient
  * with respect to the bfloat16-rounded parameters, d_loss_out (1 float,
- * required) the loss before the step, and d_params -= lr * gradient. */
+ * required) the loss before the step, and d_params -= lr * gradient.
+ * d_feat n x SM_CONF_FEATURES and d_target n float32; all device.
+ * Errors: SM_ERR_INVALID_ARG (n < 0, lr NaN or outside [0, 1e6), NULL
+ * pointer), SM_ERR_CUDA. */
 sm_status sm_conf_train_step(float *d_params, const float *d_feat, const float *d_target, int64_t n, float lr,
                              float *d_grad_out, float *d_loss_out, void *stream);
 
@@ -287,7 +300,8 @@ sm_status sm_conf_train_step(float *d_params, const float *d_feat, const float *
 sm_status sm_host_alloc(uint64_t bytes, void **out);
 sm_status sm_host_free(void *p);
 
-/* Zeroes the accumulators and observation counts. */
+/* Zeroes the accumulators and observation counts (enqueued on `stream`).
+ * Errors: SM_ERR_INVALID_ARG (NULL mesh), SM_ERR_CUDA. */
 sm_status sm_reset(sm_mesh *m, void *stream);
 
 /* Copies the accumulators (n_x x c float32) and observation counts (n_x
@@ -296,7 +310,10 @@ sm_status sm_reset(sm_mesh *m, void *stream);
  * so states of disjoint frame sets can be added. */
 sm_status sm_read_state(sm_mesh *m, float *d_acc_out, uint32_t *d_cnt_out, void *stream);
 
-/* Overwrites the accumulators and counts from device buffers (both required). */
+/* Overwrites the accumulators and counts from device buffers (both required
+ * when n_x > 0); a later render needs a new sm_normalise.
+ * Errors (both state calls): SM_ERR_INVALID_ARG (NULL mesh, or NULL state
+ * buffer for sm_load_state), SM_ERR_CUDA. */
 sm_status sm_load_state(sm_mesh *m, const float *d_acc, const uint32_t *d_cnt, void *stream);
 
 /* Synchronises `stream` and returns the first error a kernel latched since
