@@ -186,9 +186,15 @@ def cpu_baseline(scene, cams, probs, args, n_frames):
     oracle.fuse_sequence(mesh, cams.K[:n_frames], cams.cam_to_world[:n_frames], p, args.rule, args.weight,
                          nthreads=cores)
     dt = time.perf_counter() - t0
+    n1 = min(8, n_frames)  # the same oracle on one thread, on a smaller sample
+    t0 = time.perf_counter()
+    oracle.fuse_sequence(mesh, cams.K[:n1], cams.cam_to_world[:n1], p[:n1], args.rule, args.weight, nthreads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": n_frames / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
             "sample": f"first {n_frames} of the {args.frames} frames (render + fuse, {args.rule}, w^({args.weight[0].upper()})), "
-                      f"{dt:.1f} s wall"}
+                      f"{dt:.1f} s wall",
+            "single_core": {"value": n1 / dt1, "unit": "frames/s", "cores": 1,
+                            "sample": f"first {n1} frames on one thread, {dt1:.1f} s wall"}}
 
 
 # --------------------------------------------------------------------------- arms
