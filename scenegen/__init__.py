@@ -25,6 +25,10 @@ Recipes (all seed-fixed):
   roll around 0 (sd 2 deg); 640 x 480, fx = fy = 577.6, cx = 319.5, cy = 239.5.
   Predictions: softmax(2.5 onehot(gt) + field + N(0, 0.5^2)), with ``field`` a
   per-frame, per-class 11 x 8 control grid of N(0, 1.2^2) bilinearly upsampled.
+* ``apartment``: four such rooms (6 x 5 x 3 m each, 20 boxes each) in a 2 x 2
+  layout, the two crossing internal walls opened by a 0.9 x 2.1 m door in each
+  half, gridded to ~4M triangles (the learned-confidence configuration).
+  ``apartment_poses``: one ``random_walk_poses`` segment per room.
 """
 from __future__ import annotations
 
@@ -133,11 +137,21 @@ def paper_room(seed: int = BASE_SEED + 1, target_faces: int = 500_000, n_boxes: 
         (o([0.0, 0.0, 0.0]), o([0.0, Ly, 0.0]), o([0.0, 0.0, Lz])),  # x = 0
         (o([Lx, 0.0, 0.0]), o([0.0, Ly, 0.0]), o([0.0, 0.0, Lz])),   # x = Lx
     ]
-    for _ in range(n_boxes):
+    geo += _boxes(rng, n_boxes, 0.0, 0.0, Lx, Ly)
+    return _mesh_rects(_patch_rects(rng, geo, n_classes), target_faces, aligned, n_classes)
+
+
+def _boxes(rng, n: int, x_lo: float, y_lo: float, Lx: float, Ly: float):
+    """n axis-aligned boxes standing on the floor of the Lx x Ly area whose
+    corner is (x_lo, y_lo): sides U(0.3, 1.5) m, height U(0.3, 1.2) m; the five
+    visible rectangles of each (no bottom)."""
+    o = np.array
+    geo = []
+    for _ in range(n):
         w, d = rng.uniform(0.3, 1.5, size=2)
         h = rng.uniform(0.3, 1.2)
-        x0 = rng.uniform(0.0, Lx - w)
-        y0 = rng.uniform(0.0, Ly - d)
+        x0 = x_lo + rng.uniform(0.0, Lx - w)
+        y0 = y_lo + rng.uniform(0.0, Ly - d)
         geo += [
             (o([x0, y0, h]), o([w, 0.0, 0.0]), o([0.0, d, 0.0])),      # top
             (o([x0, y0, 0.0]), o([w, 0.0, 0.0]), o([0.0, 0.0, h])),    # front
@@ -145,12 +159,68 @@ def paper_room(seed: int = BASE_SEED + 1, target_faces: int = 500_000, n_boxes: 
             (o([x0, y0, 0.0]), o([0.0, d, 0.0]), o([0.0, 0.0, h])),    # left
             (o([x0 + w, y0, 0.0]), o([0.0, d, 0.0]), o([0.0, 0.0, h])),  # right
         ]
+    return geo
+
+
+def _wall_with_door(start, along, length: float, height: float, door_w: float, door_h: float):
+    """A vertical wall from `start` along the unit vector `along`, with a door
+    opening of door_w x door_h centred on it: the part left of the door, the
+    part right of it and the lintel above it."""
+    z = np.array([0.0, 0.0, 1.0])
+    side = 0.5 * (length - door_w)
+    return [
+        (start, along * side, z * height),
+        (start + along * (side + door_w), along * side, z * height),
+        (start + along * side + z * door_h, along * door_w, z * (height - door_h)),
+    ]
+
+
+def apartment(seed: int = BASE_SEED + 5, target_faces: int = 4_000_000, boxes_per_room: int = 20,
+              n_classes: int = 40, room=(6.0, 5.0, 3.0), door=(0.9, 2.1), aligned: bool = True) -> Scene:
+    """Four rooms of room[0] x room[1] x room[2] m in a 2 x 2 layout under one
+    floor and ceiling, with the same furniture and class patches as
+    ``paper_room``.  The two internal walls (x = room[0], y = room[1]) cross at
+    the middle; each half of each has a door of door[0] x door[1] m at its
+    centre, so every pair of neighbouring rooms is joined.  ~target_faces
+    triangles (+-1 %)."""
+    rng = np.random.default_rng(seed)
+    Lx, Ly, Lz = room
+    X, Y = 2 * Lx, 2 * Ly
+    o = np.array
+    ex, ey = o([1.0, 0.0, 0.0]), o([0.0, 1.0, 0.0])
+    geo = [
+        (o([0.0, 0.0, 0.0]), o([X, 0.0, 0.0]), o([0.0, Y, 0.0])),    # floor
+        (o([0.0, 0.0, Lz]), o([X, 0.0, 0.0]), o([0.0, Y, 0.0])),     # ceiling
+        (o([0.0, 0.0, 0.0]), o([X, 0.0, 0.0]), o([0.0, 0.0, Lz])),   # y = 0
+        (o([0.0, Y, 0.0]), o([X, 0.0, 0.0]), o([0.0, 0.0, Lz])),     # y = Y
+        (o([0.0, 0.0, 0.0]), o([0.0, Y, 0.0]), o([0.0, 0.0, Lz])),   # x = 0
+        (o([X, 0.0, 0.0]), o([0.0, Y, 0.0]), o([0.0, 0.0, Lz])),     # x = X
+    ]
+    for y0 in (0.0, Ly):   # internal wall x = Lx, one door per room pair
+        geo += _wall_with_door(o([Lx, y0, 0.0]), ey, Ly, Lz, door[0], door[1])
+    for x0 in (0.0, Lx):   # internal wall y = Ly
+        geo += _wall_with_door(o([x0, Ly, 0.0]), ex, Lx, Lz, door[0], door[1])
+    for i in range(2):
+        for j in range(2):
+            geo += _boxes(rng, boxes_per_room, i * Lx, j * Ly, Lx, Ly)
+    return _mesh_rects(_patch_rects(rng, geo, n_classes), target_faces, aligned, n_classes)
+
+
+def _patch_rects(rng, geo, n_classes):
+    """Rectangles cut into <= 0.5 m patches, each with a Zipf(1) class."""
     rects = []
     for org, eu, ev in geo:
         pu = max(1, math.ceil(np.linalg.norm(eu) / 0.5 - 1e-9))
         pv = max(1, math.ceil(np.linalg.norm(ev) / 0.5 - 1e-9))
         rects.append(Rect(org, eu, ev, _zipf_classes(rng, (pu, pv), n_classes)))
+    return rects
 
+
+def _mesh_rects(rects, target_faces: int, aligned: bool, n_classes: int) -> Scene:
+    """Grids every rectangle into quads of one edge length chosen so that the
+    mesh has about target_faces triangles: aligned grids refine each class
+    patch (then +-1 quad-per-patch steps bring the count within 0.5 %),
+    unaligned grids ignore the patches."""
     def quads_for(hq):
         out = []
         for r in rects:
@@ -205,6 +275,7 @@ def paper_room(seed: int = BASE_SEED + 1, target_faces: int = 500_000, n_boxes: 
     return _build(rects, quads, n_classes)
 
 
+
 # --------------------------------------------------------------------------- cameras
 def _look_pose(pos, yaw, pitch, roll):
     """Camera-to-world 4x4 (camera x right, y down, z forward; world z up)."""
@@ -234,8 +305,9 @@ def circle_poses(n: int = 8, radius: float = 0.5, H: int = 48, W: int = 64, fx: 
 
 def random_walk_poses(n: int, seed: int = BASE_SEED + 1, size=(6.0, 5.0, 3.0), height: float = 1.5,
                       margin: float = 0.5, H: int = 480, W: int = 640, fx: float = 577.6, fy: float = 577.6,
-                      cx: float = 319.5, cy: float = 239.5, fps: float = 30.0) -> Cameras:
-    """Smooth random-walk trajectory inside the room (see module docstring)."""
+                      cx: float = 319.5, cy: float = 239.5, fps: float = 30.0, origin=None) -> Cameras:
+    """Smooth random-walk trajectory inside the room (see module docstring);
+    origin: (x, y) of the room's corner if it is not at the world origin."""
     rng = np.random.default_rng(seed + 7919)
     dt = 1.0 / fps
     theta = 1.0  # 1/s mean reversion of the velocity
@@ -248,7 +320,8 @@ def random_walk_poses(n: int, seed: int = BASE_SEED + 1, size=(6.0, 5.0, 3.0), h
     pitch_dev, roll_dev = 0.0, 0.0
     Ts = []
     for _ in range(n):
-        T = _look_pose(np.array([p[0], p[1], height]), yaw, math.radians(-15.0) + pitch_dev, roll_dev)
+        pos = np.array([p[0], p[1], height]) if origin is None else np.array([origin[0] + p[0], origin[1] + p[1], height])
+        T = _look_pose(pos, yaw, math.radians(-15.0) + pitch_dev, roll_dev)
         Ts.append(T)
         v += -theta * v * dt + 0.3 * math.sqrt(2 * theta * dt) * rng.normal(size=2)
         p = p + v * dt
@@ -265,6 +338,23 @@ def random_walk_poses(n: int, seed: int = BASE_SEED + 1, size=(6.0, 5.0, 3.0), h
         roll_dev += -1.0 * roll_dev * dt + math.radians(2.0) * math.sqrt(2 * dt) * rng.normal()
     K = np.tile(np.array([fx, fy, cx, cy], dtype=np.float64), (n, 1))
     return Cameras(K, np.stack(Ts), H, W)
+
+
+def apartment_poses(n: int, seed: int = BASE_SEED + 5, room=(6.0, 5.0, 3.0), **kw) -> Cameras:
+    """n frames for ``apartment``: one random-walk segment per room (rooms in
+    the order (0,0), (1,0), (0,1), (1,1), frames split as evenly as
+    possible), each kept >= 0.5 m from that room's walls.  The segments are
+    concatenated; fusion treats frames as independent observations."""
+    parts = []
+    for k in range(4):
+        nk = n // 4 + (1 if k < n % 4 else 0)
+        if nk:
+            parts.append(random_walk_poses(nk, seed=seed + k, size=room, origin=((k % 2) * room[0], (k // 2) * room[1]),
+                                           **kw))
+    if not parts:
+        return Cameras(np.zeros((0, 4)), np.zeros((0, 4, 4)), kw.get("H", 480), kw.get("W", 640))
+    return Cameras(np.concatenate([c.K for c in parts]), np.concatenate([c.cam_to_world for c in parts]),
+                   parts[0].H, parts[0].W)
 
 
 # --------------------------------------------------------------------------- ground truth + predictions

@@ -53,3 +53,53 @@ def test_coarse_unaligned_grid_straddles_patches():
     pv_idx = np.floor(np.clip(v, 0, 1 - 1e-12) * pv).astype(int)
     straddle = (pu_idx.min(1) != pu_idx.max(1)) | (pv_idx.min(1) != pv_idx.max(1))
     assert straddle.mean() > 0.3
+
+
+def _covered(scene, p, tol=1e-9):
+    """Whether point p lies on one of the scene's rectangles."""
+    for r in scene.rects:
+        n = np.cross(r.eu, r.ev)
+        if abs(np.dot(p - r.origin, n)) > tol * np.linalg.norm(n):
+            continue
+        a = np.dot(p - r.origin, r.eu) / np.dot(r.eu, r.eu)
+        b = np.dot(p - r.origin, r.ev) / np.dot(r.ev, r.ev)
+        if 0 <= a <= 1 and 0 <= b <= 1:
+            return True
+    return False
+
+
+def test_apartment_sizes_and_determinism():
+    a = sg.apartment(target_faces=400_000)
+    b = sg.apartment(target_faces=400_000)
+    assert abs(len(a.faces) - 400_000) <= 0.01 * 400_000
+    assert np.array_equal(a.faces, b.faces) and np.array_equal(a.vertices, b.vertices)
+    assert np.array_equal(a.face_gt, b.face_gt)
+    assert len(a.rects) == 6 + 4 * 3 + 4 * 20 * 5   # shell, 4 wall halves with doors, furniture
+    assert a.face_gt.min() >= 0 and a.face_gt.max() < a.n_classes
+    assert a.vertices[:, 0].max() <= 12.0 and a.vertices[:, 1].max() <= 10.0 and a.vertices[:, 2].max() <= 3.0
+
+
+def test_apartment_doors_are_open_and_walls_closed():
+    """Every neighbouring pair of rooms is joined by a 0.9 x 2.1 m door in the
+    middle of its shared wall; the rest of that wall and the lintel are solid."""
+    a = sg.apartment(target_faces=50_000)
+    for centre, along in [((6.0, 2.5), (0, 1)), ((6.0, 7.5), (0, 1)), ((3.0, 5.0), (1, 0)), ((9.0, 5.0), (1, 0))]:
+        c = np.array([centre[0], centre[1], 1.0])
+        e = np.array([along[0], along[1], 0.0])
+        assert not _covered(a, c)                                  # the door is open
+        assert not _covered(a, c + 0.4 * e) and not _covered(a, c - 0.4 * e)
+        assert _covered(a, c + 0.6 * e) and _covered(a, c - 0.6 * e)   # wall beside the door
+        assert _covered(a, c + np.array([0.0, 0.0, 1.5]))          # lintel above it (z = 2.5)
+
+
+def test_apartment_poses_stay_in_their_rooms():
+    cams = sg.apartment_poses(400)
+    assert cams.K.shape == (400, 4) and cams.cam_to_world.shape == (400, 4, 4)
+    pos = cams.cam_to_world[:, :3, 3]
+    for k in range(4):
+        seg = pos[k * 100:(k + 1) * 100]
+        x0, y0 = (k % 2) * 6.0, (k // 2) * 5.0
+        assert np.all(seg[:, 0] >= x0 + 0.5 - 1e-9) and np.all(seg[:, 0] <= x0 + 5.5 + 1e-9)
+        assert np.all(seg[:, 1] >= y0 + 0.5 - 1e-9) and np.all(seg[:, 1] <= y0 + 4.5 + 1e-9)
+        assert np.allclose(seg[:, 2], 1.5)
+    assert sg.apartment_poses(0).K.shape == (0, 4)
