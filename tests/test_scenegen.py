@@ -103,3 +103,21 @@ def test_apartment_poses_stay_in_their_rooms():
         assert np.all(seg[:, 1] >= y0 + 0.5 - 1e-9) and np.all(seg[:, 1] <= y0 + 4.5 + 1e-9)
         assert np.allclose(seg[:, 2], 1.5)
     assert sg.apartment_poses(0).K.shape == (0, 4)
+
+
+def test_oracle_sees_through_a_door(ora):
+    """Rendered with the oracle from room (0, 0), facing the door to room (1, 0)
+    head-on: pixels through the opening see triangles beyond the internal wall
+    (x > 6 m), pixels beside it see the wall itself (x = 6 m)."""
+    a = sg.apartment(target_faces=50_000)
+    mesh = ora.Mesh(a.vertices, a.faces)
+    T = sg._look_pose(np.array([4.5, 2.5, 1.0]), 0.0, 0.0, 0.0)   # 1.5 m before the door, looking +x
+    K = np.array([40.0, 40.0, 31.5, 23.5])
+    _, face = ora.render_frame(mesh, K, T, 48, 64, want_faces=True)
+    x = a.vertices[a.faces].astype(np.float64)[..., 0].mean(1)    # triangle centroids' x
+    # rows 4-12 cross the wall plane at z <= 1.73 m, inside the 2.1 m opening and
+    # above every box (<= 1.2 m tall), so nothing of the first room is in the way
+    centre = face[4:12, 28:36]                                     # through the 0.9 m opening
+    assert np.all(centre >= 0) and np.all(x[centre] > 6.0 + 1e-6)
+    side = face[4:12, 0:4]                                         # 0.75 m or more beside the door
+    assert np.all(side >= 0) and np.allclose(x[side], 6.0)
