@@ -226,7 +226,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "rule": args.rule, "weight": args.weight},
+            "config": {"workload": WORKLOAD, "faces": int(scene.faces.shape[0]), "frames": args.frames, "ring": 1,
+                       "H": cams.H, "W": cams.W, "classes": scene.n_classes, "rule": args.rule, "weight": args.weight,
+                       "probs": "f32 HWC", "parallelism": "single"},
             "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
                              "sample": f"{per} frames per step from the first {n} frames"},
             "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -66,3 +66,6 @@ def test_reference_arm_prints_its_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    cfg = d["config"]
+    assert (cfg["H"], cfg["W"], cfg["classes"], cfg["frames"]) == (480, 640, 40, 16)
+    assert abs(cfg["faces"] - 20000) <= 200 and cfg["rule"] == "logsum" and cfg["weight"] == "pixel"
