@@ -66,7 +66,55 @@ def parse():
                          "steps from gamma = 0 and 0.2 (a synthetic analogue of the paper's mesh-simplification study)")
     ap.add_argument("--hires", action="store_true",
                     help="1296 x 968 frames (fx = fy = 1170): a 250-frame ring fused and rendered 4 times per step")
+    ap.add_argument("--dry-run", action="store_true",
+                    help="bring up the ranks (gloo, no GPU work) and print each rank's frame range")
     return ap.parse_args()
+
+
+def free_port() -> int:
+    import socket
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as so:
+        so.bind(("127.0.0.1", 0))
+        return so.getsockname()[1]
+
+
+def launch_ranks(args) -> None:
+    """--gpus N > 1 outside a distributed launcher: run this script as N ranks
+    under torchrun (one process per GPU, rendezvous on 127.0.0.1) and exit
+    with its status.  Under a launcher, WORLD_SIZE must equal N."""
+    ws = os.environ.get("WORLD_SIZE")
+    if ws is not None:
+        if int(ws) != args.gpus:
+            print(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={ws}", file=sys.stderr)
+            sys.exit(2)
+        return
+    if args.gpus <= 1:
+        return
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", f"--master-port={free_port()}", os.path.abspath(__file__)] + sys.argv[1:]
+    sys.exit(subprocess.call(cmd))
+
+
+def run_dry(args) -> None:
+    """The ranks and their frame ranges, without GPU work: every rank joins a
+    gloo group, computes its share of the frames, and rank 0 prints all shares
+    (gathered over the group) as one JSON line."""
+    from paper_2111_11103_gb300 import shard
+    ws, rank, _ = dist_env()
+    fr = shard.frame_range(args.frames, rank, ws)
+    ranges = [list(fr)]
+    if ws > 1:
+        torch.distributed.init_process_group("gloo")
+        got = [None] * ws
+        torch.distributed.all_gather_object(got, [rank, fr[0], fr[1], os.getpid()])
+        ranges = [[a, b] for _, a, b, _ in sorted(got)]
+        pids = len({p for *_, p in got})
+        torch.distributed.destroy_process_group()
+    else:
+        pids = 1
+    if rank == 0:
+        print(json.dumps({"dry_run": True, "n_ranks": ws, "processes": pids, "frames": args.frames,
+                          "frame_ranges": ranges}), flush=True)
 
 
 # --------------------------------------------------------------------------- helpers
@@ -160,17 +208,20 @@ def dist_env():
     return ws, rank, local
 
 
-def make_workload(args, dev):
+def make_workload(args, dev, fa=0, fb=None):
+    """The scene, all cameras, and the predictions of frames [fa, fb) only
+    (each rank generates its own share)."""
     scene = sg.paper_room(target_faces=args.faces)
     if args.hires:
         cams = sg.random_walk_poses(args.frames, H=968, W=1296, fx=1170.0, fy=1170.0, cx=647.5, cy=483.5)
     else:
         cams = sg.random_walk_poses(args.frames)
-    N, H, W, c = args.frames, cams.H, cams.W, scene.n_classes
-    probs = torch.empty((N, H, W, c), dtype=torch.float32, device=dev)
-    for a in range(0, N, 25):
-        b = min(N, a + 25)
-        sg.predictions(scene, cams, "paper", frames=range(a, b), device=dev, out=probs[a:b])
+    fb = args.frames if fb is None else fb
+    H, W, c = cams.H, cams.W, scene.n_classes
+    probs = torch.empty((fb - fa, H, W, c), dtype=torch.float32, device=dev)
+    for a in range(fa, fb, 25):
+        b = min(fb, a + 25)
+        sg.predictions(scene, cams, "paper", frames=range(a, b), device=dev, out=probs[a - fa:b - fa])
     torch.cuda.synchronize(dev)
     return scene, cams, probs
 
@@ -198,39 +249,47 @@ def cpu_baseline(scene, cams, probs, args, n_frames):
 
 
 # --------------------------------------------------------------------------- arms
+def workload_config(args, faces, frames, ring, H, W, c, ws):
+    """The workload keys of the JSON line (the same for both arms)."""
+    return {"workload": WORKLOAD_HIRES if args.hires else WORKLOAD, "faces": faces, "frames": frames, "ring": ring,
+            "H": H, "W": W, "classes": c, "rule": args.rule, "weight": args.weight, "probs": "f32 HWC",
+            "parallelism": f"frames{ws}" if ws > 1 else "single"}
+
+
 def run_reference(args):
+    """The oracle, as it stands, on the machine's host cores: every step renders
+    and fuses the same bounded sample (the first --cpu-frames frames, at
+    least one per core) in one call, so that the per-call set-up of its
+    per-thread accumulators is amortised as in cpu_baseline."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
     import oracle
     scene = sg.paper_room(target_faces=args.faces)
     cams = sg.random_walk_poses(args.frames)
-    n = min(args.cpu_frames, args.frames)
+    cores = os.cpu_count() or 1
+    n = min(max(args.cpu_frames, cores), args.frames)
     probs = sg.predictions(scene, cams, "paper", frames=range(n), device="cuda" if torch.cuda.is_available() else "cpu")
     p = probs.cpu().numpy()
+    del probs
     mesh = oracle.Mesh(scene.vertices, scene.faces)
-    cores = os.cpu_count() or 1
-    per = max(1, n // max(1, args.steps))
     for _ in range(args.warmup):
         oracle.fuse_sequence(mesh, cams.K[:1], cams.cam_to_world[:1], p[:1], args.rule, args.weight, nthreads=1)
     times = []
     for s in range(args.steps):
-        a = (s * per) % n
-        b = min(n, a + per)
         t0 = time.perf_counter()
-        oracle.fuse_sequence(mesh, cams.K[a:b], cams.cam_to_world[a:b], p[a:b], args.rule, args.weight,
-                             nthreads=cores)
+        oracle.fuse_sequence(mesh, cams.K[:n], cams.cam_to_world[:n], p, args.rule, args.weight, nthreads=cores)
         times.append(time.perf_counter() - t0)
-    frames = per * args.steps
-    value = frames / sum(times)
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": 1,
+    value = n * args.steps / sum(times)
+    ring = 4 if args.hires else 1
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "faces": int(scene.faces.shape[0]), "frames": args.frames, "ring": 1,
-                       "H": cams.H, "W": cams.W, "classes": scene.n_classes, "rule": args.rule, "weight": args.weight,
-                       "probs": "f32 HWC", "parallelism": "single"},
+            "config": workload_config(args, int(scene.faces.shape[0]), args.frames, ring, cams.H, cams.W,
+                                      scene.n_classes, ws),
             "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{per} frames per step from the first {n} frames"},
+                             "sample": f"the first {n} of the {args.frames} frames per step (render + fuse, "
+                                       f"{args.rule}, w^({args.weight[0].upper()})), one call on {cores} threads"},
             "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -251,15 +310,21 @@ def run_ours(args):
     if not args.no_e2e and rank == 0 and ws == 1 and not args.hires:
         h_probs = lf.pinned_empty((args.frames, 480, 640, 40), torch.float32)
 
-    scene, cams, probs = make_workload(args, dev)
-    N, H, W, c = probs.shape
+    # frames of this rank: all of them on one GPU; on several, a contiguous
+    # share (generated by this rank only), fused locally and completed by one
+    # all-reduce of the state
+    fa, fb = shard.frame_range(args.frames, rank, ws)
+    scene, cams, probs = make_workload(args, dev, fa, fb)
+    N = args.frames
+    n_loc, H, W, c = probs.shape
     K = torch.as_tensor(cams.K, device=dev)
     T = torch.as_tensor(cams.cam_to_world.reshape(N, 16), device=dev)
+    K_loc, T_loc = K[fa:fb].contiguous(), T[fa:fb].contiguous()
     V = torch.as_tensor(scene.vertices, device=dev)
     Fc = torch.as_tensor(scene.faces, device=dev)
     m = lf.sm_mesh_upload(V, Fc, None, c, args.rule, args.weight)
-    idmaps = torch.empty((N, H, W), dtype=torch.int32, device=dev)
-    images = torch.empty((N, H, W), dtype=torch.uint8, device=dev)
+    idmaps = torch.empty((n_loc, H, W), dtype=torch.int32, device=dev)
+    images = torch.empty((n_loc, H, W), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def barrier():
@@ -268,9 +333,6 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
 
     ring = 4 if args.hires else 1
-    # frames of this rank: all of them on one GPU; on several, a contiguous
-    # share, fused locally and completed by one all-reduce of the state
-    fa, fb = shard.frame_range(N, rank, ws)
     state = (torch.empty((max(lf.sm_num_rows(m), 1), c), dtype=torch.float32, device=dev),
              torch.empty(max(lf.sm_num_rows(m), 1), dtype=torch.int32, device=dev))
 
@@ -280,14 +342,12 @@ def run_ours(args):
         def step():
             lf.sm_reset(m, stream)
             for _ in range(ring):  # the frames fused (and rendered) `ring` times per step
-                if ws > 1:
-                    shard.fuse_sharded(m, x, dtype, scale, K, T, H, W, rank, ws, idmap_out=idmaps[fa:fb],
-                                       state=state)
-                else:
-                    lf.sm_fuse_frames(m, x, dtype, scale, K, T, N, H, W, idmaps, stream)
+                lf.sm_fuse_frames(m, x, dtype, scale, K_loc, T_loc, n_loc, H, W, idmaps, stream)
+            if ws > 1:
+                shard.complete_fusion(m, state)
             lf.sm_normalise(m, None, None, stream)
             for _ in range(ring):
-                lf.sm_render_idmap(m, idmaps[fa:fb], (fb - fa) * H * W, images[fa:fb], stream)
+                lf.sm_render_idmap(m, idmaps, n_loc * H * W, images, stream)
 
         for _ in range(max(args.warmup, 3)):
             step()
@@ -318,13 +378,13 @@ def run_ours(args):
         one launch processes, over the launch's average event time."""
         n_sc, ms_sc = prof["scatter"]
         per_frame = H * W * c * elem_bytes + H * W * 4 + (H * W * 4 if scaled else 0)
-        fpl = ring * (fb - fa) * args.steps / max(n_sc, 1)
+        fpl = ring * n_loc * args.steps / max(n_sc, 1)
         achieved = per_frame * fpl / (ms_sc / max(n_sc, 1) / 1e3) / 1e9
         return achieved, per_frame, fpl
 
     # frames per launch: the library's autotuner on a 256-frame sample
-    n_tune = min(256, N)
-    tuned_B = lf.sm_autotune_batch(m, probs[:n_tune], "f32", None, K[:n_tune], T[:n_tune], n_tune, H, W) \
+    n_tune = min(256, n_loc)
+    tuned_B = lf.sm_autotune_batch(m, probs[:n_tune], "f32", None, K_loc[:n_tune], T_loc[:n_tune], n_tune, H, W) \
         if n_tune >= 4 and not args.no_autotune else None
 
     def graph_timing():
@@ -332,9 +392,9 @@ def run_ours(args):
         args.steps times (one launch from the host per step)."""
         def step():
             lf.sm_reset(m)
-            lf.sm_fuse_frames(m, probs, "f32", None, K, T, N, H, W, idmaps)
+            lf.sm_fuse_frames(m, probs, "f32", None, K_loc, T_loc, n_loc, H, W, idmaps)
             lf.sm_normalise(m, None, None)
-            lf.sm_render_idmap(m, idmaps, N * H * W, images)
+            lf.sm_render_idmap(m, idmaps, n_loc * H * W, images)
 
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
@@ -363,11 +423,9 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD_HIRES if args.hires else WORKLOAD, "faces": int(scene.faces.shape[0]),
-                       "frames": N, "ring": ring, "H": H, "W": W,
-                       "classes": c, "rule": args.rule, "weight": args.weight, "probs": "f32 HWC",
-                       "l2": l2_note(probs.numel() * probs.element_size()),
-                       "parallelism": f"frames{ws}" if ws > 1 else "single", "frames_per_launch": tuned_B},
+            "config": workload_config(args, int(scene.faces.shape[0]), N, ring, H, W, c, ws),
+            "l2": l2_note(probs.numel() * probs.element_size()),
+            "frames_per_launch": tuned_B, "frame_range": [fa, fb],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": "scatter",
                          "algorithmic_bytes_per_launch": bytes_per_frame_scatter * frames_per_launch,
@@ -376,7 +434,7 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clocks}
     # step-level HBM fraction on the algorithmic bytes of the whole path
-    algo_step = ring * (fb - fa) * (H * W * c * 4 + 2 * H * W * 4 + H * W) + 2 * sg_rows(m, lf) * c * 4
+    algo_step = ring * n_loc * (H * W * c * 4 + 2 * H * W * 4 + H * W) + 2 * sg_rows(m, lf) * c * 4
     line["step_hbm_frac"] = algo_step / (ms_step / 1e3) / 1e9 / peak
     # face updates (one covered pixel added to a row, all c classes): the
     # observation counts of the last timed step, read back after the timing
@@ -401,7 +459,7 @@ def run_ours(args):
     if not args.no_forms:
         line["forms"] = storage_forms(probs, timed, scatter_roofline, peak, ring * N, args.steps)
     if not args.no_cpu and rank == 0:
-        line["cpu_baseline"] = cpu_baseline(scene, cams, probs, args, min(args.cpu_frames, N))
+        line["cpu_baseline"] = cpu_baseline(scene, cams, probs, args, min(args.cpu_frames, n_loc))
     lf.sm_mesh_free(m)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -644,6 +702,10 @@ def run_coarse(args):
 
 def main():
     args = parse()
+    launch_ranks(args)
+    if args.dry_run:
+        run_dry(args)
+        return
     if args.coarse:
         run_coarse(args)
         return

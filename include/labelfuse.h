@@ -356,13 +356,20 @@ const char *sm_last_error(void);
  * SM_NOALLOC_MAX_FRAMES cameras, about 12 MiB), which every GPU that loads
  * the library holds until the process exits.  The call allocates nothing:
  * no cudaMalloc, cudaFree or allocating library routine.
- *   - The first call on a device looks up the array's device address with
- *     that device current; make that first call before any stream capture.
+ *   - The call runs on the device that holds d_idmap_out (made current for
+ *     the call, then restored); the inputs must be memory of that device (or
+ *     managed / mapped host memory it can address).  stream must belong to
+ *     that device.
+ *   - Each call looks up the array's device address on that device (no
+ *     allocation).  The first call on a device may load the library's device
+ *     code there: make it before any stream capture.
  *   - All calls share the array and it keeps the last call's contents (each
  *     call re-arms the z-buffer first).  Calls whose work overlaps on the GPU
  *     race on it: serialise them (one stream, or events).
  * Errors: SM_ERR_INVALID_ARG (NULL pointer, H x W > SM_NOALLOC_MAX_PIXELS,
- * N > SM_NOALLOC_MAX_FRAMES, V or F >= 2^31), SM_ERR_CUDA. */
+ * N > SM_NOALLOC_MAX_FRAMES, V or F >= 2^31, an output that is not device
+ * memory, an input on another device), SM_ERR_CUDA; all checks run before
+ * anything is enqueued. */
 #define SM_NOALLOC_MAX_PIXELS 1572864 /* 1.5 Mi pixels, e.g. 1296 x 968 */
 #define SM_NOALLOC_MAX_FRAMES 1024
 sm_status sm_render_rows_noalloc(const float *d_vertices, int64_t V, const int32_t *d_faces, int64_t F,

@@ -4,6 +4,7 @@
 // normalisation, render-back, state import/export and kernel timing.
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -85,6 +86,17 @@ struct ProfScope {
     }
 };
 
+// Test hook (host only): with LABELFUSE_TEST_FAIL_ALLOC set, every device
+// allocation of the library fails as if the device were out of memory, so
+// the SM_ERR_OOM paths can be exercised without exhausting a GPU.
+bool injected_alloc_failure() { return getenv("LABELFUSE_TEST_FAIL_ALLOC") != nullptr; }
+
+cudaError_t device_alloc(void **p, size_t bytes)
+{
+    if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+
 template <class T>
 sm_status grow(T **buf, int64_t *cap, int64_t need, cudaStream_t s, int fill, const char *what)
 {
@@ -93,6 +105,7 @@ sm_status grow(T **buf, int64_t *cap, int64_t need, cudaStream_t s, int fill, co
     *buf = nullptr;
     *cap = 0;
     void *p = nullptr;
+    if (injected_alloc_failure()) return cuda_fail(cudaErrorMemoryAllocation, what);
     LF_CUDA(cudaMallocAsync(&p, (size_t)need * sizeof(T), s), what);
     if (fill >= 0) LF_CUDA(cudaMemsetAsync(p, fill, (size_t)need * sizeof(T), s), what);
     *buf = static_cast<T *>(p);
@@ -315,14 +328,14 @@ sm_status sm_mesh_upload(const float *d_vertices, int64_t V, const int32_t *d_fa
     m->texel_mode = d_texel_res != nullptr;
 
     cudaError_t e;
-    if ((e = cudaMalloc(&m->err, 2 * sizeof(int32_t))) != cudaSuccess) return bail(cuda_fail(e, "error latch"));
+    if ((e = device_alloc((void **)&m->err, 2 * sizeof(int32_t))) != cudaSuccess) return bail(cuda_fail(e, "error latch"));
     if ((e = cudaMemsetAsync(m->err, 0, 2 * sizeof(int32_t), s)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
-    if ((e = cudaMalloc(&m->verts, (size_t)(V > 0 ? V : 1) * sizeof(float4))) != cudaSuccess)
+    if ((e = device_alloc((void **)&m->verts, (size_t)(V > 0 ? V : 1) * sizeof(float4))) != cudaSuccess)
         return bail(cuda_fail(e, "vertex buffer"));
-    if ((e = cudaMalloc(&m->faces, (size_t)(F > 0 ? F : 1) * sizeof(int4))) != cudaSuccess)
+    if ((e = device_alloc((void **)&m->faces, (size_t)(F > 0 ? F : 1) * sizeof(int4))) != cudaSuccess)
         return bail(cuda_fail(e, "face buffer"));
     const int64_t nclusters = (F + lf::kClusterFaces - 1) / lf::kClusterFaces;
-    if ((e = cudaMalloc(&m->bounds, (size_t)(nclusters > 0 ? 2 * nclusters : 2) * sizeof(float4))) != cudaSuccess)
+    if ((e = device_alloc((void **)&m->bounds, (size_t)(nclusters > 0 ? 2 * nclusters : 2) * sizeof(float4))) != cudaSuccess)
         return bail(cuda_fail(e, "cluster bounds"));
     if ((e = cudaStreamCreateWithFlags(&m->rstream, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(cuda_fail(e, "raster stream"));
@@ -347,15 +360,15 @@ sm_status sm_mesh_upload(const float *d_vertices, int64_t V, const int32_t *d_fa
 
     int64_t n_x = F;
     if (m->texel_mode) {
-        if ((e = cudaMalloc(&m->row0, (size_t)(F > 0 ? F : 1) * sizeof(int32_t))) != cudaSuccess)
+        if ((e = device_alloc((void **)&m->row0, (size_t)(F > 0 ? F : 1) * sizeof(int32_t))) != cudaSuccess)
             return bail(cuda_fail(e, "row offsets"));
-        if ((e = cudaMalloc(&m->texinfo, (size_t)(F > 0 ? F : 1) * sizeof(int32_t))) != cudaSuccess)
+        if ((e = device_alloc((void **)&m->texinfo, (size_t)(F > 0 ? F : 1) * sizeof(int32_t))) != cudaSuccess)
             return bail(cuda_fail(e, "texel info"));
         void *scratch = nullptr;
         int64_t *d_nx = nullptr;
-        if ((e = cudaMalloc(&scratch, lf::texel_scan_scratch_bytes(F))) != cudaSuccess)
+        if ((e = device_alloc(&scratch, lf::texel_scan_scratch_bytes(F))) != cudaSuccess)
             return bail(cuda_fail(e, "scan scratch"));
-        if ((e = cudaMalloc(&d_nx, sizeof(int64_t))) != cudaSuccess) {
+        if ((e = device_alloc((void **)&d_nx, sizeof(int64_t))) != cudaSuccess) {
             cudaFree(scratch);
             return bail(cuda_fail(e, "scan scratch"));
         }
@@ -378,10 +391,10 @@ sm_status sm_mesh_upload(const float *d_vertices, int64_t V, const int32_t *d_fa
     m->n_x = n_x;
 
     const size_t acc_bytes = (size_t)(n_x > 0 ? n_x : 1) * n_classes * sizeof(float);
-    if ((e = cudaMalloc(&m->acc, acc_bytes)) != cudaSuccess) return bail(cuda_fail(e, "accumulators"));
-    if ((e = cudaMalloc(&m->cnt, (size_t)(n_x > 0 ? n_x : 1) * sizeof(uint32_t))) != cudaSuccess)
+    if ((e = device_alloc((void **)&m->acc, acc_bytes)) != cudaSuccess) return bail(cuda_fail(e, "accumulators"));
+    if ((e = device_alloc((void **)&m->cnt, (size_t)(n_x > 0 ? n_x : 1) * sizeof(uint32_t))) != cudaSuccess)
         return bail(cuda_fail(e, "counts"));
-    if ((e = cudaMalloc(&m->labels8, (size_t)(n_x > 0 ? n_x : 1))) != cudaSuccess)
+    if ((e = device_alloc((void **)&m->labels8, (size_t)(n_x > 0 ? n_x : 1))) != cudaSuccess)
         return bail(cuda_fail(e, "labels"));
     if ((e = cudaMemsetAsync(m->acc, 0, acc_bytes, s)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
     if ((e = cudaMemsetAsync(m->cnt, 0, (size_t)(n_x > 0 ? n_x : 1) * sizeof(uint32_t), s)) != cudaSuccess)
@@ -783,8 +796,16 @@ sm_status sm_check(sm_mesh *m, void *stream)
     if (latched != lf::kErrNone) {
         LF_CUDA(cudaMemsetAsync(m->err, 0, sizeof(int32_t), s), "clear error latch");
         LF_CUDA(cudaStreamSynchronize(s), "synchronise");
-        if (latched == lf::kErrTimeout)
+        if (latched == lf::kErrTimeout) {
+            // the kernel that gave up left part of its scratch as it was:
+            // re-arm the z-buffers and clear the row histograms so that the
+            // next call starts clean (the accumulators are the caller's to
+            // reset)
+            if (m->keys) LF_CUDA(cudaMemsetAsync(m->keys, 0xFF, (size_t)m->keys_cap * sizeof(*m->keys), s), "re-arm");
+            if (m->fcnt) LF_CUDA(cudaMemsetAsync(m->fcnt, 0, (size_t)m->fcnt_cap * sizeof(*m->fcnt), s), "re-arm");
+            LF_CUDA(cudaStreamSynchronize(s), "synchronise");
             return fail(SM_ERR_TIMEOUT, "a bounded wait inside a kernel gave up (code %d)", latched);
+        }
         const char *what = latched == lf::kErrFaceIndex   ? "a face references a vertex outside [0, V)"
                            : latched == lf::kErrRowRange  ? "a row index outside [0, n_x) reached the scatter"
                            : latched == lf::kErrTexelRes  ? "texel steps out of range"
@@ -845,6 +866,32 @@ sm_status sm_render_rows_noalloc(const float *d_vertices, int64_t V, const int32
     if (N == 0) return SM_OK;
     if (!d_K || !d_cam_to_world || !d_idmap_out || (F > 0 && (!d_vertices || !d_faces)))
         return fail(SM_ERR_INVALID_ARG, "NULL pointer");
+    // the call runs on the device that holds the output; every input must be
+    // device memory of that same device (or memory it can address directly)
+    int dev = -1;
+    {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, d_idmap_out) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+            cudaGetLastError();
+            return fail(SM_ERR_INVALID_ARG, "d_idmap_out is not device memory");
+        }
+        dev = at.device;
+        const void *ins[] = {d_K, d_cam_to_world, F > 0 ? d_vertices : nullptr, F > 0 ? d_faces : nullptr};
+        const char *names[] = {"d_K", "d_cam_to_world", "d_vertices", "d_faces"};
+        for (int k = 0; k < 4; ++k) {
+            if (!ins[k]) continue;
+            cudaPointerAttributes ai{};
+            if (cudaPointerGetAttributes(&ai, ins[k]) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(SM_ERR_INVALID_ARG, "%s: unknown pointer", names[k]);
+            }
+            const bool same_device = ai.type == cudaMemoryTypeDevice && ai.device == dev;
+            const bool addressable = ai.type == cudaMemoryTypeManaged || (ai.type == cudaMemoryTypeHost && ai.devicePointer);
+            if (!same_device && !addressable)
+                return fail(SM_ERR_INVALID_ARG, "%s is not memory of device %d, which holds d_idmap_out", names[k], dev);
+        }
+    }
+    DeviceGuard g(dev);
     cudaError_t e = lf::launch_render_rows_noalloc(d_vertices, V, d_faces, F, d_K, d_cam_to_world, N, H, W,
                                                    d_idmap_out, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "render rows (no allocation)");

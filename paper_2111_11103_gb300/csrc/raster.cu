@@ -7,8 +7,6 @@
 // compiler never contracts into FMAs, so the integer decisions (snapped vertex
 // positions, coverage, the depth key) are the same on every run and match the
 // project's raster reading bit for bit.
-#include <mutex>
-
 #include "lf_internal.cuh"
 #include "ptx.cuh"
 #include "raster_dev.cuh"
@@ -264,32 +262,20 @@ __global__ void k_fill_empty(unsigned long long *__restrict__ keys, int64_t n)
 // the z-buffer of one frame (SM_NOALLOC_MAX_PIXELS 64-bit keys) followed by
 // the per-frame cameras (SM_NOALLOC_MAX_FRAMES x 48 bytes = 6 words each).
 // Host code may not use this name as an address; it asks the runtime for the
-// device address once per device (below).
+// device address of the current device's copy (below).
 static __device__ __align__(256) unsigned long long
     g_noalloc_scratch[SM_NOALLOC_MAX_PIXELS + 6 * SM_NOALLOC_MAX_FRAMES];
 
-namespace {
-std::mutex g_noalloc_mu;
-unsigned long long *g_noalloc_ptr[64] = {};  // device address of the scratch, per device ordinal
-}  // namespace
-
-// Device address of the static scratch on the current device; the first call
-// on a device looks it up (cudaGetSymbolAddress, which needs that device
-// current and allocates nothing).
+// Device address of the static scratch on the current device.  Looked up on
+// every call (cudaGetSymbolAddress needs that device current, allocates
+// nothing and is cheap), so that no address outlives the context it belongs
+// to (after a device reset the module, and with it the array, is reloaded).
 cudaError_t noalloc_scratch(unsigned long long **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = static_cast<unsigned long long *>(p);
-    }
-    *out = g_noalloc_ptr[dev];
+    *out = static_cast<unsigned long long *>(p);
     return cudaSuccess;
 }
 

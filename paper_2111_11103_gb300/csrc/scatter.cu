@@ -29,6 +29,8 @@
 //    when it is asked for, so no separate resolve pass runs.
 // Bounded waits: a wait longer than 2 s latches kErrTimeout; the producer
 // always waits for its own copies in flight before it leaves.
+#include <cstdlib>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -98,6 +100,8 @@ struct Args {
     uint32_t *cnt;
     int32_t *err;
     bool scale_bulk;           // per-pixel scales copied with the tile
+    uint64_t wait_ns;          // limit of every barrier wait
+    int skip_it;               // test hook: the producer skips this pipeline step (-1: never)
 };
 
 // Stage layout: probabilities | keys (8 B/px) or row ids (4 B/px) | scales.
@@ -538,10 +542,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
             for (int64_t t = blockIdx.x; t < ntiles_full; t += gridDim.x, ++it) {
                 const int s = it % stages;
                 const uint32_t ph = (uint32_t)(it / stages) & 1u;
-                if (it >= stages && !mbar_wait(empty + s, ph ^ 1u, kWaitNs)) {
+                if (it >= stages && !mbar_wait(empty + s, ph ^ 1u, a.wait_ns)) {
                     atomicCAS(a.err, 0, (int32_t)kErrTimeout);
                     break;
                 }
+                if (it == a.skip_it) continue;  // test hook: this stage is never filled
                 uint8_t *st = stage0 + (size_t)s * L.stride;
                 mbar_arrive_expect_tx(full + s, tx);
                 bulk_g2s(st, a.probs + (size_t)t * L.probs_bytes, L.probs_bytes, full + s, pol);
@@ -553,8 +558,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
             }
             // every issued copy has landed before this thread leaves
             for (int j = it - stages; j < it; ++j) {
-                if (j < 0) continue;
-                if (!mbar_wait(full + (j % stages), (uint32_t)(j / stages) & 1u, kWaitNs))
+                if (j < 0 || j == a.skip_it) continue;
+                if (!mbar_wait(full + (j % stages), (uint32_t)(j / stages) & 1u, a.wait_ns))
                     atomicCAS(a.err, 0, (int32_t)kErrTimeout);
             }
         }
@@ -569,7 +574,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter_tma(Args a, int stages)
         const int s = it % stages;
         const uint32_t ph = (uint32_t)(it / stages) & 1u;
         const uint8_t *st = stage0 + (size_t)s * L.stride;
-        if (!mbar_wait(full + s, ph, kWaitNs)) {
+        if (!mbar_wait(full + s, ph, a.wait_ns)) {
             atomicCAS(a.err, 0, (int32_t)kErrTimeout);
             return;
         }
@@ -692,7 +697,16 @@ void launch_scatter_tma(sm_rule rule, sm_dtype dtype, const void *probs, const f
 {
     if (total_px <= 0) return;
     Args a{static_cast<const uint8_t *>(probs), scale, keys, ids_in, ids_out, total_px, npix, c, fcnt, alpha, wpix,
-           n_x, acc, cnt, err, scale != nullptr && ((uintptr_t)scale & 15) == 0};
+           n_x, acc, cnt, err, scale != nullptr && ((uintptr_t)scale & 15) == 0, kWaitNs, -1};
+    // Test hook (failure detection without a GPU fault): with
+    // LABELFUSE_TEST_SKIP_TILE=k the producer of every CTA leaves its k-th
+    // pipeline step unfilled and every wait gives up after 5 ms, so the
+    // consumers' bounded waits run out, the kernel returns and the timeout is
+    // latched for sm_check.  Nothing waits without a limit.
+    if (const char *env = getenv("LABELFUSE_TEST_SKIP_TILE")) {
+        a.skip_it = atoi(env);
+        a.wait_ns = 5000000ull;
+    }
     switch (rule) {
     case SM_RULE_SUM: launch_rule<SM_RULE_SUM>(dtype, a, s); break;
     case SM_RULE_LOGSUM: launch_rule<SM_RULE_LOGSUM>(dtype, a, s); break;

@@ -346,9 +346,19 @@ def sm_last_error() -> str:
 def sm_render_rows_noalloc(vertices, faces, K, cam_to_world, N: int, H: int, W: int, idmap_out, stream=None):
     """Row maps (triangle per pixel) of N frames without any device allocation;
     for callers whose device memory is owned elsewhere (see labelfuse.h)."""
+    import contextlib
+    import torch
     V = int(vertices.shape[0]) if vertices is not None else 0
     F = int(faces.shape[0]) if faces is not None else 0
     n = max(0, int(N))
+    # the library runs the call on the device that holds the output: take
+    # that device's current stream unless one is given
+    on_dev = isinstance(idmap_out, torch.Tensor) and idmap_out.is_cuda
+    with (torch.cuda.device(idmap_out.device) if on_dev else contextlib.nullcontext()):
+        _render_rows_noalloc(vertices, V, faces, F, K, cam_to_world, N, H, W, idmap_out, n, stream)
+
+
+def _render_rows_noalloc(vertices, V, faces, F, K, cam_to_world, N, H, W, idmap_out, n, stream):
     _check(lib().sm_render_rows_noalloc(_arg(vertices, "vertices", 12 * V), V, _arg(faces, "faces", 12 * F), F,
                                         _arg(K, "K", 32 * n), _arg(cam_to_world, "cam_to_world", 128 * n), int(N),
                                         int(H), int(W), _arg(idmap_out, "idmap_out", 4 * max(0, N * H * W)),

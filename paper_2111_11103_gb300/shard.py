@@ -38,6 +38,24 @@ def allreduce_state(acc: torch.Tensor, cnt: torch.Tensor, group=None) -> None:
     dist.all_reduce(cnt, op=dist.ReduceOp.SUM, group=group)
 
 
+def complete_fusion(mesh: int, state=None, group=None) -> None:
+    """After each rank has fused its own frames into the mesh: one all-reduce
+    of the accumulators and counts, loaded back, so that every rank holds the
+    whole sequence's state.  state: optional (acc, cnt) buffers to reuse.
+    Enqueued on the current CUDA stream, which the collective follows."""
+    from . import labelfuse as lf
+    if state is None:
+        import torch
+        n_x, c = lf.sm_num_rows(mesh), lf.sm_num_classes(mesh)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        state = (torch.empty((max(n_x, 1), c), dtype=torch.float32, device=dev),
+                 torch.empty(max(n_x, 1), dtype=torch.int32, device=dev))
+    acc, cnt = state
+    lf.sm_read_state(mesh, acc, cnt)
+    allreduce_state(acc, cnt, group)
+    lf.sm_load_state(mesh, acc, cnt)
+
+
 def fuse_sharded(mesh: int, probs, dtype, scale, K, cam_to_world, H: int, W: int, rank: int, world: int,
                  idmap_out=None, group=None, state=None) -> tuple[int, int]:
     """Fuses this rank's frames of the sequence (probs, scale, K, cam_to_world
@@ -56,8 +74,5 @@ def fuse_sharded(mesh: int, probs, dtype, scale, K, cam_to_world, H: int, W: int
         n_x, c = lf.sm_num_rows(mesh), lf.sm_num_classes(mesh)
         state = (torch.empty((max(n_x, 1), c), dtype=torch.float32, device=probs.device),
                  torch.empty(max(n_x, 1), dtype=torch.int32, device=probs.device))
-    acc, cnt = state
-    lf.sm_read_state(mesh, acc, cnt)
-    allreduce_state(acc, cnt, group)
-    lf.sm_load_state(mesh, acc, cnt)
+    complete_fusion(mesh, state, group)
     return a, b

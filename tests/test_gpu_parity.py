@@ -68,8 +68,8 @@ def test_tiny_texels(ora, tiny, rule, weight):
     assert res.n_x == int(((s * s + s) // 2).sum())
 
 
-@pytest.mark.parametrize("rule,weight", [("logsum", "pixel"), ("sum", "pixel"), ("logsum", "image"),
-                                         ("vote", "pixel")])
+@pytest.mark.parametrize("rule", RULES)
+@pytest.mark.parametrize("weight", WEIGHTS)
 def test_medium_paper_room(ora, medium, rule, weight):
     scene, cams, probs = medium
     res = run_gpu(scene, cams, probs, rule, weight, reraster=(rule == "logsum" and weight == "pixel"))
@@ -108,6 +108,41 @@ def test_precision_forms(ora, medium, kind, rule):
     q, scale, deq = _quantise(probs, kind)
     res = run_gpu(scene, cams, q, rule, "pixel", dtype=kind, scale=scale, reraster=False)
     check_against_oracle(ora, scene, cams, deq, res, rule, "pixel", nthreads=8)
+
+
+@pytest.fixture(scope="module")
+def small_rooms(dev):
+    """Paper-shaped rooms at c = 40 and c = 20 (the two compile-time class
+    counts of the pipelined scatter) and the tiny room at c = 4 (its runtime
+    class count): ~20k triangles, 6 frames of 203 x 151 pixels (ragged against
+    every tile size) or the tiny configuration's 8 frames of 64 x 48."""
+    rooms = {}
+    cams = sg.random_walk_poses(6, H=151, W=203, fx=183.0, fy=183.0, cx=101.0, cy=75.0)
+    for c in (40, 20):
+        scene = sg.paper_room(target_faces=20_000, n_classes=c)
+        rooms[c] = (scene, cams, sg.predictions(scene, cams, "paper", device=dev))
+    scene, cams4 = sg.tiny_room(), sg.circle_poses()
+    rooms[4] = (scene, cams4, sg.predictions(scene, cams4, "tiny", device=dev))
+    return rooms
+
+
+@pytest.mark.parametrize("c", [40, 20, 4])
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8_e4m3"])
+@pytest.mark.parametrize("rule", RULES)
+@pytest.mark.parametrize("weight", WEIGHTS)
+def test_dispatch_matrix(ora, small_rooms, c, dtype, rule, weight):
+    """Every instantiation of the pipelined scatter that the library can
+    dispatch (class count 40, 20 or runtime; F32, BF16, FP8 E4M3 storage; the
+    four rules; pixel or image weights) against the oracle, which is fed the
+    same dequantised values for the compressed forms."""
+    scene, cams, probs = small_rooms[c]
+    assert scene.n_classes == c
+    if dtype == "f32":
+        q, scale, deq = probs, None, probs.cpu().numpy()
+    else:
+        q, scale, deq = _quantise(probs, dtype)
+    res = run_gpu(scene, cams, q, rule, weight, dtype=dtype, scale=scale, reraster=False)
+    check_against_oracle(ora, scene, cams, deq, res, rule, weight, nthreads=8)
 
 
 def test_ragged_and_tiny_images(ora, dev):
