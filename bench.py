@@ -183,18 +183,25 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def scatter_traffic_per_frame():
-    """DRAM bytes (read + write) per frame of the scatter kernel, from the
-    committed ncu summary, or None when the kernel's source has changed since
-    that capture (the counters would no longer describe it)."""
-    path = os.path.join(ROOT, "profiles", "scatter_paper_room.md")
+TRAFFIC_SOURCES = ("queue.cu", "scatter_dev.cuh", "raster_dev.cuh", "ptx.cuh")
+
+
+def source_sha(files=TRAFFIC_SOURCES) -> str:
+    sha = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2111_11103_gb300", "csrc", f), "rb") as fh:
+            sha.update(fh.read())
+    return sha.hexdigest()[:16]
+
+
+def queue_traffic_per_frame():
+    """DRAM bytes (read + write) per frame of the work-queue fusion kernel,
+    from the committed ncu summary, or None when the kernel's sources have
+    changed since that capture (the counters would no longer describe it)."""
+    path = os.path.join(ROOT, "profiles", "queue_paper_room.md")
     try:
         fields = dict(re.findall(r"^\s+(\w+): (\S+)$", open(path).read(), re.M))
-        sha = hashlib.sha256()
-        for f in ("scatter.cu", "ptx.cuh"):
-            with open(os.path.join(ROOT, "paper_2111_11103_gb300", "csrc", f), "rb") as fh:
-                sha.update(fh.read())
-        if sha.hexdigest()[:16] != fields.get("source_sha"):
+        if source_sha() != fields.get("source_sha"):
             return None
         return int(fields["traffic_bytes_per_launch"]) / int(fields["frames_per_launch"])
     except (OSError, KeyError, ValueError):
@@ -373,14 +380,17 @@ def run_ours(args):
         return ms_total / args.steps, {k: lf.sm_profile_read(m, k) for k in lf.SM_KERNEL}, clk.summary()
 
     def scatter_roofline(prof, elem_bytes, scaled):
-        """Roofline of the dominant kernel (the scatter): algorithmic bytes per
-        launch = predictions (+ per-pixel scales) + row-map bytes of the frames
-        one launch processes, over the launch's average event time."""
-        n_sc, ms_sc = prof["scatter"]
+        """Roofline of the dominant kernel (the work-queue fusion kernel, which
+        renders and scatters a whole call, or the scatter of the two-stream
+        path): algorithmic bytes per launch = predictions (+ per-pixel scales)
+        + row-map bytes of the frames one launch processes, over the launch's
+        average event time on its stream."""
+        kern = "queue" if prof.get("queue", (0, 0))[0] else "scatter"
+        n_sc, ms_sc = prof[kern]
         per_frame = H * W * c * elem_bytes + H * W * 4 + (H * W * 4 if scaled else 0)
         fpl = ring * n_loc * args.steps / max(n_sc, 1)
         achieved = per_frame * fpl / (ms_sc / max(n_sc, 1) / 1e3) / 1e9
-        return achieved, per_frame, fpl
+        return achieved, per_frame, fpl, kern
 
     # frames per launch: the library's autotuner on a 256-frame sample
     n_tune = min(256, n_loc)
@@ -414,10 +424,10 @@ def run_ours(args):
     ms_step, prof, clocks = timed("f32", probs, None)
     launches = sum(n for n, _ in prof.values())
     value = ring * N / (ms_step / 1e3)  # the whole sequence (x ring), split over the ranks
-    achieved, bytes_per_frame_scatter, frames_per_launch = scatter_roofline(prof, 4, False)
+    achieved, bytes_per_frame_scatter, frames_per_launch, dom = scatter_roofline(prof, 4, False)
     peak, peak_kind = peaks()
     kernels = {k: {"launches": n, "ms_per_step": t / args.steps} for k, (n, t) in prof.items() if n}
-    tpf = scatter_traffic_per_frame()
+    tpf = queue_traffic_per_frame() if dom == "queue" else None
     traffic = None if tpf is None or (H, W, c) != (480, 640, 40) else tpf * frames_per_launch
 
     line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
@@ -427,7 +437,7 @@ def run_ours(args):
             "l2": l2_note(probs.numel() * probs.element_size()),
             "frames_per_launch": tuned_B, "frame_range": [fa, fb],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "kernel": "scatter",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": dom,
                          "algorithmic_bytes_per_launch": bytes_per_frame_scatter * frames_per_launch,
                          "frames_per_launch": frames_per_launch, "peak_kind": peak_kind},
             "kernels": kernels,
@@ -505,10 +515,10 @@ def storage_forms(probs, timed, scatter_roofline, peak, N, steps):
     for kind, dt, eb in (("bf16", "bf16", 2), ("fp8_e4m3", "fp8_e4m3", 1)):
         q, scale = quantise(probs, kind)
         ms, prof, clocks = timed(dt, q, scale)
-        achieved, per_frame, fpl = scatter_roofline(prof, eb, True)
+        achieved, per_frame, fpl, dom = scatter_roofline(prof, eb, True)
         out[kind] = {"value": N / (ms / 1e3), "unit": "frames/s", "ms_per_step": ms,
                      "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                                  "frac": achieved / peak, "kernel": "scatter",
+                                  "frac": achieved / peak, "kernel": dom,
                                   "algorithmic_bytes_per_frame": per_frame, "frames_per_launch": fpl},
                      "kernels": {k: {"launches": n, "ms_per_step": t / steps} for k, (n, t) in prof.items() if n},
                      "clocks": clocks}

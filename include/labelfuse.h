@@ -213,8 +213,32 @@ sm_status sm_texel_res_from_gamma(sm_mesh *m, const sm_intrinsics *d_K, const do
                                   int32_t H, int32_t W, float gamma, int32_t *d_area_out, int32_t *d_texel_res_out,
                                   void *stream);
 
-/* Autotuner of the frames per launch (the paper has no counterpart: a
- * throughput setting of this implementation).  Fuses the given frames twice per
+/* Shape of the work-queue fusion (the paper has no counterpart: a throughput
+ * setting of this implementation).  For a mesh uploaded without texel steps,
+ * with pixel weights w^(P) and c = 20 or 40, sm_fuse_frames runs the renderer
+ * and the scatter of a whole call in one persistent kernel that takes work
+ * items from a device queue: frames are cut into batches of
+ * frames_per_batch frames; raster items (one frame, raster_rounds x 1,152
+ * clusters of 32 faces) run `lookahead` batches ahead of scatter items
+ * (scatter_tiles tiles of 256 pixels), on the same SMs.  This call sets that
+ * shape for later calls with frames of H x W pixels; results do not depend on
+ * it.  frames_per_batch = 0 makes this mesh use the two-stream path (a raster
+ * launch and a scatter launch per batch) instead.
+ *   frames_per_batch  0, or a multiple of 4 in [4, 128]  (default 8)
+ *   lookahead         [0, 4]                               (default 1)
+ *   raster_rounds     [1, 64]                              (default 1)
+ *   scatter_tiles     [1, 4096]                            (default 32)
+ * Errors: SM_ERR_INVALID_ARG. */
+sm_status sm_set_queue_shape(sm_mesh *m, int32_t H, int32_t W, int32_t frames_per_batch, int32_t lookahead,
+                             int32_t raster_rounds, int32_t scatter_tiles);
+
+/* Autotuner of the launch shape (the paper has no counterpart: a throughput
+ * setting of this implementation).  For a mesh that fuses through the work
+ * queue (see sm_set_queue_shape) it tunes the queue's shape one parameter at
+ * a time from the defaults (frames per batch in {4, 8, 12, 16, 24, 32, 48},
+ * lookahead in {0, 1, 2}, raster rounds in {1, 2, 4}, scatter tiles in {16,
+ * 32, 64, 128}) and *best_out receives the frames per batch.  Otherwise it
+ * tunes the frames per launch of the two-stream path: fuses the given frames twice per
  * candidate batch size (multiples of 4 up to 128 frames, both z-buffer slots
  * within 1 GB; the first pass sizes the scratch buffers), times the second on
  * `stream` with CUDA events, and keeps the
@@ -389,7 +413,8 @@ typedef enum sm_kernel {
     SM_K_SCATTER = 4,   /* probability stream -> accumulator rows              */
     SM_K_NORMALISE = 5, /* rows -> distributions and labels                    */
     SM_K_RENDER = 6,    /* row maps -> label images                            */
-    SM_K_COUNT_KINDS = 7
+    SM_K_QUEUE = 7,     /* raster + scatter of a whole call in the work queue  */
+    SM_K_COUNT_KINDS = 8
 } sm_kernel;
 
 sm_status sm_profile_enable(sm_mesh *m, int32_t on);

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "liblabelfuse.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "raster.cu", "fuse.cu", "mesh.cu", "scatter.cu", "confidence.cu"]
+SOURCES = ["api.cu", "raster.cu", "fuse.cu", "mesh.cu", "scatter.cu", "queue.cu", "confidence.cu"]
 
 
 def nvcc() -> str:

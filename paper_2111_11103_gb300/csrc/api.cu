@@ -184,13 +184,15 @@ sm_status raster_batch(sm_mesh *m, int f0, int nb, int H, int W, int32_t *idm, c
 // Elements per z-buffer slot, rounded so every slot starts 256-byte aligned.
 int64_t slot_stride(int B, int64_t npix) { return ((int64_t)B * npix + 31) & ~31LL; }
 
+// Cameras of N frames (set up on the device) and z-buffer room for `slots`
+// slots of B frames; every key is empty between calls.
 sm_status prepare_frames(sm_mesh *m, const sm_intrinsics *d_K, const double *d_T, int N, int64_t npix, int B,
-                         bool need_idbuf, cudaStream_t s)
+                         bool need_idbuf, cudaStream_t s, int slots = 2)
 {
     sm_status st;
     if ((st = grow(&m->cams, &m->cams_cap, N, s, -1, "camera buffer")) != SM_OK) return st;
-    // two z-buffer slots (raster of batch b+1 overlaps the scatter of batch b)
-    if ((st = grow(&m->keys, &m->keys_cap, 2 * slot_stride(B, npix), s, 0xFF, "z-buffer")) != SM_OK) return st;
+    // (two slots for the stream path: raster of batch b+1 beside the scatter of batch b)
+    if ((st = grow(&m->keys, &m->keys_cap, slots * slot_stride(B, npix), s, 0xFF, "z-buffer")) != SM_OK) return st;
     if (need_idbuf && (st = grow(&m->idbuf, &m->idbuf_cap, (int64_t)B * npix, s, -1, "row-map buffer")) != SM_OK)
         return st;
     {
@@ -198,6 +200,84 @@ sm_status prepare_frames(sm_mesh *m, const sm_intrinsics *d_K, const double *d_T
         lf::launch_project(d_K, d_T, N, m->cams, s);
     }
     LF_LAUNCHED("camera set-up");
+    return SM_OK;
+}
+
+// Shape of the work-queue fusion for frames of npix pixels: the tuned or set
+// shape, else defaults (8-frame batches, raster one batch ahead, one cull
+// round per raster item, 32 tiles per scatter item).
+struct QueueShape {
+    int B, L, R, S;
+};
+
+QueueShape queue_shape(const sm_mesh *m, int64_t npix)
+{
+    QueueShape q{8, 1, 1, 32};
+    if (m->q_npix == npix) {
+        if (m->qB > 0) q.B = m->qB;
+        if (m->qL > 0) q.L = m->qL;
+        if (m->qR > 0) q.R = m->qR;
+        if (m->qS > 0) q.S = m->qS;
+    }
+    return q;
+}
+
+// Fusion of N frames in face mode with pixel weights through the persistent
+// work-queue kernel: full batches in one launch, the remaining frames (fewer
+// than a batch) in a second.
+sm_status fuse_queue_impl(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
+                          const sm_intrinsics *d_K, const double *d_T, int32_t N, int32_t H, int32_t W,
+                          int32_t *d_idmap_out, cudaStream_t s)
+{
+    const int64_t npix = (int64_t)H * W;
+    const QueueShape qs = queue_shape(m, npix);
+    const int B = N < qs.B ? N : qs.B;  // a multiple of 4 unless it is the whole call
+    const int slots = qs.L + 2;
+    const int nfull = N / B, rem = N - nfull * B;
+    sm_status st;
+    if ((st = prepare_frames(m, d_K, d_T, N, npix, B, false, s, slots)) != SM_OK) return st;
+    const int nbmax = nfull > 1 ? nfull : 1;
+    if ((st = grow(&m->qctr, &m->qctr_cap, (int64_t)lf::fuse_queue_counter_words(nbmax), s, -1, "queue counters")) !=
+        SM_OK)
+        return st;
+    const size_t esz = dtype_size(dtype);
+    lf::FuseQueueLaunch l{};
+    l.V = m->verts;
+    l.faces = m->faces;
+    l.F = m->F;
+    l.bounds = m->bounds;
+    l.H = H;
+    l.W = W;
+    l.npix = npix;
+    l.dtype = dtype;
+    l.c = m->c;
+    l.rule = m->rule;
+    l.acc = m->acc;
+    l.cnt = m->cnt;
+    l.n_x = m->n_x;
+    l.err = m->err;
+    l.keys = m->keys;
+    l.slot_stride = slot_stride(B, npix);
+    l.lookahead = qs.L;
+    l.raster_rounds = qs.R;
+    l.scatter_tiles = qs.S;
+    l.counters = m->qctr;
+    for (int part = 0; part < 2; ++part) {
+        const int f0 = part == 0 ? 0 : nfull * B;
+        l.nb = part == 0 ? nfull : (rem > 0 ? 1 : 0);
+        l.B = part == 0 ? B : rem;
+        if (l.nb == 0) continue;
+        l.cams = m->cams + f0;
+        l.probs = static_cast<const char *>(d_probs) + (size_t)f0 * npix * m->c * esz;
+        l.scale = d_scale ? d_scale + (size_t)f0 * npix : nullptr;
+        l.ids_out = d_idmap_out ? d_idmap_out + (int64_t)f0 * npix : nullptr;
+        {
+            ProfScope p(m, SM_K_QUEUE, s);
+            lf::launch_fuse_queue(l, s);
+        }
+        LF_LAUNCHED("fusion work queue");
+    }
+    m->normalised = false;
     return SM_OK;
 }
 
@@ -224,6 +304,10 @@ sm_status fuse_impl(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float
     // face mode with the pipelined scatter: the scatter reads the z-buffer
     // keys itself; otherwise a resolve pass writes the row map first
     const bool from_keys = tma && !m->texel_mode;
+    // face mode with pixel weights and c = 20 / 40: raster and scatter of the
+    // whole call in the persistent work-queue kernel
+    if (from_keys && !image_w && !d_weights && lf::fuse_queue_supported(m->c) && !m->stream_path)
+        return fuse_queue_impl(m, d_probs, dtype, d_scale, d_K, d_cam_to_world, N, H, W, d_idmap_out, s);
     const bool need_ids = !from_keys || image_w;
     // the pipelined scatter reads its row map from the library's aligned buffer
     const bool ids_internal = need_ids && (!d_idmap_out || (tma && !from_keys));
@@ -542,42 +626,123 @@ sm_status sm_autotune_batch(sm_mesh *m, const void *d_probs, sm_dtype dtype, con
         cudaEventDestroy(e0);
         return fail(SM_ERR_CUDA, "events");
     }
-    int best = 0;
-    float best_ms = 0.0f;
-    const int saved_B = m->tuned_B;
-    const int64_t saved_npix = m->tuned_npix;
-    // candidates: multiples of 4 frames whose two z-buffer slots stay within 1 GB
-    for (int B = 4; B <= 128 && B <= N && (int64_t)B * npix * 16 <= (1024ll << 20); B += 4) {
-        m->tuned_B = B;
-        m->tuned_npix = npix;
-        const int n = (N / B) * B;  // whole launches only
+    // time of one fusion of the first n frames per frame (two passes: the
+    // first sizes the scratch buffers, the second is timed)
+    auto per_frame = [&](int n, float *out) -> sm_status {
         float ms = 0.0f;
-        for (int rep = 0; rep < 2 && st == SM_OK; ++rep) {  // the first pass grows the scratch
-            if ((st = sm_reset(m, stream)) != SM_OK) break;
-            if (cudaEventRecord(e0, s) != cudaSuccess) st = fail(SM_ERR_CUDA, "event");
-            if (st == SM_OK) st = sm_fuse_frames(m, d_probs, dtype, d_scale, d_K, d_cam_to_world, n, H, W, nullptr, stream);
-            if (st == SM_OK && cudaEventRecord(e1, s) != cudaSuccess) st = fail(SM_ERR_CUDA, "event");
-            if (st == SM_OK && cudaEventSynchronize(e1) != cudaSuccess) st = fail(SM_ERR_CUDA, "synchronise");
-            if (st == SM_OK) cudaEventElapsedTime(&ms, e0, e1);
+        sm_status r = SM_OK;
+        for (int rep = 0; rep < 2 && r == SM_OK; ++rep) {
+            if ((r = sm_reset(m, stream)) != SM_OK) break;
+            if (cudaEventRecord(e0, s) != cudaSuccess) r = fail(SM_ERR_CUDA, "event");
+            if (r == SM_OK) r = sm_fuse_frames(m, d_probs, dtype, d_scale, d_K, d_cam_to_world, n, H, W, nullptr, stream);
+            if (r == SM_OK && cudaEventRecord(e1, s) != cudaSuccess) r = fail(SM_ERR_CUDA, "event");
+            if (r == SM_OK && cudaEventSynchronize(e1) != cudaSuccess) r = fail(SM_ERR_CUDA, "synchronise");
+            if (r == SM_OK) cudaEventElapsedTime(&ms, e0, e1);
         }
-        if (st != SM_OK) break;
-        const float per_frame = ms / (float)n;
-        if (best == 0 || per_frame < best_ms) {
-            best = B;
-            best_ms = per_frame;
+        *out = ms / (float)n;
+        return r;
+    };
+    const bool queue = !m->texel_mode && m->weight == SM_WEIGHT_PIXEL && lf::scatter_tma_supported(m->c) &&
+                       lf::fuse_queue_supported(m->c) && !m->stream_path;
+    int best = 0;
+    if (queue) {
+        // work-queue shape, one parameter at a time from the defaults:
+        // frames per batch, raster lookahead, cull rounds per raster item,
+        // tiles per scatter item
+        const QueueShape saved{m->qB, m->qL, m->qR, m->qS};
+        const int64_t saved_npix = m->q_npix;
+        QueueShape cur = queue_shape(m, -1);
+        m->q_npix = npix;
+        auto apply = [&](const QueueShape &q) {
+            m->qB = q.B;
+            m->qL = q.L;
+            m->qR = q.R;
+            m->qS = q.S;
+        };
+        float best_ms = 0.0f;
+        apply(cur);
+        st = per_frame(N, &best_ms);
+        const int Bs[] = {4, 8, 12, 16, 24, 32, 48}, Ls[] = {0, 1, 2}, Rs[] = {1, 2, 4}, Ss[] = {16, 32, 64, 128};
+        for (int dim = 0; dim < 4 && st == SM_OK; ++dim) {
+            const int *vals = dim == 0 ? Bs : dim == 1 ? Ls : dim == 2 ? Rs : Ss;
+            const int nv = dim == 0 ? 7 : dim == 1 ? 3 : dim == 2 ? 3 : 4;
+            for (int k = 0; k < nv && st == SM_OK; ++k) {
+                QueueShape c = cur;
+                int *field = dim == 0 ? &c.B : dim == 1 ? &c.L : dim == 2 ? &c.R : &c.S;
+                if (*field == vals[k] || (dim == 0 && vals[k] > N)) continue;
+                *field = vals[k];
+                apply(c);
+                float ms = 0.0f;
+                if ((st = per_frame(N, &ms)) != SM_OK) break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    cur = c;
+                }
+            }
+        }
+        if (st == SM_OK) st = sm_reset(m, stream);
+        if (st != SM_OK) {
+            apply(saved);
+            m->q_npix = saved_npix;
+        } else {
+            apply(cur);
+            best = cur.B;
+        }
+    } else {
+        float best_ms = 0.0f;
+        const int saved_B = m->tuned_B;
+        const int64_t saved_npix = m->tuned_npix;
+        // candidates: multiples of 4 frames whose two z-buffer slots stay within 1 GB
+        for (int B = 4; B <= 128 && B <= N && (int64_t)B * npix * 16 <= (1024ll << 20); B += 4) {
+            m->tuned_B = B;
+            m->tuned_npix = npix;
+            float ms = 0.0f;
+            if ((st = per_frame((N / B) * B, &ms)) != SM_OK) break;  // whole launches only
+            if (best == 0 || ms < best_ms) {
+                best = B;
+                best_ms = ms;
+            }
+        }
+        if (st == SM_OK) st = sm_reset(m, stream);
+        if (st != SM_OK || best == 0) {
+            m->tuned_B = saved_B;
+            m->tuned_npix = saved_npix;
+        } else {
+            m->tuned_B = best;
+            m->tuned_npix = npix;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (st == SM_OK) st = sm_reset(m, stream);
-    if (st != SM_OK || best == 0) {
-        m->tuned_B = saved_B;
-        m->tuned_npix = saved_npix;
-        return st != SM_OK ? st : fail(SM_ERR_INTERNAL, "autotuner found no candidate");
-    }
-    m->tuned_B = best;
-    m->tuned_npix = npix;
+    if (st != SM_OK) return st;
+    if (best == 0) return fail(SM_ERR_INTERNAL, "autotuner found no candidate");
     if (best_out) *best_out = best;
+    return SM_OK;
+}
+
+sm_status sm_set_queue_shape(sm_mesh *m, int32_t H, int32_t W, int32_t frames_per_batch, int32_t lookahead,
+                             int32_t raster_rounds, int32_t scatter_tiles)
+{
+    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
+    sm_status st = check_image(0, H, W);
+    if (st != SM_OK) return st;
+    if (frames_per_batch == 0) {
+        m->stream_path = true;
+        return SM_OK;
+    }
+    if (frames_per_batch < 4 || frames_per_batch > 128 || (frames_per_batch & 3) != 0)
+        return fail(SM_ERR_INVALID_ARG, "frames per batch %d: a multiple of 4 in [4, 128], or 0", frames_per_batch);
+    if (lookahead < 0 || lookahead > 4) return fail(SM_ERR_INVALID_ARG, "lookahead %d outside [0, 4]", lookahead);
+    if (raster_rounds < 1 || raster_rounds > 64)
+        return fail(SM_ERR_INVALID_ARG, "raster rounds %d outside [1, 64]", raster_rounds);
+    if (scatter_tiles < 1 || scatter_tiles > 4096)
+        return fail(SM_ERR_INVALID_ARG, "scatter tiles %d outside [1, 4096]", scatter_tiles);
+    m->stream_path = false;
+    m->qB = frames_per_batch;
+    m->qL = lookahead;
+    m->qR = raster_rounds;
+    m->qS = scatter_tiles;
+    m->q_npix = (int64_t)H * W;
     return SM_OK;
 }
 
@@ -827,7 +992,7 @@ sm_status sm_mesh_free(sm_mesh *m)
         cudaDeviceSynchronize();
         void *bufs[] = {m->verts, m->faces,  m->row0,   m->texinfo, m->acc,     m->cnt,    m->labels8,
                         m->err,   m->cams,   m->keys,   m->idbuf,   m->fcnt,    m->bounds, m->hstage,
-                        m->hids,  m->hlabels, m->hcam,  m->clist,   m->ccount, m->area};
+                        m->hids,  m->hlabels, m->hcam,  m->clist,   m->ccount, m->area,    m->qctr};
         for (void *b : bufs)
             if (b) cudaFree(b);
         if (m->rstream) cudaStreamDestroy(m->rstream);

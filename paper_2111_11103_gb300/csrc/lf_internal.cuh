@@ -99,6 +99,42 @@ void launch_scatter_tma(sm_rule rule, sm_dtype dtype, const void *probs, const f
                         unsigned long long *keys, const int32_t *ids_in, int32_t *ids_out, int64_t total_px,
                         int64_t npix, int c, const uint32_t *fcnt, float alpha, const float *wpix, int64_t n_x,
                         float *acc, uint32_t *cnt, int32_t *err, cudaStream_t s);
+// Persistent fusion kernel with a device work queue (queue.cu): raster and
+// scatter of nb batches of B frames in one launch (face mode, pixel weights,
+// c = 20 or 40).  keys: lookahead + 2 slots of slot_stride keys, all empty on
+// entry and on return; counters: fuse_queue_counter_words(nb) words, zeroed
+// by the launch.
+struct FuseQueueLaunch {
+    const float4 *V;
+    const int4 *faces;
+    int64_t F;
+    const float4 *bounds;
+    const Camera *cams;  // first frame of the launch
+    int H, W;
+    int64_t npix;
+    const void *probs;   // first frame of the launch
+    const float *scale;
+    sm_dtype dtype;
+    int c;
+    sm_rule rule;
+    int32_t *ids_out;    // optional, first frame of the launch
+    float *acc;
+    uint32_t *cnt;
+    int64_t n_x;
+    int32_t *err;
+    unsigned long long *keys;
+    int64_t slot_stride;
+    int nb, B;
+    int lookahead;       // batches the raster runs ahead of the scatter
+    int raster_rounds;   // cull rounds (fuse_queue_raster_round() clusters each) per raster item
+    int scatter_tiles;   // 256-pixel tiles per scatter item
+    uint32_t *counters;
+};
+bool fuse_queue_supported(int c);
+int fuse_queue_raster_round();
+uint32_t fuse_queue_counter_words(int nb);
+void launch_fuse_queue(const FuseQueueLaunch &l, cudaStream_t s);
+
 // Visible-area pre-pass (fuse.cu): per-frame pixel counts of the triangles in
 // a batch's z-buffers (re-armed), folded into per-triangle maxima; texel
 // steps from the maxima.
@@ -141,6 +177,11 @@ struct sm_mesh {
     float alpha = 1.0f;  // image-weight mix (sm_set_weight_mix)
     int tuned_B = 0;          // frames per launch chosen by sm_autotune_batch ...
     int64_t tuned_npix = 0;   // ... for frames of this many pixels
+    // shape of the work-queue fusion (sm_set_queue_shape / sm_autotune_batch)
+    // for frames of q_npix pixels; zero fields take the defaults
+    int qB = 0, qL = 0, qR = 0, qS = 0;
+    int64_t q_npix = 0;
+    bool stream_path = false;  // sm_set_queue_shape(..., 0 frames): keep the two-stream path
     bool texel_mode = false;
     bool normalised = false;
 
@@ -169,6 +210,8 @@ struct sm_mesh {
     int64_t idbuf_cap = 0;
     uint32_t *fcnt = nullptr;
     int64_t fcnt_cap = 0;
+    uint32_t *qctr = nullptr;  // work-queue head, completion counts and abort flag
+    int64_t qctr_cap = 0;
 
     // raster stream + events that pipeline raster(batch b+1) with scatter(batch b)
     cudaStream_t rstream = nullptr;

@@ -122,6 +122,23 @@ __device__ __forceinline__ void red_add_u32(uint32_t *addr, uint32_t v, uint64_t
     asm volatile("red.global.add.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(addr), "r"(v), "l"(policy) : "memory");
 }
 
+// Load with acquire semantics at GPU scope: later accesses of this thread are
+// ordered after it (pairs with a release such as __threadfence + atomic).
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Orders this thread's earlier generic-proxy accesses of global memory
+// (including what an acquire made visible to it) before its later async-proxy
+// (bulk copy) accesses of global memory.
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 __device__ __forceinline__ void red_min_u64(unsigned long long *addr, unsigned long long v)
 {
     asm volatile("red.global.min.u64 [%0], %1;" ::"l"(addr), "l"(v) : "memory");

@@ -88,14 +88,10 @@ __global__ void k_cluster_bounds(const float4 *__restrict__ V, const int4 *__res
     }
 }
 
-// Cluster cull of one batch: one thread per (cluster, frame) evaluates the 8
-// corners of the cluster's world box in homogeneous image coordinates.  If
-// one affine bound is violated at all corners it is violated everywhere in
-// the box: every vertex then projects more than 2 pixels left of / right of /
-// above / below the image, or lies in front of the near plane (so the
-// renderer drops every triangle anyway); the 2-pixel and 0.01 m margins
-// dwarf the binary32 evaluation error.  Every other cluster is appended to
-// its frame's list (one atomic per warp).  blockIdx.y = frame in the batch.
+// Cluster cull of one batch: one thread per (cluster, frame) applies the
+// conservative frustum test (cluster_may_be_visible) and appends the clusters
+// that may be visible to its frame's list (one atomic per warp).
+// blockIdx.y = frame in the batch.
 __global__ void __launch_bounds__(256) k_cull_clusters(const float4 *__restrict__ bounds, int64_t ncl,
                                                        const Camera *__restrict__ cams, int frame0, int H, int W,
                                                        int32_t *__restrict__ list, uint32_t *__restrict__ count)
@@ -105,26 +101,7 @@ __global__ void __launch_bounds__(256) k_cull_clusters(const float4 *__restrict_
     if (threadIdx.x < 12) A[threadIdx.x] = cams[frame0 + b].a[threadIdx.x];
     __syncthreads();
     const int64_t cl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool keep = false;
-    if (cl < ncl) {
-        const float4 lo = bounds[2 * cl], hi = bounds[2 * cl + 1];
-        if (lo.w == 0.0f) {
-            bool left = true, right = true, top = true, bottom = true, near = true;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const float px = (k & 1) ? hi.x : lo.x, py = (k & 2) ? hi.y : lo.y, pz = (k & 4) ? hi.z : lo.z;
-                const float X = A[0] * px + A[1] * py + A[2] * pz + A[3];
-                const float Y = A[4] * px + A[5] * py + A[6] * pz + A[7];
-                const float Z = A[8] * px + A[9] * py + A[10] * pz + A[11];
-                left = left && X + 512.0f * Z < 0.0f;
-                right = right && X - 256.0f * (float)(W + 1) * Z > 0.0f;
-                top = top && Y + 512.0f * Z < 0.0f;
-                bottom = bottom && Y - 256.0f * (float)(H + 1) * Z > 0.0f;
-                near = near && Z < kZNear - 0.01f;
-            }
-            keep = !(left || right || top || bottom || near);
-        }
-    }
+    const bool keep = cl < ncl && cluster_may_be_visible(bounds, cl, A, H, W);
     const unsigned mask = __ballot_sync(0xffffffffu, keep);
     if (!mask) return;
     const int lane = threadIdx.x & 31;

@@ -139,6 +139,35 @@ __device__ __forceinline__ void raster_box(const Tri &t, int x0, int x1, int y0,
     }
 }
 
+// Conservative frustum test of one 32-face cluster for one frame (A: the
+// frame's camera rows).  The 8 corners of the cluster's world box are
+// evaluated in homogeneous image coordinates; if one affine bound is violated
+// at all corners it is violated everywhere in the box: every vertex then
+// projects more than 2 pixels left of / right of / above / below the image,
+// or lies in front of the near plane, so the renderer drops every triangle of
+// the cluster anyway.  The 2-pixel and 0.01 m margins dwarf the binary32
+// evaluation error, so a culled cluster never holds a pixel.
+__device__ __forceinline__ bool cluster_may_be_visible(const float4 *__restrict__ bounds, int64_t cl, const float *A,
+                                                       int H, int W)
+{
+    const float4 lo = bounds[2 * cl], hi = bounds[2 * cl + 1];
+    if (lo.w != 0.0f) return false;  // no valid face
+    bool left = true, right = true, top = true, bottom = true, near = true;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float px = (k & 1) ? hi.x : lo.x, py = (k & 2) ? hi.y : lo.y, pz = (k & 4) ? hi.z : lo.z;
+        const float X = A[0] * px + A[1] * py + A[2] * pz + A[3];
+        const float Y = A[4] * px + A[5] * py + A[6] * pz + A[7];
+        const float Z = A[8] * px + A[9] * py + A[10] * pz + A[11];
+        left = left && X + 512.0f * Z < 0.0f;
+        right = right && X - 256.0f * (float)(W + 1) * Z > 0.0f;
+        top = top && Y + 512.0f * Z < 0.0f;
+        bottom = bottom && Y - 256.0f * (float)(H + 1) * Z > 0.0f;
+        near = near && Z < kZNear - 0.01f;
+    }
+    return !(left || right || top || bottom || near);
+}
+
 // Set-up and box walk of face f for one frame (one thread per face; faces
 // past F, dropped by the packer, or culled by set-up draw nothing).
 __device__ __forceinline__ void raster_face(const float *A, const float4 *__restrict__ V,

@@ -26,7 +26,8 @@ LIB_PATH = os.path.join(PKG, "liblabelfuse.so")
 SM_RULE = {"sum": 0, "logsum": 1, "maxsum": 2, "vote": 3}
 SM_WEIGHT = {"pixel": 0, "image": 1}
 SM_DTYPE = {"f32": 0, "bf16": 1, "fp8_e4m3": 2}
-SM_KERNEL = {"project": 0, "raster": 1, "resolve": 2, "count": 3, "scatter": 4, "normalise": 5, "render": 6}
+SM_KERNEL = {"project": 0, "raster": 1, "resolve": 2, "count": 3, "scatter": 4, "normalise": 5, "render": 6,
+             "queue": 7}
 SM_OK = 0
 SM_ERR_INVALID_ARG = 1
 SM_MAX_CLASSES = 254
@@ -35,7 +36,7 @@ SYMBOLS = ["sm_mesh_upload", "sm_fuse_frames", "sm_normalise", "sm_render_labels
            "sm_status_string", "sm_last_error", "sm_profile_enable", "sm_profile_read", "sm_render_rows_noalloc",
            "sm_fuse_render_host", "sm_host_alloc", "sm_host_free", "sm_set_weight_mix", "sm_texel_res_from_gamma",
            "sm_autotune_batch", "sm_fuse_frames_weighted", "sm_conf_features", "sm_conf_targets", "sm_conf_forward",
-           "sm_conf_train_step"]
+           "sm_conf_train_step", "sm_set_queue_shape"]
 SM_CONF_FEATURES = 5
 SM_CONF_PARAMS = 1281
 SM_NOALLOC_MAX_PIXELS = 1572864
@@ -84,6 +85,7 @@ def lib() -> ctypes.CDLL:
             "sm_conf_targets": [P, P, i32, P, P, i64, P, P],
             "sm_conf_forward": [P, P, i64, P, P],
             "sm_conf_train_step": [P, P, P, i64, ctypes.c_float, P, P, P],
+            "sm_set_queue_shape": [P, i32, i32, i32, i32, i32, i32],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -222,6 +224,14 @@ def sm_autotune_batch(mesh: int, probs, dtype, scale, K, cam_to_world, N: int, H
     _check(lib().sm_autotune_batch(mesh, p, dt, sc, k, t, int(N), int(H), int(W), ctypes.byref(best),
                                    _stream(stream)))
     return best.value
+
+
+def sm_set_queue_shape(mesh: int, H: int, W: int, frames_per_batch: int, lookahead: int = 1, raster_rounds: int = 1,
+                       scatter_tiles: int = 32):
+    """Shape of the work-queue fusion for H x W frames; frames_per_batch = 0
+    selects the two-stream path for this mesh."""
+    _check(lib().sm_set_queue_shape(mesh, int(H), int(W), int(frames_per_batch), int(lookahead), int(raster_rounds),
+                                    int(scatter_tiles)))
 
 
 def sm_fuse_frames_weighted(mesh: int, probs, dtype, scale, K, cam_to_world, N: int, H: int, W: int, weights,

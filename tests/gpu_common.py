@@ -42,7 +42,10 @@ def to_dev(scene, cams, texel_res=None, dev="cuda"):
 
 
 def run_gpu(scene, cams, probs, rule, weight, texel_res=None, dtype="f32", scale=None, reraster=True,
-            n_classes=None, alpha=None):
+            n_classes=None, alpha=None, queue_shape=None):
+    """Fuses, normalises and renders through the C ABI.  queue_shape: None
+    (the library's choice), 0 (the two-stream path) or (frames per batch,
+    lookahead, raster rounds, scatter tiles) of the work-queue path."""
     from paper_2111_11103_gb300 import labelfuse as lf
     dev = probs.device
     N, H, W = cams.K.shape[0], cams.H, cams.W
@@ -52,6 +55,8 @@ def run_gpu(scene, cams, probs, rule, weight, texel_res=None, dtype="f32", scale
     try:
         if alpha is not None:
             lf.sm_set_weight_mix(m, alpha)
+        if queue_shape is not None:
+            lf.sm_set_queue_shape(m, H, W, *((0,) if queue_shape == 0 else tuple(queue_shape)))
         n_x = lf.sm_num_rows(m)
         idm = torch.full((N, H, W), -7, dtype=torch.int32, device=dev)
         lf.sm_fuse_frames(m, probs, dtype, scale, K, T, N, H, W, idm)

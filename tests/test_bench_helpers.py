@@ -34,12 +34,13 @@ def test_quantise_scales_and_codes():
         assert float(q.float().amax()) == top  # the largest class maps to the top code exactly
 
 
-def test_scatter_traffic_lookup_follows_the_source_hash():
-    """The committed capture's traffic is used only while the kernel source
-    it was taken on is unchanged; then it is a plausible per-frame figure."""
+def test_traffic_lookup_follows_the_source_hash():
+    """The committed capture's traffic is used only while the kernel sources
+    it was taken on are unchanged; then it is a plausible per-frame figure."""
     b = _bench()
-    tpf = b.scatter_traffic_per_frame()
-    assert tpf is None or 5.0e7 < tpf < 6.0e7  # bytes per 640 x 480 x 40 frame
+    tpf = b.queue_traffic_per_frame()
+    assert tpf is None or 5.0e7 < tpf < 6.5e7  # bytes per 640 x 480 x 40 frame
+    assert len(b.source_sha()) == 16
 
 
 def test_l2_note_states_the_resident_size():

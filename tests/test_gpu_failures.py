@@ -52,10 +52,24 @@ def _fuse_and_compare(ora, lf, m, dev, scene, cams, probs, rule, weight):
     assert_acc_close(acc.cpu().numpy(), A)
 
 
-@pytest.mark.parametrize("weight", ["pixel", "image"])
-def test_scatter_wait_runs_out_and_recovers(ora, tiny, monkeypatch, weight):
+@pytest.fixture()
+def room20():
+    """A small paper-shaped room with c = 20: pixel weights fuse through the
+    persistent work-queue kernel."""
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    dev = torch.device("cuda:0")
+    scene = sg.paper_room(target_faces=20_000, n_classes=20)
+    cams = sg.random_walk_poses(8, H=96, W=128, fx=115.0, fy=115.0, cx=63.5, cy=47.5)
+    return dev, scene, cams, sg.predictions(scene, cams, "paper", device=dev)
+
+
+@pytest.mark.parametrize("case,weight", [("tiny", "pixel"), ("tiny", "image"), ("room20", "pixel")])
+def test_scatter_wait_runs_out_and_recovers(ora, request, monkeypatch, case, weight):
+    """Stream-ordered scatter (c = 4, both weights) and the work-queue kernel
+    (c = 20, pixel weights): a stage that is never filled makes the waits give
+    up; the call is reported as SM_ERR_TIMEOUT and the next one is exact."""
     from paper_2111_11103_gb300 import labelfuse as lf
-    dev, scene, cams, probs = tiny
+    dev, scene, cams, probs = request.getfixturevalue(case)
     N, H, W, c = cams.K.shape[0], cams.H, cams.W, scene.n_classes
     V, Fc, K, T, _ = to_dev(scene, cams, None, dev)
     m = lf.sm_mesh_upload(V, Fc, None, c, "logsum", weight)

@@ -126,23 +126,41 @@ def small_rooms(dev):
     return rooms
 
 
+PATHS = [("image", None), ("pixel", None), ("pixel", 0)]  # (weight, queue_shape): queue / two-stream paths
+
+
 @pytest.mark.parametrize("c", [40, 20, 4])
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8_e4m3"])
 @pytest.mark.parametrize("rule", RULES)
-@pytest.mark.parametrize("weight", WEIGHTS)
-def test_dispatch_matrix(ora, small_rooms, c, dtype, rule, weight):
-    """Every instantiation of the pipelined scatter that the library can
-    dispatch (class count 40, 20 or runtime; F32, BF16, FP8 E4M3 storage; the
-    four rules; pixel or image weights) against the oracle, which is fed the
-    same dequantised values for the compressed forms."""
+@pytest.mark.parametrize("weight,path", PATHS)
+def test_dispatch_matrix(ora, small_rooms, c, dtype, rule, weight, path):
+    """Every kernel instantiation that the library can dispatch against the
+    oracle: class count 40, 20 or runtime; F32, BF16, FP8 E4M3 storage; the
+    four rules; image weights (two-stream path), pixel weights through the
+    work-queue kernel (c = 20, 40) and through the two-stream path.  The
+    oracle is fed the same dequantised values for the compressed forms."""
     scene, cams, probs = small_rooms[c]
     assert scene.n_classes == c
     if dtype == "f32":
         q, scale, deq = probs, None, probs.cpu().numpy()
     else:
         q, scale, deq = _quantise(probs, dtype)
-    res = run_gpu(scene, cams, q, rule, weight, dtype=dtype, scale=scale, reraster=False)
+    res = run_gpu(scene, cams, q, rule, weight, dtype=dtype, scale=scale, reraster=False, queue_shape=path)
     check_against_oracle(ora, scene, cams, deq, res, rule, weight, nthreads=8)
+
+
+@pytest.mark.parametrize("shape", [(4, 0, 1, 1), (4, 1, 1, 7), (8, 2, 2, 32), (12, 1, 4, 4096), (16, 3, 1, 64),
+                                   (128, 1, 1, 32)])
+@pytest.mark.parametrize("rule", ["logsum", "maxsum"])
+def test_queue_shapes(ora, medium, shape, rule):
+    """The work-queue kernel under uneven shapes: 24 frames of 203 x 151 in
+    batches of 4 to 128 frames (a remainder batch, or one batch shorter than
+    the set length), the raster 0 to 3 batches ahead, raster items of 1 to 4
+    cull rounds, scatter items of 1 to 4096 tiles (one item per batch, and
+    items that end on a batch's partial tile): results against the oracle."""
+    scene, cams, probs = medium
+    res = run_gpu(scene, cams, probs, rule, "pixel", reraster=False, queue_shape=shape)
+    check_against_oracle(ora, scene, cams, probs.cpu().numpy(), res, rule, "pixel", nthreads=8)
 
 
 def test_ragged_and_tiny_images(ora, dev):
