@@ -59,8 +59,13 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay timing")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default frames per launch")
     ap.add_argument("--scenes", type=int, default=0,
-                    help="batched form: this many independent rooms of uneven size, fused one by one, side by side "
-                         "on streams, and as one captured CUDA graph")
+                    help="batched form: this many independent rooms of uneven size (64 for the stated spread), fused "
+                         "one by one, side by side on streams, through work-queue launches, and as a CUDA graph")
+    ap.add_argument("--ring", type=int, default=16, help="--scenes: resident frames per room")
+    ap.add_argument("--learned", action="store_true",
+                    help="learned-confidence form: the 4M-triangle apartment, --frames frames (5000 by default), "
+                         "4 texel steps, plain against confidence-weighted fusion")
+    ap.add_argument("--train-frames", type=int, default=160, help="--learned: frames whose observations train the net")
     ap.add_argument("--coarse", action="store_true",
                     help="pixel accuracy of the fused render-back for meshes of 500k to 5k triangles, with texel "
                          "steps from gamma = 0 and 0.2 (a synthetic analogue of the paper's mesh-simplification study)")
@@ -574,88 +579,232 @@ def e2e(args, lf, scene, probs, K, T, dev, stream, h_probs=None):
 
 
 def run_scenes(args):
-    """Batched form, scaled to one GPU's memory: independent procedural rooms
-    with triangles log-uniform in [50k, 500k], 40-160 frames, 320 x 240 or
-    640 x 480, c = 20 or 40 (seeded).  A step fuses and normalises every room
-    and renders every frame; frames/s over all rooms for three launch modes."""
-    import numpy as np
+    """Batched form (BASELINE config 4): args.scenes independent procedural
+    rooms with triangles log-uniform in [50k, 2M], 200-3,000 frames,
+    resolutions drawn from 320 x 240 / 640 x 480 / 1296 x 968, c = 20 or 40,
+    FP32 or BF16 predictions (seeded).  The spread's predictions would take
+    terabytes, so each room keeps a ring of --ring resident frames and fuses
+    them round after round until it has fused its N frames (a repeated
+    observation is a valid one under every rule).  A step fuses every room's N
+    frames, normalises every room and renders the ring's frames of every room
+    from their row maps; frames/s = sum of N over the step time.  Launch
+    modes: one room after another (sm_fuse_frames), rooms side by side on four
+    streams, all rooms of a round in one sm_fuse_scenes call (work-queue
+    launches grouped by class count and storage type), and that step captured
+    as one CUDA graph."""
     from paper_2111_11103_gb300 import labelfuse as lf
-    from paper_2111_11103_gb300.scenes import SceneJob, fuse_scenes
+    from paper_2111_11103_gb300.scenes import SceneJob, fuse_scenes, fuse_scenes_queued
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     rng = np.random.default_rng(2111111034)
+    R = args.ring
     rooms = []
+    t_gen = time.perf_counter()
     for i in range(args.scenes):
-        F = int(np.exp(rng.uniform(np.log(5e4), np.log(5e5))))
-        N = int(rng.integers(40, 161))
-        H, W, f = ((240, 320, 288.8) if rng.uniform() < 0.5 else (480, 640, 577.6))
+        F = int(np.exp(rng.uniform(np.log(5e4), np.log(2e6))))
+        N = int(rng.integers(200, 3001))
+        H, W, f = [(240, 320, 288.8), (480, 640, 577.6), (968, 1296, 1170.0)][int(rng.integers(0, 3))]
         c = 20 if rng.uniform() < 0.5 else 40
+        dtype = "f32" if rng.uniform() < 0.5 else "bf16"
         scene = sg.paper_room(seed=1000 + i, target_faces=F, n_classes=c)
-        cams = sg.random_walk_poses(N, seed=2000 + i, H=H, W=W, fx=f, fy=f, cx=W / 2 - 0.5, cy=H / 2 - 0.5)
+        cams = sg.random_walk_poses(R, seed=2000 + i, H=H, W=W, fx=f, fy=f, cx=W / 2 - 0.5, cy=H / 2 - 0.5)
         probs = sg.predictions(scene, cams, "paper", device=dev)
+        scale = None
+        if dtype == "bf16":
+            probs, scale = quantise(probs, "bf16")
         K = torch.as_tensor(cams.K, device=dev)
-        T = torch.as_tensor(cams.cam_to_world.reshape(N, 16), device=dev)
+        T = torch.as_tensor(cams.cam_to_world.reshape(R, 16), device=dev)
         m = lf.sm_mesh_upload(torch.as_tensor(scene.vertices, device=dev), torch.as_tensor(scene.faces, device=dev),
                               None, c, "logsum", "pixel")
-        idm = torch.empty((N, H, W), dtype=torch.int32, device=dev)
-        img = torch.empty((N, H, W), dtype=torch.uint8, device=dev)
-        rooms.append((m, SceneJob(m, probs, K, T, H, W, idmap_out=idm,
-                                  labels_out=torch.empty(lf.sm_num_rows(m), dtype=torch.int32, device=dev)), img))
-    frames = sum(int(j.K.shape[0]) for _, j, _ in rooms)
+        idm = torch.empty((R, H, W), dtype=torch.int32, device=dev)
+        img = torch.empty((R, H, W), dtype=torch.uint8, device=dev)
+        rooms.append({"mesh": m, "N": N, "H": H, "W": W, "c": c, "dtype": dtype, "faces": int(scene.faces.shape[0]),
+                      "probs": probs, "scale": scale, "K": K, "T": T, "idm": idm, "img": img})
+    t_gen = time.perf_counter() - t_gen
+    frames = sum(r["N"] for r in rooms)
+    rounds = max((r["N"] + R - 1) // R for r in rooms)
 
-    def render_all():
-        for m, j, img in rooms:
-            lf.sm_render_idmap(m, j.idmap_out, img.numel(), img)
+    def round_jobs(k):
+        """Every room still fusing in round k, with its frames of that round."""
+        jobs = []
+        for r in rooms:
+            n = min(R, r["N"] - k * R)
+            if n > 0:
+                jobs.append(SceneJob(r["mesh"], r["probs"][:n], r["K"][:n], r["T"][:n], r["H"], r["W"], r["dtype"],
+                                     None if r["scale"] is None else r["scale"][:n], idmap_out=r["idm"][:n]))
+        return jobs
+
+    plans = [round_jobs(k) for k in range(rounds)]
+
+    def finish():
+        for r in rooms:
+            lf.sm_normalise(r["mesh"])
+            lf.sm_render_idmap(r["mesh"], r["idm"], r["idm"].numel(), r["img"])
+
+    def reset():
+        for r in rooms:
+            lf.sm_reset(r["mesh"])
 
     def one_by_one():
-        for m, j, _ in rooms:
-            lf.sm_reset(m)
-            lf.sm_fuse_frames(m, j.probs, "f32", None, j.K, j.cam_to_world, int(j.K.shape[0]), j.H, j.W, j.idmap_out)
-            lf.sm_normalise(m, None, j.labels_out)
-        render_all()
+        reset()
+        for jobs in plans:
+            for j in jobs:
+                lf.sm_fuse_frames(j.mesh, j.probs, j.dtype, j.scale, j.K, j.cam_to_world, int(j.K.shape[0]), j.H, j.W,
+                                  j.idmap_out)
+        finish()
 
     def side_by_side():
-        for m, _, _ in rooms:
-            lf.sm_reset(m)
-        fuse_scenes([j for _, j, _ in rooms], streams=4)
-        render_all()
+        reset()
+        for jobs in plans:
+            fuse_scenes(jobs, streams=4)
+        finish()
+
+    def queued():
+        reset()
+        for jobs in plans:
+            fuse_scenes_queued(jobs)
+        finish()
 
     def timing(fn):
         for _ in range(max(args.warmup, 3)):
             fn()
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.steps):
-            fn()
-        e1.record()
-        torch.cuda.synchronize(dev)
-        return e0.elapsed_time(e1) / args.steps
+        with ClockSampler(0) as clk:
+            e0.record()
+            for _ in range(args.steps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / args.steps, clk.summary()
 
     out = {}
-    for name, fn in (("one_by_one", one_by_one), ("side_by_side", side_by_side)):
-        ms = timing(fn)
-        out[name] = {"value": frames / (ms / 1e3), "unit": "frames/s", "ms_per_step": ms}
+    for name, fn in (("one_by_one", one_by_one), ("side_by_side", side_by_side), ("work_queue", queued)):
+        ms, clk = timing(fn)
+        out[name] = {"value": frames / (ms / 1e3), "unit": "frames/s", "ms_per_step": ms, "clocks": clk}
     g = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):
-        side_by_side()
+        queued()
     torch.cuda.current_stream().wait_stream(side)
     with torch.cuda.graph(g):
-        side_by_side()
-    ms = timing(g.replay)
-    out["graph"] = {"value": frames / (ms / 1e3), "unit": "frames/s", "ms_per_step": ms}
-    for m, _, _ in rooms:
-        lf.sm_check(m)
-        lf.sm_mesh_free(m)
-    best = max(out.values(), key=lambda v: v["value"])
+        queued()
+    ms, clk = timing(g.replay)
+    out["work_queue_graph"] = {"value": frames / (ms / 1e3), "unit": "frames/s", "ms_per_step": ms, "clocks": clk}
+    for r in rooms:
+        lf.sm_check(r["mesh"])
+        lf.sm_mesh_free(r["mesh"])
+    best_name = max(out, key=lambda k: out[k]["value"])
+    best = out[best_name]
     line = {"metric": "frames/s fuse+render, batched independent rooms", "value": best["value"], "unit": "frames/s",
             "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": best["ms_per_step"],
-            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{args.scenes} rooms, 50k-500k triangles, 40-160 frames, 320x240 or 640x480, "
-                                   f"c = 20 or 40", "frames": frames, "rule": "logsum", "weight": "pixel"},
-            "modes": out}
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32/bf16", "data": "synthetic",
+            "config": {"workload": f"{args.scenes} rooms, 50k-2M triangles, 200-3000 frames, 320x240 / 640x480 / "
+                                   f"1296x968, c = 20 or 40, FP32 or BF16", "frames": frames, "ring": R,
+                       "rounds": rounds, "rule": "logsum", "weight": "pixel",
+                       "rooms": [{k: r[k] for k in ("faces", "N", "H", "W", "c", "dtype")} for r in rooms]},
+            "best_mode": best_name, "modes": out, "generation_s": t_gen, "clocks": best["clocks"]}
+    print(json.dumps(line), flush=True)
+
+
+def run_learned(args):
+    """Learned form (BASELINE config 5): the 4M-triangle apartment (four
+    rooms joined by doors), --frames frames of 640 x 480 (5,000 by default),
+    c = 40, 4 texel steps per triangle (10 texels), predictions of the
+    "structured" recipe (confidently wrong more often at grazing angles, far
+    away and near the border) stored as FP8 E4M3 with a per-pixel scale so
+    that the whole sequence stays resident.  The confidence network is
+    trained on the observations of a sample of frames, labelled by agreement
+    with the plain fused labels; then the whole sequence is fused plainly and
+    weighted by the network, and each fusion's render-back is scored by pixel
+    accuracy against the synthetic ground truth.  Also timed: the fused
+    inference (features + network, per frame) against the fusion itself."""
+    from paper_2111_11103_gb300 import confidence as conf
+    from paper_2111_11103_gb300 import labelfuse as lf
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    N = args.frames
+    t0 = time.perf_counter()
+    scene = sg.apartment(target_faces=args.faces if args.faces != 500_000 else 4_000_000)
+    cams = sg.apartment_poses(N)
+    H, W, c = cams.H, cams.W, scene.n_classes
+    q = torch.empty((N, H, W, c), dtype=torch.float8_e4m3fn, device=dev)
+    scale = torch.empty((N, H, W), dtype=torch.float32, device=dev)
+    gt_all = torch.empty((N, H, W), dtype=torch.int8, device=dev)  # ground truth, kept for the scoring
+    for a in range(0, N, 25):
+        b = min(N, a + 25)
+        p = sg.predictions(scene, cams, "structured", frames=range(a, b), device=dev, gt_out=gt_all[a:b])
+        q[a:b], scale[a:b] = quantise(p, "fp8_e4m3")
+        del p
+    t_gen = time.perf_counter() - t0
+    K = torch.as_tensor(cams.K, device=dev)
+    T = torch.as_tensor(cams.cam_to_world.reshape(N, 16), device=dev)
+    V = torch.as_tensor(scene.vertices, device=dev)
+    Fc = torch.as_tensor(scene.faces, device=dev)
+    s_t = torch.full((len(scene.faces),), 4, dtype=torch.int32, device=dev)
+    m = lf.sm_mesh_upload(V, Fc, s_t, c, "logsum", "pixel")
+    n_x = lf.sm_num_rows(m)
+    # training on a sample of frames spread over the sequence
+    n_train = min(N, args.train_frames)
+    sel = torch.linspace(0, N - 1, n_train, device=dev).round().long()
+    qs, ss, Ks, Ts = q[sel].contiguous(), scale[sel].contiguous(), K[sel].contiguous(), T[sel].contiguous()
+    t0 = time.perf_counter()
+    params, losses = conf.train(m, qs, Ks, Ts, H, W, steps=300, lr=1.0, batch=200_000, dtype="fp8_e4m3", scale=ss)
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t0
+    del qs, ss
+    idm = torch.empty((N, H, W), dtype=torch.int32, device=dev)
+    w = torch.empty((N, H, W), dtype=torch.float32, device=dev)
+    out = {}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for mode in ("plain", "weighted"):
+        lf.sm_reset(m)
+        torch.cuda.synchronize(dev)
+        ev[0].record()
+        if mode == "plain":
+            lf.sm_fuse_frames(m, q, "fp8_e4m3", scale, K, T, N, H, W, idm)
+            ev[1].record()
+        else:
+            lf.sm_conf_weights(m, q, "fp8_e4m3", scale, K, T, N, H, W, params, w, idm)
+            ev[1].record()
+            lf.sm_fuse_frames_weighted(m, q, "fp8_e4m3", scale, K, T, N, H, W, w, idm)
+        ev[2].record()
+        lf.sm_normalise(m)
+        torch.cuda.synchronize(dev)
+        lf.sm_check(m)
+        # render-back of every frame, scored against the ray-cast ground truth in chunks
+        hit = tot = 0
+        img = torch.empty((25, H, W), dtype=torch.uint8, device=dev)
+        for a in range(0, N, 25):
+            b = min(N, a + 25)
+            lf.sm_render_idmap(m, idm[a:b], (b - a) * H * W, img[:b - a])
+            gt = gt_all[a:b].long()
+            seen = gt >= 0
+            hit += int((img[:b - a].long()[seen] == gt[seen]).sum())
+            tot += int(seen.sum())
+        entry = {"pixel_accuracy": hit / max(tot, 1), "covered_pixels": tot,
+                 "fusion_ms": ev[1].elapsed_time(ev[2]) if mode == "weighted" else ev[0].elapsed_time(ev[1])}
+        if mode == "weighted":
+            entry["inference_ms"] = ev[0].elapsed_time(ev[1])
+            entry["inference_us_per_frame"] = 1e3 * entry["inference_ms"] / N
+        out[mode] = entry
+    raw_hit = raw_tot = 0
+    for a in range(0, N, 25):
+        b = min(N, a + 25)
+        am = (q[a:b].float() * scale[a:b, ..., None]).argmax(-1)
+        gt = gt_all[a:b].long()
+        seen = gt >= 0
+        raw_hit += int((am[seen] == gt[seen]).sum())
+        raw_tot += int(seen.sum())
+    lf.sm_mesh_free(m)
+    line = {"study": "learned per-observation confidence, weighted vs plain fusion", "frames": N, "H": H, "W": W,
+            "classes": c, "triangles": int(scene.faces.shape[0]), "texel_rows": n_x, "texel_steps": 4,
+            "storage": "fp8_e4m3 + per-pixel scale", "recipe": "structured", "rule": "logsum",
+            "train_frames": n_train, "train_steps": 300, "loss_first_last": [float(losses[0]), float(losses[-1])],
+            "raw_argmax_accuracy": raw_hit / max(raw_tot, 1), "plain": out["plain"], "weighted": out["weighted"],
+            "gain": out["weighted"]["pixel_accuracy"] - out["plain"]["pixel_accuracy"],
+            "generation_s": t_gen, "training_s": t_train}
     print(json.dumps(line), flush=True)
 
 
@@ -718,6 +867,11 @@ def main():
         return
     if args.coarse:
         run_coarse(args)
+        return
+    if args.learned:
+        if args.frames == 1000:
+            args.frames = 5000
+        run_learned(args)
         return
     if args.scenes:
         run_scenes(args)

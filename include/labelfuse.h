@@ -213,39 +213,74 @@ sm_status sm_texel_res_from_gamma(sm_mesh *m, const sm_intrinsics *d_K, const do
                                   int32_t H, int32_t W, float gamma, int32_t *d_area_out, int32_t *d_texel_res_out,
                                   void *stream);
 
-/* Shape of the work-queue fusion (the paper has no counterpart: a throughput
- * setting of this implementation).  For a mesh uploaded without texel steps,
- * with pixel weights w^(P) and c = 20 or 40, sm_fuse_frames runs the renderer
- * and the scatter of a whole call in one persistent kernel that takes work
- * items from a device queue: frames are cut into batches of
- * frames_per_batch frames; raster items (one frame, raster_rounds x 1,152
- * clusters of 32 faces) run `lookahead` batches ahead of scatter items
- * (scatter_tiles tiles of 256 pixels), on the same SMs.  This call sets that
- * shape for later calls with frames of H x W pixels; results do not depend on
- * it.  frames_per_batch = 0 makes this mesh use the two-stream path (a raster
- * launch and a scatter launch per batch) instead.
- *   frames_per_batch  0, or a multiple of 4 in [4, 128]  (default 8)
- *   lookahead         [0, 4]                               (default 1)
+/* Frames of one scene for sm_fuse_scenes: the arguments of sm_fuse_frames
+ * (device pointers, same layouts) for one mesh. */
+typedef struct sm_scene_frames {
+    sm_mesh *mesh;
+    const void *d_probs;            /* N x H x W x c, HWC, dtype; 16-byte aligned */
+    sm_dtype dtype;
+    const float *d_scale;           /* N x H x W, NULL iff SM_F32 */
+    const sm_intrinsics *d_K;       /* N */
+    const double *d_cam_to_world;   /* N x 16 row-major */
+    int32_t N, H, W;
+    int32_t *d_idmap_out;           /* N x H x W or NULL */
+} sm_scene_frames;
+
+/* Fuses the frames of many independent scenes, each into its own mesh, as
+ * sm_fuse_frames would one after another (Sec. 3.3.1 and 3.3.2 per scene;
+ * batching many scenes is a throughput setting of this implementation, the
+ * paper has no counterpart).  Scenes whose meshes have no texel steps, pixel
+ * weights w^(P) and c = 20 or 40 go through the persistent work-queue kernel:
+ * those with the same class count, storage type and rule share one launch
+ * (up to 12 scenes; plus one launch for the frames past their last full
+ * batch), whose CTAs take (scene, frame batch) raster and scatter items from
+ * a device queue, so uneven scenes leave no launch tails between them.  The
+ * queue shape of each scene is its mesh's (sm_set_queue_shape or
+ * sm_autotune_batch for its frame size, else the defaults).  Other scenes are
+ * fused by sm_fuse_frames on the same stream.  Meshes must be distinct and on
+ * one device.  Everything is enqueued on `stream`; results per scene equal
+ * sm_fuse_frames'.
+ * Errors: SM_ERR_INVALID_ARG (NULL, shared mesh, meshes on different devices,
+ * n > 1024, any argument sm_fuse_frames would refuse, reported with the
+ * scene's index), SM_ERR_OOM, SM_ERR_CUDA. */
+sm_status sm_fuse_scenes(const sm_scene_frames *scenes, int32_t n, void *stream);
+
+/* Launch path and shape of the fusion (the paper has no counterpart: a
+ * throughput setting of this implementation; results do not depend on it).
+ * By default sm_fuse_frames takes the two-stream path: per batch of frames a
+ * raster launch (cluster cull + raster) on a second stream and a persistent
+ * scatter launch.  For a mesh uploaded without texel steps, with pixel
+ * weights w^(P) and c = 20 or 40, a non-zero frames_per_batch switches the
+ * mesh to the work-queue path: one persistent kernel per call takes work
+ * items from a device queue, raster items (one frame, raster_rounds x 1,152
+ * clusters of 32 faces) running `lookahead` batches ahead of scatter items
+ * (scatter_tiles tiles of 256 pixels) and spread evenly among them, so that
+ * raster and scatter share the SMs without a launch boundary between batches.
+ * The shape applies to later calls with frames of H x W pixels (other sizes
+ * take the defaults).  frames_per_batch = 0 returns the mesh to the
+ * two-stream path.
+ *   frames_per_batch  0, or a multiple of 4 in [4, 128]  (default 32)
+ *   lookahead         [1, 4]                               (default 2)
  *   raster_rounds     [1, 64]                              (default 1)
- *   scatter_tiles     [1, 4096]                            (default 32)
+ *   scatter_tiles     [1, 4096]                            (default 128)
  * Errors: SM_ERR_INVALID_ARG. */
 sm_status sm_set_queue_shape(sm_mesh *m, int32_t H, int32_t W, int32_t frames_per_batch, int32_t lookahead,
                              int32_t raster_rounds, int32_t scatter_tiles);
 
-/* Autotuner of the launch shape (the paper has no counterpart: a throughput
- * setting of this implementation).  For a mesh that fuses through the work
- * queue (see sm_set_queue_shape) it tunes the queue's shape one parameter at
- * a time from the defaults (frames per batch in {4, 8, 12, 16, 24, 32, 48},
- * lookahead in {0, 1, 2}, raster rounds in {1, 2, 4}, scatter tiles in {16,
- * 32, 64, 128}) and *best_out receives the frames per batch.  Otherwise it
- * tunes the frames per launch of the two-stream path: fuses the given frames twice per
- * candidate batch size (multiples of 4 up to 128 frames, both z-buffer slots
- * within 1 GB; the first pass sizes the scratch buffers), times the second on
- * `stream` with CUDA events, and keeps the
- * fastest per-frame time for frames of H x W pixels: later calls on this mesh
- * with that frame size launch that many frames at a time (results do not
- * depend on it).  Synchronises `stream`; resets the accumulators (P and
- * counts are zero afterwards).  *best_out, if not NULL, receives the choice.
+/* Autotuner of the launch path and shape (the paper has no counterpart: a
+ * throughput setting of this implementation).  Tunes the frames per launch
+ * of the two-stream path: fuses the given frames twice per candidate batch
+ * size (multiples of 4 up to 128 frames, both z-buffer slots within 1 GB; the
+ * first pass sizes the scratch buffers) and times the second on `stream`
+ * with CUDA events.  For a mesh that the work-queue path applies to (see
+ * sm_set_queue_shape) it then tunes the queue's shape one parameter at a
+ * time from its defaults (frames per batch in {8, 16, 24, 32, 48, 64},
+ * lookahead in {1, 2, 3}, raster rounds in {1, 2, 4}, scatter tiles in {32,
+ * 64, 128, 256}) and keeps whichever path has the faster per-frame time.
+ * Later calls on this mesh with frames of H x W pixels use the choice
+ * (results do not depend on it).  Synchronises `stream`; resets the
+ * accumulators (P and counts are zero afterwards).  *best_out, if not NULL,
+ * receives the chosen frames per launch (or per batch of the queue).
  *   d_probs ...  N >= 4 frames as for sm_fuse_frames (a representative
  *                sample: 2-4 x 128 frames is plenty).
  * Errors: SM_ERR_INVALID_ARG, SM_ERR_OOM, SM_ERR_CUDA. */
@@ -287,6 +322,23 @@ sm_status sm_fuse_frames_weighted(sm_mesh *m, const void *d_probs, sm_dtype dtyp
 sm_status sm_conf_features(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
                            const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N, int32_t H, int32_t W,
                            float *d_feat_out, int32_t *d_rows_out, void *stream);
+
+/* Learned confidence inference in one pass (an extension of the weighted
+ * rules of Sec. 3.2.2; the paper has no counterpart): renders the N frames
+ * (as sm_fuse_frames) and, per pixel, computes the five features of
+ * sm_conf_features and the network's weight w = sigmoid(o) of
+ * sm_conf_forward, without writing the features out.  The 32 x 32 hidden
+ * layer runs on the tensor cores with its inputs (the first layer's ReLU
+ * activations) rounded to bfloat16 and float32 accumulation, so w differs
+ * from sm_conf_forward's by that rounding (about 1e-3 at most).
+ *   d_params     SM_CONF_PARAMS float32 (device).
+ *   d_w_out      N x H x W float32: w, 0 for background pixels.
+ *   d_rows_out   N x H x W int32: the row map (-1 = background).
+ * The result feeds sm_fuse_frames_weighted.  Leaves the accumulators
+ * untouched.  Errors: SM_ERR_INVALID_ARG, SM_ERR_OOM, SM_ERR_CUDA. */
+sm_status sm_conf_weights(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
+                          const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N, int32_t H, int32_t W,
+                          const float *d_params, float *d_w_out, int32_t *d_rows_out, void *stream);
 
 /* Training targets: d_target_out[k] = 1 where pixel k's first arg max equals
  * the fused label of its row d_rows[k], else 0 (background, unseen rows).

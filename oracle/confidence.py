@@ -48,14 +48,18 @@ def unpack(params):
     return out
 
 
-def forward(params, X, rounding: bool = True):
+def forward(params, X, rounding: bool = True, act_bf16: bool = False):
     """o and w = sigmoid(o) for observations X (n x 5), with the parameters
     rounded to bfloat16 (rounding=False: as given, for finite differences);
-    also returns the hidden activations for backward."""
+    also returns the hidden activations for backward.  act_bf16: the first
+    layer's activations are rounded to bfloat16 before the hidden layer, the
+    precision of a hidden layer computed on bfloat16 tensor cores."""
     W1, b1, W2, b2, w3, b3 = unpack(bf16_round(params) if rounding else params)
     X = np.asarray(X, dtype=np.float64)
     z1 = X @ W1.T + b1
     h1 = np.maximum(z1, 0.0)
+    if act_bf16:
+        h1 = bf16_round(h1)
     z2 = h1 @ W2.T + b2
     h2 = np.maximum(z2, 0.0)
     o = h2 @ w3 + b3[0]

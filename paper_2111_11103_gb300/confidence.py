@@ -49,12 +49,11 @@ def train(mesh: int, probs, K, cam_to_world, H: int, W: int, steps: int = 200, l
 def fuse_with_confidence(mesh: int, params, probs, K, cam_to_world, H: int, W: int, dtype="f32", scale=None,
                          idmap_out=None):
     """Fuses the frames into the mesh with each observation weighed by the
-    network's confidence."""
+    network's confidence (features and network in one pass, sm_conf_weights,
+    then sm_fuse_frames_weighted).  Returns the weights."""
     N, dev = int(K.shape[0]), probs.device
-    feat = torch.empty((N, H, W, lf.SM_CONF_FEATURES), device=dev)
     rows = torch.empty((N, H, W), dtype=torch.int32, device=dev)
-    lf.sm_conf_features(mesh, probs, dtype, scale, K, cam_to_world, N, H, W, feat, rows)
     w = torch.empty((N, H, W), device=dev)
-    lf.sm_conf_forward(params, feat, N * H * W, w)
+    lf.sm_conf_weights(mesh, probs, dtype, scale, K, cam_to_world, N, H, W, params, w, rows)
     lf.sm_fuse_frames_weighted(mesh, probs, dtype, scale, K, cam_to_world, N, H, W, w, idmap_out)
     return w

@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "lf_internal.cuh"
 
@@ -204,15 +205,16 @@ sm_status prepare_frames(sm_mesh *m, const sm_intrinsics *d_K, const double *d_T
 }
 
 // Shape of the work-queue fusion for frames of npix pixels: the tuned or set
-// shape, else defaults (8-frame batches, raster one batch ahead, one cull
-// round per raster item, 32 tiles per scatter item).
+// shape, else defaults (32-frame batches, raster two batches ahead, one cull
+// round per raster item, 128 tiles per scatter item: the fastest measured on
+// the paper-shaped workload).
 struct QueueShape {
     int B, L, R, S;
 };
 
 QueueShape queue_shape(const sm_mesh *m, int64_t npix)
 {
-    QueueShape q{8, 1, 1, 32};
+    QueueShape q{32, 2, 1, 128};
     if (m->q_npix == npix) {
         if (m->qB > 0) q.B = m->qB;
         if (m->qL > 0) q.L = m->qL;
@@ -222,12 +224,17 @@ QueueShape queue_shape(const sm_mesh *m, int64_t npix)
     return q;
 }
 
-// Fusion of N frames in face mode with pixel weights through the persistent
-// work-queue kernel: full batches in one launch, the remaining frames (fewer
-// than a batch) in a second.
-sm_status fuse_queue_impl(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
-                          const sm_intrinsics *d_K, const double *d_T, int32_t N, int32_t H, int32_t W,
-                          int32_t *d_idmap_out, cudaStream_t s)
+// One scene's pieces for work-queue launches: cameras set up and z-buffer
+// slots grown; the full batches in pieces of at most fuse_queue_max_batches()
+// batches, then the remaining frames (fewer than a batch) as one more piece.
+struct QueuePrep {
+    std::vector<lf::FuseQueueScene> full, rest;
+    int lookahead = 1;
+};
+
+sm_status prepare_queue_scene(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
+                              const sm_intrinsics *d_K, const double *d_T, int32_t N, int32_t H, int32_t W,
+                              int32_t *d_idmap_out, cudaStream_t s, QueuePrep *out)
 {
     const int64_t npix = (int64_t)H * W;
     const QueueShape qs = queue_shape(m, npix);
@@ -236,12 +243,11 @@ sm_status fuse_queue_impl(sm_mesh *m, const void *d_probs, sm_dtype dtype, const
     const int nfull = N / B, rem = N - nfull * B;
     sm_status st;
     if ((st = prepare_frames(m, d_K, d_T, N, npix, B, false, s, slots)) != SM_OK) return st;
-    const int nbmax = nfull > 1 ? nfull : 1;
-    if ((st = grow(&m->qctr, &m->qctr_cap, (int64_t)lf::fuse_queue_counter_words(nbmax), s, -1, "queue counters")) !=
-        SM_OK)
+    if ((st = grow(&m->qctr, &m->qctr_cap, (int64_t)lf::fuse_queue_counter_words(lf::fuse_queue_max_batches()), s,
+                   -1, "queue counters")) != SM_OK)
         return st;
     const size_t esz = dtype_size(dtype);
-    lf::FuseQueueLaunch l{};
+    lf::FuseQueueScene l{};
     l.V = m->verts;
     l.faces = m->faces;
     l.F = m->F;
@@ -249,36 +255,79 @@ sm_status fuse_queue_impl(sm_mesh *m, const void *d_probs, sm_dtype dtype, const
     l.H = H;
     l.W = W;
     l.npix = npix;
-    l.dtype = dtype;
-    l.c = m->c;
-    l.rule = m->rule;
     l.acc = m->acc;
     l.cnt = m->cnt;
     l.n_x = m->n_x;
     l.err = m->err;
     l.keys = m->keys;
     l.slot_stride = slot_stride(B, npix);
-    l.lookahead = qs.L;
+    l.slots = slots;
     l.raster_rounds = qs.R;
     l.scatter_tiles = qs.S;
-    l.counters = m->qctr;
-    for (int part = 0; part < 2; ++part) {
-        const int f0 = part == 0 ? 0 : nfull * B;
-        l.nb = part == 0 ? nfull : (rem > 0 ? 1 : 0);
-        l.B = part == 0 ? B : rem;
-        if (l.nb == 0) continue;
-        l.cams = m->cams + f0;
-        l.probs = static_cast<const char *>(d_probs) + (size_t)f0 * npix * m->c * esz;
-        l.scale = d_scale ? d_scale + (size_t)f0 * npix : nullptr;
-        l.ids_out = d_idmap_out ? d_idmap_out + (int64_t)f0 * npix : nullptr;
-        {
-            ProfScope p(m, SM_K_QUEUE, s);
-            lf::launch_fuse_queue(l, s);
-        }
-        LF_LAUNCHED("fusion work queue");
-    }
+    l.owner = m;
+    auto piece = [&](int f0, int nb, int Bp) {
+        lf::FuseQueueScene p = l;
+        p.nb = nb;
+        p.B = Bp;
+        p.cams = m->cams + f0;
+        p.probs = static_cast<const char *>(d_probs) + (size_t)f0 * npix * m->c * esz;
+        p.scale = d_scale ? d_scale + (size_t)f0 * npix : nullptr;
+        p.ids_out = d_idmap_out ? d_idmap_out + (int64_t)f0 * npix : nullptr;
+        return p;
+    };
+    const int maxb = lf::fuse_queue_max_batches();
+    for (int b0 = 0; b0 < nfull; b0 += maxb)
+        out->full.push_back(piece(b0 * B, nfull - b0 < maxb ? nfull - b0 : maxb, B));
+    if (rem > 0) out->rest.push_back(piece(nfull * B, 1, rem));
+    out->lookahead = qs.L;
     m->normalised = false;
     return SM_OK;
+}
+
+// Launches the pieces in order, packed into as few work-queue launches as
+// the limits allow (scenes and batches per launch, no two pieces of one mesh
+// in a launch); every launch takes the smallest lookahead of its pieces.
+sm_status launch_pieces(const std::vector<lf::FuseQueueScene> &pieces, const std::vector<int> &lookahead,
+                        sm_dtype dtype, int c, sm_rule rule, sm_mesh *lead, cudaStream_t s)
+{
+    const int maxs = lf::fuse_queue_max_scenes(), maxb = lf::fuse_queue_max_batches();
+    size_t k = 0;
+    while (k < pieces.size()) {
+        std::vector<lf::FuseQueueScene> batch;
+        int G = 0, L = 4;
+        while (k < pieces.size() && (int)batch.size() < maxs && G + pieces[k].nb <= maxb) {
+            bool dup = false;
+            for (const auto &q : batch) dup = dup || q.owner == pieces[k].owner;
+            if (dup) break;
+            batch.push_back(pieces[k]);
+            G += pieces[k].nb;
+            if (lookahead[k] < L) L = lookahead[k];
+            ++k;
+        }
+        bool ok;
+        {
+            ProfScope p(lead, SM_K_QUEUE, s);
+            ok = lf::launch_fuse_queue(batch.data(), (int)batch.size(), dtype, c, rule, L, lead->qctr, s);
+        }
+        if (!ok) return fail(SM_ERR_INTERNAL, "work-queue launch refused its pieces (%d)", (int)batch.size());
+        LF_LAUNCHED("fusion work queue");
+    }
+    return SM_OK;
+}
+
+// Fusion of N frames in face mode with pixel weights through the persistent
+// work-queue kernel: the full batches (in launches of at most
+// fuse_queue_max_batches() batches), then the remaining frames.
+sm_status fuse_queue_impl(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
+                          const sm_intrinsics *d_K, const double *d_T, int32_t N, int32_t H, int32_t W,
+                          int32_t *d_idmap_out, cudaStream_t s)
+{
+    QueuePrep prep;
+    sm_status st = prepare_queue_scene(m, d_probs, dtype, d_scale, d_K, d_T, N, H, W, d_idmap_out, s, &prep);
+    if (st != SM_OK) return st;
+    std::vector<lf::FuseQueueScene> pieces(prep.full);
+    pieces.insert(pieces.end(), prep.rest.begin(), prep.rest.end());
+    return launch_pieces(pieces, std::vector<int>(pieces.size(), prep.lookahead), dtype, m->c, m->rule, m, s);
 }
 
 // Fusion of N frames (sm_fuse_frames; d_weights: explicit per-pixel weights, or null).
@@ -306,7 +355,7 @@ sm_status fuse_impl(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float
     const bool from_keys = tma && !m->texel_mode;
     // face mode with pixel weights and c = 20 / 40: raster and scatter of the
     // whole call in the persistent work-queue kernel
-    if (from_keys && !image_w && !d_weights && lf::fuse_queue_supported(m->c) && !m->stream_path)
+    if (from_keys && !image_w && !d_weights && lf::fuse_queue_supported(m->c) && m->use_queue)
         return fuse_queue_impl(m, d_probs, dtype, d_scale, d_K, d_cam_to_world, N, H, W, d_idmap_out, s);
     const bool need_ids = !from_keys || image_w;
     // the pipelined scatter reads its row map from the library's aligned buffer
@@ -505,6 +554,84 @@ sm_status sm_fuse_frames_weighted(sm_mesh *m, const void *d_probs, sm_dtype dtyp
     return fuse_impl(m, d_probs, dtype, d_scale, d_K, d_cam_to_world, N, H, W, d_weights, d_idmap_out, stream);
 }
 
+sm_status sm_fuse_scenes(const sm_scene_frames *scenes, int32_t n, void *stream)
+{
+    if (n < 0 || (n > 0 && !scenes)) return fail(SM_ERR_INVALID_ARG, "scenes is NULL or n < 0");
+    if (n == 0) return SM_OK;
+    for (int k = 0; k < n; ++k) {
+        const sm_scene_frames &sf = scenes[k];
+        if (!sf.mesh) return fail(SM_ERR_INVALID_ARG, "scene %d: mesh is NULL", k);
+        for (int j = 0; j < k; ++j)
+            if (scenes[j].mesh == sf.mesh) return fail(SM_ERR_INVALID_ARG, "scenes %d and %d share a mesh", j, k);
+    }
+    for (int k = 0; k < n; ++k) {
+        const sm_scene_frames &sf = scenes[k];
+        if (sf.mesh->device != scenes[0].mesh->device)
+            return fail(SM_ERR_INVALID_ARG, "scene %d: its mesh is on device %d, scene 0's on %d", k, sf.mesh->device,
+                        scenes[0].mesh->device);
+        sm_status st = check_image(sf.N, sf.H, sf.W);
+        if (st != SM_OK) {
+            char msg[sizeof g_last_error];
+            snprintf(msg, sizeof msg, "%s", g_last_error);
+            return fail(st, "scene %d: %s", k, msg);
+        }
+        if ((int)sf.dtype < 0 || (int)sf.dtype > 2) return fail(SM_ERR_INVALID_ARG, "scene %d: unknown dtype", k);
+        if ((sf.dtype == SM_F32) != (sf.d_scale == nullptr) && sf.N > 0)
+            return fail(SM_ERR_INVALID_ARG, "scene %d: a scale is given iff BF16/FP8", k);
+        if (sf.N > 0 && (!sf.d_probs || !sf.d_K || !sf.d_cam_to_world))
+            return fail(SM_ERR_INVALID_ARG, "scene %d: NULL input pointer", k);
+        if (sf.N > 0 && ((uintptr_t)sf.d_probs & 15) != 0)
+            return fail(SM_ERR_INVALID_ARG, "scene %d: probabilities not 16-byte aligned", k);
+    }
+    DeviceGuard g(scenes[0].mesh->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // scenes the work queue applies to are grouped by (class count, storage
+    // type, rule): one persistent launch (plus one for remainders) per group
+    // of up to fuse_queue_max_scenes() scenes; the others fuse on their own
+    bool done[1024] = {};
+    if (n > 1024) return fail(SM_ERR_INVALID_ARG, "at most 1024 scenes per call (got %d)", n);
+    for (int k = 0; k < n; ++k) {
+        const sm_scene_frames &sf = scenes[k];
+        sm_mesh *m = sf.mesh;
+        const bool eligible = sf.N > 0 && !m->texel_mode && m->weight == SM_WEIGHT_PIXEL &&
+                              lf::scatter_tma_supported(m->c) && lf::fuse_queue_supported(m->c);
+        if (!eligible) {
+            sm_status st = sm_fuse_frames(m, sf.d_probs, sf.dtype, sf.d_scale, sf.d_K, sf.d_cam_to_world, sf.N, sf.H,
+                                          sf.W, sf.d_idmap_out, stream);
+            if (st != SM_OK) return st;
+            done[k] = true;
+        }
+    }
+    for (int k = 0; k < n; ++k) {
+        if (done[k]) continue;
+        // the group of scene k: every not yet fused scene with its class
+        // count, storage type and rule; their full-batch pieces first, then
+        // the remainders, packed into work-queue launches
+        std::vector<lf::FuseQueueScene> full, rest;
+        std::vector<int> lfull, lrest;
+        sm_mesh *lead = scenes[k].mesh;
+        for (int j = k; j < n; ++j) {
+            const sm_scene_frames &sf = scenes[j];
+            if (done[j] || sf.mesh->c != lead->c || sf.dtype != scenes[k].dtype || sf.mesh->rule != lead->rule)
+                continue;
+            QueuePrep prep;
+            sm_status st = prepare_queue_scene(sf.mesh, sf.d_probs, sf.dtype, sf.d_scale, sf.d_K, sf.d_cam_to_world,
+                                               sf.N, sf.H, sf.W, sf.d_idmap_out, s, &prep);
+            if (st != SM_OK) return st;
+            full.insert(full.end(), prep.full.begin(), prep.full.end());
+            lfull.insert(lfull.end(), prep.full.size(), prep.lookahead);
+            rest.insert(rest.end(), prep.rest.begin(), prep.rest.end());
+            lrest.insert(lrest.end(), prep.rest.size(), prep.lookahead);
+            done[j] = true;
+        }
+        full.insert(full.end(), rest.begin(), rest.end());
+        lfull.insert(lfull.end(), lrest.begin(), lrest.end());
+        sm_status st = launch_pieces(full, lfull, scenes[k].dtype, lead->c, lead->rule, lead, s);
+        if (st != SM_OK) return st;
+    }
+    return SM_OK;
+}
+
 sm_status sm_normalise(sm_mesh *m, float *d_dist, int32_t *d_labels, void *stream)
 {
     if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
@@ -642,54 +769,14 @@ sm_status sm_autotune_batch(sm_mesh *m, const void *d_probs, sm_dtype dtype, con
         *out = ms / (float)n;
         return r;
     };
-    const bool queue = !m->texel_mode && m->weight == SM_WEIGHT_PIXEL && lf::scatter_tma_supported(m->c) &&
-                       lf::fuse_queue_supported(m->c) && !m->stream_path;
+    const bool eligible = !m->texel_mode && m->weight == SM_WEIGHT_PIXEL && lf::scatter_tma_supported(m->c) &&
+                          lf::fuse_queue_supported(m->c);
+    const bool saved_queue = m->use_queue;
     int best = 0;
-    if (queue) {
-        // work-queue shape, one parameter at a time from the defaults:
-        // frames per batch, raster lookahead, cull rounds per raster item,
-        // tiles per scatter item
-        const QueueShape saved{m->qB, m->qL, m->qR, m->qS};
-        const int64_t saved_npix = m->q_npix;
-        QueueShape cur = queue_shape(m, -1);
-        m->q_npix = npix;
-        auto apply = [&](const QueueShape &q) {
-            m->qB = q.B;
-            m->qL = q.L;
-            m->qR = q.R;
-            m->qS = q.S;
-        };
-        float best_ms = 0.0f;
-        apply(cur);
-        st = per_frame(N, &best_ms);
-        const int Bs[] = {4, 8, 12, 16, 24, 32, 48}, Ls[] = {0, 1, 2}, Rs[] = {1, 2, 4}, Ss[] = {16, 32, 64, 128};
-        for (int dim = 0; dim < 4 && st == SM_OK; ++dim) {
-            const int *vals = dim == 0 ? Bs : dim == 1 ? Ls : dim == 2 ? Rs : Ss;
-            const int nv = dim == 0 ? 7 : dim == 1 ? 3 : dim == 2 ? 3 : 4;
-            for (int k = 0; k < nv && st == SM_OK; ++k) {
-                QueueShape c = cur;
-                int *field = dim == 0 ? &c.B : dim == 1 ? &c.L : dim == 2 ? &c.R : &c.S;
-                if (*field == vals[k] || (dim == 0 && vals[k] > N)) continue;
-                *field = vals[k];
-                apply(c);
-                float ms = 0.0f;
-                if ((st = per_frame(N, &ms)) != SM_OK) break;
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    cur = c;
-                }
-            }
-        }
-        if (st == SM_OK) st = sm_reset(m, stream);
-        if (st != SM_OK) {
-            apply(saved);
-            m->q_npix = saved_npix;
-        } else {
-            apply(cur);
-            best = cur.B;
-        }
-    } else {
-        float best_ms = 0.0f;
+    float best_stream = 0.0f, best_queue = 0.0f;
+    {
+        // two-stream path: frames per launch
+        m->use_queue = false;
         const int saved_B = m->tuned_B;
         const int64_t saved_npix = m->tuned_npix;
         // candidates: multiples of 4 frames whose two z-buffer slots stay within 1 GB
@@ -698,12 +785,11 @@ sm_status sm_autotune_batch(sm_mesh *m, const void *d_probs, sm_dtype dtype, con
             m->tuned_npix = npix;
             float ms = 0.0f;
             if ((st = per_frame((N / B) * B, &ms)) != SM_OK) break;  // whole launches only
-            if (best == 0 || ms < best_ms) {
+            if (best == 0 || ms < best_stream) {
                 best = B;
-                best_ms = ms;
+                best_stream = ms;
             }
         }
-        if (st == SM_OK) st = sm_reset(m, stream);
         if (st != SM_OK || best == 0) {
             m->tuned_B = saved_B;
             m->tuned_npix = saved_npix;
@@ -712,6 +798,54 @@ sm_status sm_autotune_batch(sm_mesh *m, const void *d_probs, sm_dtype dtype, con
             m->tuned_npix = npix;
         }
     }
+    if (eligible && st == SM_OK && best != 0) {
+        // work-queue path: its shape, one parameter at a time from the
+        // defaults (frames per batch, raster lookahead, cull rounds per raster
+        // item, tiles per scatter item); kept if it beats the two-stream path
+        const QueueShape saved{m->qB, m->qL, m->qR, m->qS};
+        const int64_t saved_npix = m->q_npix;
+        QueueShape cur = queue_shape(m, -1);
+        m->q_npix = npix;
+        m->use_queue = true;
+        auto apply = [&](const QueueShape &q) {
+            m->qB = q.B;
+            m->qL = q.L;
+            m->qR = q.R;
+            m->qS = q.S;
+        };
+        apply(cur);
+        st = per_frame(N, &best_queue);
+        const int Bs[] = {8, 16, 24, 32, 48, 64}, Ls[] = {1, 2, 3}, Rs[] = {1, 2, 4}, Ss[] = {32, 64, 128, 256};
+        for (int dim = 0; dim < 4 && st == SM_OK; ++dim) {
+            const int *vals = dim == 0 ? Bs : dim == 1 ? Ls : dim == 2 ? Rs : Ss;
+            const int nv = dim == 0 ? 6 : dim == 1 ? 3 : dim == 2 ? 3 : 4;
+            for (int k = 0; k < nv && st == SM_OK; ++k) {
+                QueueShape c = cur;
+                int *field = dim == 0 ? &c.B : dim == 1 ? &c.L : dim == 2 ? &c.R : &c.S;
+                if (*field == vals[k] || (dim == 0 && vals[k] > N)) continue;
+                *field = vals[k];
+                apply(c);
+                float ms = 0.0f;
+                if ((st = per_frame(N, &ms)) != SM_OK) break;
+                if (ms < best_queue) {
+                    best_queue = ms;
+                    cur = c;
+                }
+            }
+        }
+        if (st == SM_OK && best_queue < best_stream) {
+            apply(cur);
+            best = cur.B;
+        } else {
+            apply(saved);
+            m->q_npix = saved_npix;
+            m->use_queue = false;
+        }
+    } else {
+        m->use_queue = saved_queue;  // the queue path does not apply to this mesh (or tuning failed)
+    }
+    if (st == SM_OK) st = sm_reset(m, stream);
+    if (st != SM_OK) m->use_queue = saved_queue;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != SM_OK) return st;
@@ -727,17 +861,17 @@ sm_status sm_set_queue_shape(sm_mesh *m, int32_t H, int32_t W, int32_t frames_pe
     sm_status st = check_image(0, H, W);
     if (st != SM_OK) return st;
     if (frames_per_batch == 0) {
-        m->stream_path = true;
+        m->use_queue = false;
         return SM_OK;
     }
     if (frames_per_batch < 4 || frames_per_batch > 128 || (frames_per_batch & 3) != 0)
         return fail(SM_ERR_INVALID_ARG, "frames per batch %d: a multiple of 4 in [4, 128], or 0", frames_per_batch);
-    if (lookahead < 0 || lookahead > 4) return fail(SM_ERR_INVALID_ARG, "lookahead %d outside [0, 4]", lookahead);
+    if (lookahead < 1 || lookahead > 4) return fail(SM_ERR_INVALID_ARG, "lookahead %d outside [1, 4]", lookahead);
     if (raster_rounds < 1 || raster_rounds > 64)
         return fail(SM_ERR_INVALID_ARG, "raster rounds %d outside [1, 64]", raster_rounds);
     if (scatter_tiles < 1 || scatter_tiles > 4096)
         return fail(SM_ERR_INVALID_ARG, "scatter tiles %d outside [1, 4096]", scatter_tiles);
-    m->stream_path = false;
+    m->use_queue = true;
     m->qB = frames_per_batch;
     m->qL = lookahead;
     m->qR = raster_rounds;
@@ -776,6 +910,37 @@ sm_status sm_conf_features(sm_mesh *m, const void *d_probs, sm_dtype dtype, cons
         // row map of the batch (re-arms the z-buffer)
         if ((st = resolve_only(m, f0, nb, H, W, m->keys, d_rows_out + (int64_t)f0 * npix, s, nullptr)) != SM_OK)
             return st;
+    }
+    return SM_OK;
+}
+
+sm_status sm_conf_weights(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
+                          const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N, int32_t H, int32_t W,
+                          const float *d_params, float *d_w_out, int32_t *d_rows_out, void *stream)
+{
+    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
+    sm_status st = check_image(N, H, W);
+    if (st != SM_OK) return st;
+    if ((int)dtype < 0 || (int)dtype > 2) return fail(SM_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
+    if ((dtype == SM_F32) != (d_scale == nullptr) && N > 0) return fail(SM_ERR_INVALID_ARG, "scale given iff BF16/FP8");
+    if (N == 0) return SM_OK;
+    if (!d_probs || !d_K || !d_cam_to_world || !d_params || !d_w_out || !d_rows_out)
+        return fail(SM_ERR_INVALID_ARG, "NULL pointer");
+    DeviceGuard g(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t npix = (int64_t)H * W;
+    const int B = batch_frames(m, npix, N);
+    if ((st = prepare_frames(m, d_K, d_cam_to_world, N, npix, B, false, s)) != SM_OK) return st;
+    const size_t esz = dtype_size(dtype);
+    for (int f0 = 0; f0 < N; f0 += B) {
+        const int nb = (N - f0 < B) ? N - f0 : B;
+        if ((st = raster_only(m, f0, nb, H, W, m->keys, s)) != SM_OK) return st;
+        lf::launch_conf_weights(m->keys, npix * nb, H, W, m->verts, m->faces, m->F, d_K + f0,
+                                d_cam_to_world + 16 * (int64_t)f0,
+                                static_cast<const char *>(d_probs) + (size_t)f0 * npix * m->c * esz, dtype,
+                                d_scale ? d_scale + (size_t)f0 * npix : nullptr, m->c, d_params,
+                                d_w_out + (size_t)f0 * npix, d_rows_out + (int64_t)f0 * npix, s);
+        LF_LAUNCHED("confidence weights");
     }
     return SM_OK;
 }

@@ -126,6 +126,177 @@ __device__ __forceinline__ float mlp_forward(const float *s, const float *x, flo
     return o;
 }
 
+// ---- inference fused with the features, hidden layer on the tensor cores ----
+
+// Two floats rounded to bfloat16 (nearest even) and packed, the first in the
+// low half (the element with the lower column index of an mma fragment).
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// D = A B + C for one 16 x 8 x 16 tile: A 16 x 16 bfloat16 (row major), B
+// 16 x 8 bfloat16 (column major), C and D float32; fragments as the PTX ISA
+// lays them out for mma.m16n8k16 (g = lane / 4, t = lane % 4): a0 (row g,
+// cols 2t, 2t+1), a1 (row g+8, same cols), a2 / a3 (cols + 8); b0 (rows 2t,
+// 2t+1, col g), b1 (rows + 8); c0, c1 (row g, cols 2t, 2t+1), c2, c3 (row g+8).
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Features of pixel p of a rasterised batch (see k_conf_features), from its
+// z-buffer key; false for background.
+__device__ __forceinline__ bool pixel_features(unsigned long long key, int64_t p, int H, int W,
+                                               const float4 *__restrict__ V, const int4 *__restrict__ faces, int64_t F,
+                                               const sm_intrinsics *__restrict__ K, const double *__restrict__ T,
+                                               const void *__restrict__ probs, sm_dtype dt,
+                                               const float *__restrict__ scale, int c, float (&x)[kF])
+{
+    const int64_t npix = (int64_t)H * W;
+    const int b = (int)(p / npix);
+    const int64_t q = p - (int64_t)b * npix;
+    const int y = (int)(q / W), xx = (int)(q - (int64_t)y * W);
+    const int64_t f = (int64_t)(unsigned int)key;
+    if (key == kEmptyKey || f >= F) return false;
+    const sm_intrinsics Kb = K[b];
+    const double *Tb = T + 16 * (int64_t)b;
+    const float dx = ((float)xx - (float)Kb.cx) / (float)Kb.fx, dy = ((float)y - (float)Kb.cy) / (float)Kb.fy;
+    float ray[3];
+    for (int r = 0; r < 3; ++r) ray[r] = (float)Tb[4 * r] * dx + (float)Tb[4 * r + 1] * dy + (float)Tb[4 * r + 2];
+    const int4 fc = faces[f];
+    const float4 a = V[fc.x], bb = V[fc.y], cc = V[fc.z];
+    const float e1[3] = {bb.x - a.x, bb.y - a.y, bb.z - a.z}, e2[3] = {cc.x - a.x, cc.y - a.y, cc.z - a.z};
+    const float n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    const float dot = n[0] * ray[0] + n[1] * ray[1] + n[2] * ray[2];
+    const float nn = sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    const float rr = sqrtf(ray[0] * ray[0] + ray[1] * ray[1] + ray[2] * ray[2]);
+    x[0] = nn > 0.0f ? fabsf(dot) / (nn * rr) : 0.0f;
+    const float inv_z = __uint_as_float(0xFFFFFFFFu - (unsigned int)(key >> 32));
+    x[1] = inv_z > 0.0f ? 0.25f / inv_z : 0.0f;
+    const float sc = (dt == SM_F32) ? 1.0f : scale[p];
+    float ent = 0.0f, m1 = -INFINITY, m2 = -INFINITY;
+    for (int j = 0; j < c; ++j) {
+        const float v = load_p(probs, dt, p * c + j, sc);
+        ent -= v * logf(fmaxf(v, kPMin));
+        if (v > m1) {
+            m2 = m1;
+            m1 = v;
+        } else if (v > m2) {
+            m2 = v;
+        }
+    }
+    x[2] = c > 1 ? ent / logf((float)c) : 0.0f;
+    x[3] = c > 1 ? m1 - m2 : m1;
+    const int d = min(min(xx, y), min(W - 1 - xx, H - 1 - y));
+    x[4] = (float)d / (0.5f * (float)min(W, H));
+    return true;
+}
+
+// One thread per pixel of a rasterised batch, one warp per 32 pixels: the
+// features, then w = sigmoid(network) with the bfloat16 parameters; the
+// first layer in float32, the 32 x 32 hidden layer as 16 tensor-core tiles
+// per warp (activations rounded to bfloat16, float32 accumulation), the
+// output layer in float32.  Writes w (0 for background) and the row map, and
+// re-arms the z-buffer.
+__global__ void __launch_bounds__(256)
+    k_conf_weights(unsigned long long *__restrict__ keys, int64_t total, int H, int W, const float4 *__restrict__ V,
+                   const int4 *__restrict__ faces, int64_t F, const sm_intrinsics *__restrict__ K,
+                   const double *__restrict__ T, const void *__restrict__ probs, sm_dtype dt,
+                   const float *__restrict__ scale, int c, const float *__restrict__ params, float *__restrict__ w_out,
+                   int32_t *__restrict__ rows_out)
+{
+    __shared__ float s[SM_CONF_PARAMS];
+    __shared__ __align__(16) __nv_bfloat16 hs[8][32][kH + 8];  // per warp: its 32 pixels' activations (padded rows)
+    __shared__ __align__(16) __nv_bfloat16 w2[kH][kH + 8];     // W2 (row = output), bfloat16
+    load_params(params, s);
+    for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) w2[i / kH][i % kH] = __float2bfloat16_rn(s[kW2 + i]);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    // B fragments of W2^T for the 4 output tiles x 2 input steps (loaded once)
+    uint32_t bf[4][2][2];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            bf[nt][ks][0] = *reinterpret_cast<const uint32_t *>(&w2[8 * nt + g][16 * ks + 2 * t]);
+            bf[nt][ks][1] = *reinterpret_cast<const uint32_t *>(&w2[8 * nt + g][16 * ks + 8 + 2 * t]);
+        }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + warp * 32; base < total; base += stride) {
+        const int64_t p = base + lane;
+        float x[kF] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        bool fg = false;
+        int32_t row = -1;
+        if (p < total) {
+            const unsigned long long key = keys[p];
+            keys[p] = kEmptyKey;
+            fg = pixel_features(key, p, H, W, V, faces, F, K, T, probs, dt, scale, c, x);
+            if (fg) row = (int32_t)(unsigned int)key;
+            rows_out[p] = row;
+        }
+        // first layer, float32, into this lane's row of activations
+#pragma unroll
+        for (int i = 0; i < kH; i += 2) {
+            float z0 = s[kB1 + i], z1 = s[kB1 + i + 1];
+#pragma unroll
+            for (int k = 0; k < kF; ++k) {
+                z0 = fmaf(s[kW1 + i * kF + k], x[k], z0);
+                z1 = fmaf(s[kW1 + (i + 1) * kF + k], x[k], z1);
+            }
+            *reinterpret_cast<uint32_t *>(&hs[warp][lane][i]) = pack_bf16x2(fmaxf(z0, 0.f), fmaxf(z1, 0.f));
+        }
+        __syncwarp();
+        // hidden layer: 32 pixels x 32 outputs = 2 x 4 tiles, K = 32 in 2 steps
+        float o[2][2] = {{s[kB3], s[kB3]}, {s[kB3], s[kB3]}};  // per m tile: rows g and g + 8
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            uint32_t af[2][4];
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                af[ks][0] = *reinterpret_cast<const uint32_t *>(&hs[warp][16 * mt + g][16 * ks + 2 * t]);
+                af[ks][1] = *reinterpret_cast<const uint32_t *>(&hs[warp][16 * mt + g + 8][16 * ks + 2 * t]);
+                af[ks][2] = *reinterpret_cast<const uint32_t *>(&hs[warp][16 * mt + g][16 * ks + 8 + 2 * t]);
+                af[ks][3] = *reinterpret_cast<const uint32_t *>(&hs[warp][16 * mt + g + 8][16 * ks + 8 + 2 * t]);
+            }
+            float part[2] = {0.f, 0.f};
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int j = 8 * nt + 2 * t;  // this thread's two output columns
+                float d[4] = {s[kB2 + j], s[kB2 + j + 1], s[kB2 + j], s[kB2 + j + 1]};
+                mma_bf16_16816(d, af[0], bf[nt][0]);
+                mma_bf16_16816(d, af[1], bf[nt][1]);
+                // output layer: w3 . relu(z2), this thread's columns
+                part[0] = fmaf(s[kW3 + j], fmaxf(d[0], 0.f), part[0]);
+                part[0] = fmaf(s[kW3 + j + 1], fmaxf(d[1], 0.f), part[0]);
+                part[1] = fmaf(s[kW3 + j], fmaxf(d[2], 0.f), part[1]);
+                part[1] = fmaf(s[kW3 + j + 1], fmaxf(d[3], 0.f), part[1]);
+            }
+            // sum over the 4 threads of the group (all 32 columns)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                part[h] += __shfl_xor_sync(0xffffffffu, part[h], 1);
+                part[h] += __shfl_xor_sync(0xffffffffu, part[h], 2);
+                o[mt][h] += part[h];
+            }
+        }
+        // pixel 16 mt + g (+ 8) of the warp: its lane fetches the output from
+        // thread 4 g of the group (the lanes own rows g and g + 8 of each tile)
+        const int mt = lane >> 4, r = lane & 15;
+        const int src = 4 * (r & 7);
+        const float o0 = __shfl_sync(0xffffffffu, o[0][0], src), o1 = __shfl_sync(0xffffffffu, o[0][1], src);
+        const float o2 = __shfl_sync(0xffffffffu, o[1][0], src), o3 = __shfl_sync(0xffffffffu, o[1][1], src);
+        const float ol = mt == 0 ? (r < 8 ? o0 : o1) : (r < 8 ? o2 : o3);
+        if (p < total) w_out[p] = fg ? 1.0f / (1.0f + expf(-ol)) : 0.0f;
+        __syncwarp();  // the activations are rewritten by the next pixels
+    }
+}
+
 __global__ void __launch_bounds__(256)
     k_conf_forward(const float *__restrict__ params, const float *__restrict__ feat, int64_t n, float *__restrict__ w)
 {
@@ -240,6 +411,17 @@ void launch_conf_features(const unsigned long long *keys, int64_t total, int H, 
     if (total <= 0) return;
     k_conf_features<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(keys, total, H, W, V, faces, F, K, T, probs, dt,
                                                                     scale, c, feat);
+}
+
+void launch_conf_weights(unsigned long long *keys, int64_t total, int H, int W, const float4 *V, const int4 *faces,
+                         int64_t F, const sm_intrinsics *K, const double *T, const void *probs, sm_dtype dt,
+                         const float *scale, int c, const float *params, float *w, int32_t *rows, cudaStream_t s)
+{
+    if (total <= 0) return;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    k_conf_weights<<<(unsigned)blocks, 256, 0, s>>>(keys, total, H, W, V, faces, F, K, T, probs, dt, scale, c, params,
+                                                    w, rows);
 }
 
 void launch_conf_forward(const float *params, const float *feat, int64_t n, float *w, cudaStream_t s)

@@ -216,22 +216,31 @@ __global__ void k_render(const int32_t *__restrict__ idmap, int64_t npix, const 
     out[p] = (row < 0 || row >= n_x) ? (uint8_t)255 : labels8[row];
 }
 
-// 16 pixels per thread: four 16-byte row-map loads, one 16-byte label store.
+// 16 pixels per thread: four 16-byte row-map loads, one 16-byte label store;
+// a pixel on the same row as the previous one reuses its label (runs of a
+// few pixels per triangle are the rule), so most label gathers are skipped.
 __global__ void k_render16(const int4 *__restrict__ idmap, int64_t n16, const uint8_t *__restrict__ labels8,
                            int64_t n_x, uint4 *__restrict__ out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n16) return;
+    int4 r[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) r[j] = __ldcs(idmap + 4 * i + j);
     uint32_t w[4];
+    int prev = -1;
+    uint32_t plab = 255u;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const int4 r = __ldcs(idmap + 4 * i + j);
-        const int rr[4] = {r.x, r.y, r.z, r.w};
+        const int rr[4] = {r[j].x, r[j].y, r[j].z, r[j].w};
         uint32_t packed = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const uint32_t lab = (rr[k] < 0 || rr[k] >= n_x) ? 255u : (uint32_t)labels8[rr[k]];
-            packed |= lab << (8 * k);
+            if (rr[k] != prev) {
+                plab = (rr[k] < 0 || rr[k] >= n_x) ? 255u : (uint32_t)labels8[rr[k]];
+                prev = rr[k];
+            }
+            packed |= plab << (8 * k);
         }
         w[j] = packed;
     }

@@ -100,40 +100,44 @@ void launch_scatter_tma(sm_rule rule, sm_dtype dtype, const void *probs, const f
                         int64_t npix, int c, const uint32_t *fcnt, float alpha, const float *wpix, int64_t n_x,
                         float *acc, uint32_t *cnt, int32_t *err, cudaStream_t s);
 // Persistent fusion kernel with a device work queue (queue.cu): raster and
-// scatter of nb batches of B frames in one launch (face mode, pixel weights,
-// c = 20 or 40).  keys: lookahead + 2 slots of slot_stride keys, all empty on
-// entry and on return; counters: fuse_queue_counter_words(nb) words, zeroed
-// by the launch.
-struct FuseQueueLaunch {
+// scatter of up to fuse_queue_max_scenes() scene pieces with at most
+// fuse_queue_max_batches() batches in all, in one launch (face mode, pixel
+// weights; one class count, 20 or 40, one storage type and one rule per
+// launch; no two pieces of one mesh).  Per piece: nb batches of B frames
+// into `slots` z-buffer slots of slot_stride keys (slots > lookahead), all
+// keys empty on entry and on return.  counters: fuse_queue_counter_words(G)
+// words for G batches in all, zeroed by the launch.
+struct FuseQueueScene {
     const float4 *V;
     const int4 *faces;
     int64_t F;
     const float4 *bounds;
-    const Camera *cams;  // first frame of the launch
+    const Camera *cams;  // first frame of the piece
     int H, W;
     int64_t npix;
-    const void *probs;   // first frame of the launch
+    const void *probs;   // first frame of the piece
     const float *scale;
-    sm_dtype dtype;
-    int c;
-    sm_rule rule;
-    int32_t *ids_out;    // optional, first frame of the launch
+    int32_t *ids_out;    // optional, first frame of the piece
     float *acc;
     uint32_t *cnt;
     int64_t n_x;
     int32_t *err;
     unsigned long long *keys;
     int64_t slot_stride;
+    int slots;
     int nb, B;
-    int lookahead;       // batches the raster runs ahead of the scatter
     int raster_rounds;   // cull rounds (fuse_queue_raster_round() clusters each) per raster item
     int scatter_tiles;   // 256-pixel tiles per scatter item
-    uint32_t *counters;
+    const void *owner;   // the mesh the piece belongs to
 };
 bool fuse_queue_supported(int c);
 int fuse_queue_raster_round();
-uint32_t fuse_queue_counter_words(int nb);
-void launch_fuse_queue(const FuseQueueLaunch &l, cudaStream_t s);
+int fuse_queue_max_scenes();
+int fuse_queue_max_batches();
+uint32_t fuse_queue_counter_words(int G);
+// false (nothing enqueued) if the pieces break a limit above
+bool launch_fuse_queue(const FuseQueueScene *scenes, int n, sm_dtype dtype, int c, sm_rule rule, int lookahead,
+                       uint32_t *counters, cudaStream_t s);
 
 // Visible-area pre-pass (fuse.cu): per-frame pixel counts of the triangles in
 // a batch's z-buffers (re-armed), folded into per-triangle maxima; texel
@@ -146,6 +150,11 @@ void launch_conf_features(const unsigned long long *keys, int64_t total, int H, 
                           const int4 *faces, int64_t F, const sm_intrinsics *K, const double *T, const void *probs,
                           sm_dtype dt, const float *scale, int c, float *feat, cudaStream_t s);
 void launch_conf_forward(const float *params, const float *feat, int64_t n, float *w, cudaStream_t s);
+// Features and network output in one pass over a rasterised batch (tensor
+// cores for the hidden layer); writes weights and the row map, re-arms keys.
+void launch_conf_weights(unsigned long long *keys, int64_t total, int H, int W, const float4 *V, const int4 *faces,
+                         int64_t F, const sm_intrinsics *K, const double *T, const void *probs, sm_dtype dt,
+                         const float *scale, int c, const float *params, float *w, int32_t *rows, cudaStream_t s);
 void launch_conf_train_step(float *params, const float *feat, const float *target, int64_t n, float lr, float *grad,
                             float *loss, cudaStream_t s);
 void launch_conf_targets(const void *probs, sm_dtype dt, const float *scale, int c, const int32_t *rows, int64_t n,
@@ -177,11 +186,12 @@ struct sm_mesh {
     float alpha = 1.0f;  // image-weight mix (sm_set_weight_mix)
     int tuned_B = 0;          // frames per launch chosen by sm_autotune_batch ...
     int64_t tuned_npix = 0;   // ... for frames of this many pixels
-    // shape of the work-queue fusion (sm_set_queue_shape / sm_autotune_batch)
-    // for frames of q_npix pixels; zero fields take the defaults
+    // work-queue fusion (sm_set_queue_shape / sm_autotune_batch): used when
+    // use_queue is set, with this shape for frames of q_npix pixels (zero
+    // fields take the defaults)
     int qB = 0, qL = 0, qR = 0, qS = 0;
     int64_t q_npix = 0;
-    bool stream_path = false;  // sm_set_queue_shape(..., 0 frames): keep the two-stream path
+    bool use_queue = false;
     bool texel_mode = false;
     bool normalised = false;
 

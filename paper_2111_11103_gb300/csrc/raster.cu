@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(256) k_raster_flat(const float *__restrict__ V
     for (int k = 0; k < 3; ++k) P[k] = make_float4(V[3 * (int64_t)ix[k]], V[3 * (int64_t)ix[k] + 1],
                                                    V[3 * (int64_t)ix[k] + 2], 0.0f);
     Tri t;
-    if (!setup_triangle(A, P, make_int4(0, 1, 2, 1), t)) return;
+    if (!setup_triangle(A, P, make_int4(0, 1, 2, 1), t, H, W)) return;
     int minx = min(t.x[0], min(t.x[1], t.x[2])), maxx = max(t.x[0], max(t.x[1], t.x[2]));
     int miny = min(t.y[0], min(t.y[1], t.y[2])), maxy = max(t.y[0], max(t.y[1], t.y[2]));
     int x0 = max(ceil256(minx), 0), x1 = min(floor256(maxx), W - 1);

@@ -19,20 +19,32 @@ __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ float i2f(long long v) { return __ll2float_rn(v); }
 
-// Projects and snaps one vertex; false if it is at/behind the near plane or
-// outside the snap range (its triangle is then dropped).
-__device__ __forceinline__ bool project_vertex(const float *A, float4 p, int &xs, int &ys, float &iz)
+// Camera-space transform of a vertex in binary32 with a fixed operation
+// order: X, Y = image x, y times the depth, in 1/256-pixel units; Z = depth.
+__device__ __forceinline__ void transform_vertex(const float *A, float4 p, float &X, float &Y, float &Z)
 {
-    float X = fadd(fadd(fadd(fmul(A[0], p.x), fmul(A[1], p.y)), fmul(A[2], p.z)), A[3]);
-    float Y = fadd(fadd(fadd(fmul(A[4], p.x), fmul(A[5], p.y)), fmul(A[6], p.z)), A[7]);
-    float Z = fadd(fadd(fadd(fmul(A[8], p.x), fmul(A[9], p.y)), fmul(A[10], p.z)), A[11]);
-    if (!(Z > kZNear)) return false;
-    float xf = fdiv(X, Z);
-    float yf = fdiv(Y, Z);
+    X = fadd(fadd(fadd(fmul(A[0], p.x), fmul(A[1], p.y)), fmul(A[2], p.z)), A[3]);
+    Y = fadd(fadd(fadd(fmul(A[4], p.x), fmul(A[5], p.y)), fmul(A[6], p.z)), A[7]);
+    Z = fadd(fadd(fadd(fmul(A[8], p.x), fmul(A[9], p.y)), fmul(A[10], p.z)), A[11]);
+}
+
+// Snaps a transformed vertex (Z > near plane): xs = rint(X / Z), ys =
+// rint(Y / Z) with correctly rounded quotients, iz = RN(1 / Z); false if
+// outside the snap range (the triangle is then dropped).  The quotients come
+// from one correctly rounded reciprocal y = RN(1 / Z) by Markstein's
+// correction (P. Markstein, IBM J. Res. Dev. 34(1), 1990): q = RN(a y), the
+// exact remainder r = a - Z q (one FMA), RN(q + r y) = RN(a / Z) for
+// quotients in the normal range; a smaller quotient snaps to 0 either way.
+__device__ __forceinline__ bool snap_vertex(float X, float Y, float Z, int &xs, int &ys, float &iz)
+{
+    const float y = __frcp_rn(Z);
+    const float qx = fmul(X, y), qy = fmul(Y, y);
+    const float xf = __fmaf_rn(__fmaf_rn(-Z, qx, X), y, qx);
+    const float yf = __fmaf_rn(__fmaf_rn(-Z, qy, Y), y, qy);
     if (!(fabsf(xf) <= kSnapLimit) || !(fabsf(yf) <= kSnapLimit)) return false;
     xs = __float2int_rn(xf);
     ys = __float2int_rn(yf);
-    iz = fdiv(1.0f, Z);
+    iz = y;
     return true;
 }
 
@@ -45,11 +57,35 @@ struct Tri {
     bool swapped;
 };
 
-__device__ __forceinline__ bool setup_triangle(const float *A, const float4 *__restrict__ V, int4 f, Tri &t)
+// Set-up of face f: false if it draws nothing (a vertex at or behind the
+// near plane, outside the snap range, or zero area).  With an image size
+// (W > 0), a face whose three vertices all lie more than 2 pixels beyond the
+// same image side is dropped before its divisions: its bounding box misses
+// the image, so nothing changes (the quotients round monotonically, and the
+// side bounds are exact or dwarf their rounding).
+__device__ __forceinline__ bool setup_triangle(const float *A, const float4 *__restrict__ V, int4 f, Tri &t,
+                                               int H = 0, int W = 0)
 {
-    if (!project_vertex(A, V[f.x], t.x[0], t.y[0], t.iz[0])) return false;
-    if (!project_vertex(A, V[f.y], t.x[1], t.y[1], t.iz[1])) return false;
-    if (!project_vertex(A, V[f.z], t.x[2], t.y[2], t.iz[2])) return false;
+    float X[3], Y[3], Z[3];
+    transform_vertex(A, V[f.x], X[0], Y[0], Z[0]);
+    transform_vertex(A, V[f.y], X[1], Y[1], Z[1]);
+    transform_vertex(A, V[f.z], X[2], Y[2], Z[2]);
+    if (!(Z[0] > kZNear) || !(Z[1] > kZNear) || !(Z[2] > kZNear)) return false;
+    if (W > 0) {
+        const float right = 256.0f * (float)(W + 1), bottom = 256.0f * (float)(H + 1);
+        bool l = true, r = true, u = true, d = true;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            l = l && X[k] < -512.0f * Z[k];
+            r = r && X[k] > right * Z[k];
+            u = u && Y[k] < -512.0f * Z[k];
+            d = d && Y[k] > bottom * Z[k];
+        }
+        if (l || r || u || d) return false;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        if (!snap_vertex(X[k], Y[k], Z[k], t.x[k], t.y[k], t.iz[k])) return false;
     long long area2 = (long long)(t.x[1] - t.x[0]) * (t.y[2] - t.y[0]) - (long long)(t.y[1] - t.y[0]) * (t.x[2] - t.x[0]);
     if (area2 == 0) return false;
     t.swapped = area2 < 0;
@@ -120,8 +156,12 @@ __device__ __forceinline__ void raster_box(const Tri &t, int x0, int x1, int y0,
     for (int py = y0; py <= y1; ++py) {
         T e0 = e_row[0], e1 = e_row[1], e2 = e_row[2];
         unsigned long long *row_keys = frame_keys + (int64_t)py * W;
+        bool in_run = false;  // the covered samples of a row form one run (a convex face)
         for (int px = x0; px <= x1; ++px) {
-            if (e0 > 0 && e1 > 0 && e2 > 0) {
+            const bool inside = e0 > 0 && e1 > 0 && e2 > 0;
+            if (!inside && in_run) break;
+            if (inside) {
+                in_run = true;
                 const float num = fadd(fadd(fmul(to_float(e0 - tl[0]), t.iz[0]), fmul(to_float(e1 - tl[1]), t.iz[1])),
                                        fmul(to_float(e2 - tl[2]), t.iz[2]));
                 const float q = fmul(num, rcp);
@@ -178,7 +218,7 @@ __device__ __forceinline__ void raster_face(const float *A, const float4 *__rest
     const int4 fc = faces[f];
     if (!fc.w) return;
     Tri t;
-    if (!setup_triangle(A, V, fc, t)) return;
+    if (!setup_triangle(A, V, fc, t, H, W)) return;
     int minx = min(t.x[0], min(t.x[1], t.x[2])), maxx = max(t.x[0], max(t.x[1], t.x[2]));
     int miny = min(t.y[0], min(t.y[1], t.y[2])), maxy = max(t.y[0], max(t.y[1], t.y[2]));
     int x0 = max(ceil256(minx), 0), x1 = min(floor256(maxx), W - 1);

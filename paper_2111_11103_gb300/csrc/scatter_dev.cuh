@@ -339,6 +339,13 @@ __device__ __forceinline__ void warp_tile_q(const ScatterArgs &a, const uint8_t 
     constexpr int STEPS = (32 + G - 1) / G;  // the longest group range
     constexpr int pstride = C * ES;
     constexpr bool PROD = RULE == SM_RULE_LOGSUM;
+    // BF16 / FP8 storage (p = q * scale, one scale per pixel): sum scales in
+    // its FMA; max-sum and vote decide on the codes (a positive common scale
+    // keeps the order and the ties of a pixel's classes) and scale only the
+    // kept maximum; log-sum scales each value before its clamp (measured
+    // faster than clamping codes at 2^-30 / scale, which needs per-entry scale
+    // products in shared memory).
+    constexpr bool SCALED = DT != SM_F32;
     // first and last pixel of every group range
     constexpr uint32_t kFirst = [] {
         uint32_t m = 0;
@@ -370,7 +377,7 @@ __device__ __forceinline__ void warp_tile_q(const ScatterArgs &a, const uint8_t 
             v[u][m] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (SMEM || rk >= 0) {
                 v[u][m] = load_quad<DT, SMEM>(pb + u * pstride, 4 * (q + LPP * m));
-                if (DT != SM_F32) v[u][m] = scale4(v[u][m], sv[u]);
+                if (SCALED && PROD) v[u][m] = scale4(v[u][m], sv[u]);
             }
         }
     }
@@ -416,10 +423,17 @@ __device__ __forceinline__ void warp_tile_q(const ScatterArgs &a, const uint8_t 
         if (RULE == SM_RULE_SUM) {
 #pragma unroll
             for (int m = 0; m < QPL; ++m) {
-                s[m].x = st ? v[u][m].x : s[m].x + v[u][m].x;
-                s[m].y = st ? v[u][m].y : s[m].y + v[u][m].y;
-                s[m].z = st ? v[u][m].z : s[m].z + v[u][m].z;
-                s[m].w = st ? v[u][m].w : s[m].w + v[u][m].w;
+                if (SCALED) {
+                    s[m].x = fmaf(v[u][m].x, sv[u], st ? 0.f : s[m].x);
+                    s[m].y = fmaf(v[u][m].y, sv[u], st ? 0.f : s[m].y);
+                    s[m].z = fmaf(v[u][m].z, sv[u], st ? 0.f : s[m].z);
+                    s[m].w = fmaf(v[u][m].w, sv[u], st ? 0.f : s[m].w);
+                } else {
+                    s[m].x = st ? v[u][m].x : s[m].x + v[u][m].x;
+                    s[m].y = st ? v[u][m].y : s[m].y + v[u][m].y;
+                    s[m].z = st ? v[u][m].z : s[m].z + v[u][m].z;
+                    s[m].w = st ? v[u][m].w : s[m].w + v[u][m].w;
+                }
             }
         } else if (RULE == SM_RULE_LOGSUM) {
 #pragma unroll
@@ -455,13 +469,14 @@ __device__ __forceinline__ void warp_tile_q(const ScatterArgs &a, const uint8_t 
                     ga = oa;
                 }
             }
+            const float gv = SCALED ? __fmul_rn(gm, sv[u]) : gm;  // the kept maximum, scaled once
 #pragma unroll
             for (int m = 0; m < QPL; ++m) {
                 const int j = q + LPP * m;
                 float4 c;
                 if (RULE == SM_RULE_MAXSUM) {
-                    c = make_float4(v[u][m].x == gm ? v[u][m].x : 0.f, v[u][m].y == gm ? v[u][m].y : 0.f,
-                                    v[u][m].z == gm ? v[u][m].z : 0.f, v[u][m].w == gm ? v[u][m].w : 0.f);
+                    c = make_float4(v[u][m].x == gm ? gv : 0.f, v[u][m].y == gm ? gv : 0.f,
+                                    v[u][m].z == gm ? gv : 0.f, v[u][m].w == gm ? gv : 0.f);
                 } else {
                     c = make_float4(ga == 4 * j ? 1.f : 0.f, ga == 4 * j + 1 ? 1.f : 0.f,
                                     ga == 4 * j + 2 ? 1.f : 0.f, ga == 4 * j + 3 ? 1.f : 0.f);

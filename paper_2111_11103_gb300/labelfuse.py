@@ -36,11 +36,19 @@ SYMBOLS = ["sm_mesh_upload", "sm_fuse_frames", "sm_normalise", "sm_render_labels
            "sm_status_string", "sm_last_error", "sm_profile_enable", "sm_profile_read", "sm_render_rows_noalloc",
            "sm_fuse_render_host", "sm_host_alloc", "sm_host_free", "sm_set_weight_mix", "sm_texel_res_from_gamma",
            "sm_autotune_batch", "sm_fuse_frames_weighted", "sm_conf_features", "sm_conf_targets", "sm_conf_forward",
-           "sm_conf_train_step", "sm_set_queue_shape"]
+           "sm_conf_train_step", "sm_set_queue_shape", "sm_fuse_scenes", "sm_conf_weights"]
 SM_CONF_FEATURES = 5
 SM_CONF_PARAMS = 1281
 SM_NOALLOC_MAX_PIXELS = 1572864
 SM_NOALLOC_MAX_FRAMES = 1024
+
+
+class SceneFrames(ctypes.Structure):
+    """sm_scene_frames: one scene's frames for sm_fuse_scenes."""
+    _fields_ = [("mesh", ctypes.c_void_p), ("d_probs", ctypes.c_void_p), ("dtype", ctypes.c_int),
+                ("d_scale", ctypes.c_void_p), ("d_K", ctypes.c_void_p), ("d_cam_to_world", ctypes.c_void_p),
+                ("N", ctypes.c_int32), ("H", ctypes.c_int32), ("W", ctypes.c_int32),
+                ("d_idmap_out", ctypes.c_void_p)]
 
 
 class LabelFuseError(RuntimeError):
@@ -86,6 +94,8 @@ def lib() -> ctypes.CDLL:
             "sm_conf_forward": [P, P, i64, P, P],
             "sm_conf_train_step": [P, P, P, i64, ctypes.c_float, P, P, P],
             "sm_set_queue_shape": [P, i32, i32, i32, i32, i32, i32],
+            "sm_fuse_scenes": [P, i32, P],
+            "sm_conf_weights": [P, P, i32, P, P, P, i32, i32, i32, P, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -234,6 +244,19 @@ def sm_set_queue_shape(mesh: int, H: int, W: int, frames_per_batch: int, lookahe
                                     int(scatter_tiles)))
 
 
+def sm_fuse_scenes(scenes, stream=None):
+    """Fuses several scenes' frames, each into its own mesh (one call).
+    scenes: (mesh, probs, dtype, scale, K, cam_to_world, N, H, W, idmap_out)
+    per scene, with the arguments of sm_fuse_frames."""
+    arr = (SceneFrames * max(1, len(scenes)))()
+    for i, (mesh, probs, dtype, scale, K, T, N, H, W, idm) in enumerate(scenes):
+        dt = _enum(SM_DTYPE, dtype)
+        p, sc, k, t = _frames_args(mesh, probs, dt, scale, K, T, N, H, W)
+        arr[i] = SceneFrames(mesh, p, dt, sc, k, t, int(N), int(H), int(W),
+                             _arg(idm, "idmap_out", 4 * max(0, N * H * W)))
+    _check(lib().sm_fuse_scenes(arr if scenes else None, len(scenes), _stream(stream)))
+
+
 def sm_fuse_frames_weighted(mesh: int, probs, dtype, scale, K, cam_to_world, N: int, H: int, W: int, weights,
                             idmap_out=None, stream=None):
     dt = _enum(SM_DTYPE, dtype)
@@ -252,6 +275,16 @@ def sm_conf_features(mesh: int, probs, dtype, scale, K, cam_to_world, N: int, H:
     _check(lib().sm_conf_features(mesh, p, dt, sc, k, t, int(N), int(H), int(W),
                                   _arg(feat_out, "feat_out", 4 * SM_CONF_FEATURES * n), _arg(rows_out, "rows_out", 4 * n),
                                   _stream(stream)))
+
+
+def sm_conf_weights(mesh: int, probs, dtype, scale, K, cam_to_world, N: int, H: int, W: int, params, w_out, rows_out,
+                    stream=None):
+    dt = _enum(SM_DTYPE, dtype)
+    p, sc, k, t = _frames_args(mesh, probs, dt, scale, K, cam_to_world, N, H, W)
+    n = max(0, N * H * W)
+    _check(lib().sm_conf_weights(mesh, p, dt, sc, k, t, int(N), int(H), int(W),
+                                 _arg(params, "params", 4 * SM_CONF_PARAMS), _arg(w_out, "w_out", 4 * n),
+                                 _arg(rows_out, "rows_out", 4 * n), _stream(stream)))
 
 
 def sm_conf_targets(mesh: int, probs, dtype, scale, rows, n_pixels: int, target_out, stream=None):

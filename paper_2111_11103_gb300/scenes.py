@@ -37,6 +37,23 @@ def _pool(n: int) -> list:
     return _POOLS[key]
 
 
+def fuse_scenes_queued(jobs: list[SceneJob]) -> None:
+    """Fuses (and, where an output is given, normalises) every scene with one
+    sm_fuse_scenes call on the current stream: scenes that the work queue
+    applies to share persistent launches (the library groups them by class
+    count, storage type and rule); the others are fused one by one."""
+    from . import labelfuse as lf
+    if len({j.mesh for j in jobs}) != len(jobs):
+        raise ValueError("a mesh may appear in one job only")
+    if not jobs:
+        return
+    lf.sm_fuse_scenes([(j.mesh, j.probs, j.dtype, j.scale, j.K, j.cam_to_world, int(j.K.shape[0]), j.H, j.W,
+                        j.idmap_out) for j in jobs])
+    for j in jobs:
+        if j.dist_out is not None or j.labels_out is not None:
+            lf.sm_normalise(j.mesh, j.dist_out, j.labels_out)
+
+
 def fuse_scenes(jobs: list[SceneJob], streams: int = 4) -> None:
     """Fuses (and, where an output is given, normalises) every scene; scene i
     runs on stream i % streams.  The streams start after the work already on

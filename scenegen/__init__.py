@@ -361,6 +361,14 @@ def apartment_poses(n: int, seed: int = BASE_SEED + 5, room=(6.0, 5.0, 3.0), **k
 def ray_cast_classes(scene: Scene, K, T, H: int, W: int, device="cpu", chunk: int = 65536) -> torch.Tensor:
     """Class of the nearest rectangle seen through every pixel centre (analytic
     ray cast against the scene's rectangles); -1 where nothing is hit."""
+    return ray_cast(scene, K, T, H, W, device, chunk)[0]
+
+
+def ray_cast(scene: Scene, K, T, H: int, W: int, device="cpu", chunk: int = 65536):
+    """Analytic ray cast through every pixel centre: (class of the nearest
+    rectangle, -1 where nothing is hit; its depth along the optical axis;
+    |cos| of the angle between the viewing ray and the rectangle's normal),
+    each H x W (depth and cos are 0 where nothing is hit)."""
     dev = torch.device(device)
     fx, fy, cx, cy = (float(x) for x in K)
     Tt = torch.as_tensor(np.asarray(T, dtype=np.float64), device=dev)
@@ -382,6 +390,9 @@ def ray_cast_classes(scene: Scene, K, T, H: int, W: int, device="cpu", chunk: in
     offs = torch.as_tensor(np.cumsum([0] + [r.classes.size for r in scene.rects])[:-1], device=dev)
     flat = torch.as_tensor(np.concatenate([r.classes.ravel() for r in scene.rects]), device=dev)
     out = torch.empty(H * W, dtype=torch.int64, device=dev)
+    depth = torch.zeros(H * W, dtype=torch.float64, device=dev)
+    cosang = torch.zeros(H * W, dtype=torch.float64, device=dev)
+    nn = torch.linalg.norm(Nrm, dim=1)
     for s in range(0, H * W, chunk):
         d = dirs[s:s + chunk]
         t = tnum[None, :] / (d @ Nrm.T)
@@ -396,25 +407,61 @@ def ray_cast_classes(scene: Scene, K, T, H: int, W: int, device="cpu", chunk: in
         iu = torch.minimum(torch.clamp((ai * pu).floor().long(), min=0), pu - 1)
         iv = torch.minimum(torch.clamp((bi * pv).floor().long(), min=0), pv - 1)
         cls = flat[offs[ridx] + iu * pv + iv]
-        out[s:s + chunk] = torch.where(torch.isfinite(tmin), cls, torch.full_like(cls, -1))
-    return out.reshape(H, W)
+        hit = torch.isfinite(tmin)
+        out[s:s + chunk] = torch.where(hit, cls, torch.full_like(cls, -1))
+        # the camera-space direction has z = 1, so the ray parameter is the depth
+        depth[s:s + chunk] = torch.where(hit, tmin, torch.zeros_like(tmin))
+        cs = ((d * Nrm[ridx]).sum(1)).abs() / (torch.linalg.norm(d, dim=1) * nn[ridx])
+        cosang[s:s + chunk] = torch.where(hit, cs, torch.zeros_like(cs))
+    return out.reshape(H, W), depth.reshape(H, W), cosang.reshape(H, W)
 
 
 RECIPES = {
     # boost, i.i.d. noise sd, spatial field sd (0 = none)
     "tiny": (3.0, 1.0, 0.0),
     "paper": (2.5, 0.5, 1.2),
+    "structured": (2.5, 0.5, 0.6),
 }
 
 
+def structured_error_rate(depth, cosang, H: int, W: int):
+    """Probability that the "structured" recipe's prediction of a pixel is
+    confidently wrong: it grows with the grazing angle (1 - |cos|), with the
+    depth beyond 2 m and near the image border (within 24 pixels), as a
+    segmentation network's errors do; at most 0.95."""
+    dev = depth.device
+    ys, xs = torch.meshgrid(torch.arange(H, device=dev, dtype=torch.float64),
+                            torch.arange(W, device=dev, dtype=torch.float64), indexing="ij")
+    border = torch.minimum(torch.minimum(xs, ys), torch.minimum(W - 1 - xs, H - 1 - ys))
+    r = (0.9 * (1.0 - cosang) ** 2 + 0.4 * ((depth - 2.0) / 4.0).clamp(0.0, 1.0)
+         + 0.4 * (1.0 - border / 24.0).clamp(0.0, 1.0))
+    return r.clamp(0.0, 0.95)
+
+
+def confuser_class(gt: torch.Tensor, c: int) -> torch.Tensor:
+    """The wrong class the "structured" recipe predicts for true class gt:
+    (7 gt + 3) mod c, never gt for even c (7 gt + 3 = gt mod c would need
+    6 gt = -3 mod c, odd against even); gt + 1 for odd c."""
+    wrong = (7 * gt + 3) % c
+    return torch.where(wrong == gt, (gt + 1) % c, wrong)
+
+
 def predictions(scene: Scene, cams: Cameras, recipe: str = "paper", frames=None, seed: int = BASE_SEED,
-                device="cpu", out: torch.Tensor | None = None) -> torch.Tensor:
+                device="cpu", out: torch.Tensor | None = None, gt_out: torch.Tensor | None = None) -> torch.Tensor:
     """Softmax predictions (len(frames) x H x W x c float32, HWC) on ``device``.
+    Recipes: "tiny" and "paper" (see the module docstring); "structured" adds
+    confidently wrong predictions (a fixed confuser class per true class) at
+    a rate that grows with the grazing angle, the depth and the nearness to
+    the image border (structured_error_rate), for the learned confidence.
+
+    gt_out, if given (len(frames) x H x W, any integer type), receives the
+    ground-truth class of every pixel (-1: nothing hit).
 
     Frame i draws its noise from a generator seeded with (seed, i) only, so a
     frame's values do not depend on which other frames are generated with it
     (they do depend on the device: CPU and CUDA generators differ)."""
     boost, sd, field_sd = RECIPES[recipe]
+    structured = recipe == "structured"
     dev = torch.device(device)
     frames = range(cams.K.shape[0]) if frames is None else frames
     frames = list(frames)
@@ -424,7 +471,9 @@ def predictions(scene: Scene, cams: Cameras, recipe: str = "paper", frames=None,
     for n, i in enumerate(frames):
         g = torch.Generator(device=dev)
         g.manual_seed((seed * 1_000_003 + i * 7_919) % (2 ** 63 - 1))
-        gt = ray_cast_classes(scene, cams.K[i], cams.cam_to_world[i], H, W, device=dev)
+        gt, depth, cosang = ray_cast(scene, cams.K[i], cams.cam_to_world[i], H, W, device=dev)
+        if gt_out is not None:
+            gt_out[n] = gt
         logits = torch.randn((H, W, c), generator=g, device=dev, dtype=torch.float32) * sd
         if field_sd > 0:
             grid = torch.randn((1, c, 8, 11), generator=g, device=dev, dtype=torch.float32) * field_sd
@@ -432,6 +481,10 @@ def predictions(scene: Scene, cams: Cameras, recipe: str = "paper", frames=None,
             logits += field[0].permute(1, 2, 0)
         onehot = torch.zeros((H, W, c), device=dev, dtype=torch.float32)
         valid = gt >= 0
+        if structured:  # confidently wrong where the view is hard (grazing, far, border)
+            u = torch.rand((H, W), generator=g, device=dev, dtype=torch.float64)
+            wrong = valid & (u < structured_error_rate(depth, cosang, H, W))
+            gt = torch.where(wrong, confuser_class(gt, c), gt)
         onehot[valid, gt[valid]] = boost
         logits += onehot
         out[n] = torch.softmax(logits, dim=-1)

@@ -97,6 +97,8 @@ def test_every_mesh_call_rejects_a_null_handle(libpath):
         "sm_autotune_batch": (None, None, 0, None, None, None, 1, 4, 4, ctypes.byref(b), None),
         "sm_conf_features": (None, None, 0, None, None, None, 1, 4, 4, None, None, None),
         "sm_conf_targets": (None, None, 0, None, None, 16, None, None),
+        "sm_set_queue_shape": (None, 4, 4, 8, 1, 1, 32),
+        "sm_conf_weights": (None, None, 0, None, None, None, 1, 4, 4, None, None, None, None),
     }
     queries = {"sm_num_rows", "sm_num_classes", "sm_mesh_free"}  # -1, -1 and a no-op for NULL
     assert sorted(set(calls) | queries) == _mesh_functions()
@@ -214,3 +216,18 @@ int main(void)
     code, text, reason, rows, freed = r.stdout.strip().split("|")
     assert (code, text, rows, freed) == ("1", "invalid argument", "-1", "0")
     assert "n_classes" in reason
+
+
+def test_fuse_scenes_rejects_bad_scene_lists_on_host(libpath):
+    """sm_fuse_scenes refuses a NULL list, a NULL mesh (naming the scene) and
+    a mesh that appears twice, before any CUDA call."""
+    from paper_2111_11103_gb300 import labelfuse as lf
+    L = lf.lib()
+    assert L.sm_fuse_scenes(None, 2, None) == 1
+    assert L.sm_fuse_scenes(None, 0, None) == 0
+    arr = (lf.SceneFrames * 2)()
+    assert L.sm_fuse_scenes(arr, 2, None) == 1
+    assert "scene 0" in lf.sm_last_error() and "NULL" in lf.sm_last_error()
+    arr[0].mesh = arr[1].mesh = 16  # never dereferenced: refused as shared first
+    assert L.sm_fuse_scenes(arr, 2, None) == 1
+    assert "share a mesh" in lf.sm_last_error()

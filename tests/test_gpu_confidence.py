@@ -146,3 +146,80 @@ def test_targets_and_training_lower_the_loss(ora, dev, medium):
         losses.append(float(loss))
     assert losses[-1] < 0.9 * losses[0]
     assert np.isfinite(losses).all()
+
+
+def test_fused_inference_matches_oracle(ora, dev, medium):
+    """sm_conf_weights (features and network in one pass, hidden layer on the
+    tensor cores): row maps bit for bit; weights against the oracle's network
+    with the first layer's activations rounded to bfloat16 (as the tensor
+    cores take them) within 2e-4, and against the float32-activation forward
+    pass (sm_conf_forward) within 4e-3."""
+    from paper_2111_11103_gb300 import labelfuse as lf
+    scene, cams, probs = medium
+    N, H, W, c = cams.K.shape[0], cams.H, cams.W, scene.n_classes
+    params = torch.as_tensor(_params(6, 0.3), device=dev)
+    V, Fc, K, T, _ = to_dev(scene, cams, None, dev)
+    m = lf.sm_mesh_upload(V, Fc, None, c, "sum", "pixel")
+    try:
+        w = torch.full((N, H, W), -1.0, device=dev)
+        rows = torch.full((N, H, W), -7, dtype=torch.int32, device=dev)
+        lf.sm_conf_weights(m, probs, "f32", None, K, T, N, H, W, params, w, rows)
+        lf.sm_check(m)
+    finally:
+        lf.sm_mesh_free(m)
+    feat, rows_f = gpu_features(scene, cams, probs, dev)
+    assert torch.equal(rows, rows_f)
+    w_fp32 = torch.empty((N, H, W), device=dev)
+    lf.sm_conf_forward(params, feat, N * H * W, w_fp32)
+    w, rows, w_fp32 = w.cpu().numpy(), rows.cpu().numpy(), w_fp32.cpu().numpy()
+    assert np.all(w[rows < 0] == 0.0)
+    fg = rows >= 0
+    np.testing.assert_allclose(w[fg], w_fp32[fg], rtol=0, atol=4e-3)
+    P = probs.cpu().numpy()
+    for i in range(N):
+        X, face = cf.features(ora, scene.vertices, scene.faces, cams.K[i], cams.cam_to_world[i], P[i], H, W)
+        assert np.array_equal(rows[i].ravel(), face)
+        _, w_ora, _ = cf.forward(params.cpu().numpy(), X, act_bf16=True)
+        sel = face >= 0
+        err = np.abs(w[i].ravel()[sel] - w_ora[sel])
+        assert err.max() <= 2e-4 and err.mean() <= 2e-6, (err.max(), err.mean())
+
+
+def test_learned_confidence_gains_over_plain_fusion(dev):
+    """The network's gain: predictions whose errors follow the view (the
+    "structured" recipe: confidently wrong more often at grazing angles, far
+    away and near the image border).  The network is trained on agreement
+    with the plain fused labels; the render-back pixel accuracy against the
+    synthetic ground truth of the weighted fusion must beat plain fusion."""
+    from paper_2111_11103_gb300 import confidence as conf
+    from paper_2111_11103_gb300 import labelfuse as lf
+    scene = sg.paper_room(target_faces=60_000)
+    cams = sg.random_walk_poses(48, H=151, W=203, fx=183.0, fy=183.0, cx=101.0, cy=75.0)
+    N, H, W, c = cams.K.shape[0], cams.H, cams.W, scene.n_classes
+    probs = sg.predictions(scene, cams, "structured", device=dev)
+    gt = torch.stack([sg.ray_cast_classes(scene, cams.K[i], cams.cam_to_world[i], H, W, device=dev)
+                      for i in range(N)])
+    V, Fc, K, T, _ = to_dev(scene, cams, None, dev)
+    acc = {}
+    m = lf.sm_mesh_upload(V, Fc, None, c, "logsum", "pixel")
+    try:
+        params, losses = conf.train(m, probs, K, T, H, W, steps=300, lr=1.0, batch=200_000)
+        assert losses[-1] < losses[0]
+        idm = torch.empty((N, H, W), dtype=torch.int32, device=dev)
+        img = torch.empty((N, H, W), dtype=torch.uint8, device=dev)
+        for mode in ("plain", "weighted"):
+            lf.sm_reset(m)
+            if mode == "plain":
+                lf.sm_fuse_frames(m, probs, "f32", None, K, T, N, H, W, idm)
+            else:
+                conf.fuse_with_confidence(m, params, probs, K, T, H, W, idmap_out=idm)
+            lf.sm_normalise(m)
+            lf.sm_render_idmap(m, idm, N * H * W, img)
+            seen = gt >= 0
+            acc[mode] = float((img.long()[seen] == gt[seen]).float().mean())
+        lf.sm_check(m)
+    finally:
+        lf.sm_mesh_free(m)
+    raw = float((probs.argmax(-1)[gt >= 0] == gt[gt >= 0]).float().mean())
+    print(f"pixel accuracy: raw {raw:.4f}, plain fusion {acc['plain']:.4f}, weighted {acc['weighted']:.4f}")
+    assert acc["weighted"] >= acc["plain"] + 0.005

@@ -152,3 +152,66 @@ def test_scenes_side_by_side_match_the_oracle(ora, dev):
     finally:
         for m in meshes:
             lf.sm_mesh_free(m)
+
+
+def test_fuse_scenes_work_queue_matches_the_oracle(ora, dev):
+    """sm_fuse_scenes on an uneven batch: scenes with c = 20 and 40, F32 and
+    BF16 storage, 5-13 frames of different sizes and different queue shapes
+    share persistent work-queue launches (grouped by class count, storage
+    type and rule); a c = 4 scene and a texel-mode scene take the per-scene
+    path.  Every scene's row maps, counts and accumulators against the
+    oracle, on two calls in a row."""
+    from paper_2111_11103_gb300 import labelfuse as lf
+    from test_gpu_parity import _quantise
+    specs = [  # (scene, cams, dtype, texel steps, queue shape or None)
+        (sg.paper_room(seed=11, target_faces=20_000, n_classes=20),
+         sg.random_walk_poses(7, seed=3, H=120, W=160, fx=150.0, fy=150.0, cx=79.5, cy=59.5), "f32", None,
+         (4, 1, 1, 16)),
+        (sg.paper_room(seed=12, target_faces=30_000), sg.random_walk_poses(13, seed=4, H=96, W=128, fx=115.0,
+                                                                            fy=115.0, cx=63.5, cy=47.5),
+         "f32", None, (8, 2, 2, 64)),
+        (sg.paper_room(seed=13, target_faces=15_000), sg.random_walk_poses(5, seed=5, H=151, W=203, fx=183.0,
+                                                                            fy=183.0, cx=101.0, cy=75.0),
+         "bf16", None, None),
+        (sg.paper_room(seed=14, target_faces=25_000, n_classes=20),
+         sg.random_walk_poses(9, seed=6, H=48, W=64, fx=58.0, fy=58.0, cx=31.5, cy=23.5), "f32", None, (4, 3, 1, 1)),
+        (sg.tiny_room(), sg.circle_poses(n=6), "f32", None, None),
+        (sg.paper_room(seed=15, target_faces=10_000, n_classes=20),
+         sg.random_walk_poses(6, seed=7, H=64, W=96, fx=80.0, fy=80.0, cx=47.5, cy=31.5), "f32", 2, None),
+    ]
+    meshes, calls, checks = [], [], []
+    try:
+        for scene, cams, dtype, texel, shape in specs:
+            N, H, W, c = cams.K.shape[0], cams.H, cams.W, scene.n_classes
+            probs = sg.predictions(scene, cams, "tiny" if c == 4 else "paper", device=dev)
+            if dtype == "f32":
+                q, scale, deq = probs, None, probs.cpu().numpy()
+            else:
+                q, scale, deq = _quantise(probs, dtype)
+            s = None if texel is None else np.full(len(scene.faces), texel, dtype=np.int32)
+            V, Fc, K, T, tr = to_dev(scene, cams, s, dev)
+            m = lf.sm_mesh_upload(V, Fc, tr, c, "logsum", "pixel")
+            meshes.append(m)
+            if shape is not None:
+                lf.sm_set_queue_shape(m, H, W, *shape)
+            idm = torch.full((N, H, W), -9, dtype=torch.int32, device=dev)
+            calls.append((m, q, dtype, scale, K, T, N, H, W, idm))
+            A, cnt, idm_o = ora.fuse_sequence(ora.Mesh(scene.vertices, scene.faces, texel_res=s), cams.K,
+                                              cams.cam_to_world, deq, "logsum", "pixel", nthreads=8, want_idmaps=True)
+            checks.append((m, c, idm, A, cnt, idm_o))
+        for _ in range(2):
+            for m in meshes:
+                lf.sm_reset(m)
+            lf.sm_fuse_scenes(calls)
+            torch.cuda.synchronize()
+            for m, c, idm, A, cnt_o, idm_o in checks:
+                acc, cnt = _state(lf, m, lf.sm_num_rows(m), c, dev)
+                lf.sm_check(m)
+                assert np.array_equal(idm.cpu().numpy(), idm_o)
+                assert np.array_equal(cnt.astype(np.int64), cnt_o)
+                assert_acc_close(acc, A)
+        with pytest.raises(lf.LabelFuseError):
+            lf.sm_fuse_scenes([calls[0], calls[0]])
+    finally:
+        for m in meshes:
+            lf.sm_mesh_free(m)

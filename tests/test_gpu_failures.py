@@ -74,6 +74,8 @@ def test_scatter_wait_runs_out_and_recovers(ora, request, monkeypatch, case, wei
     V, Fc, K, T, _ = to_dev(scene, cams, None, dev)
     m = lf.sm_mesh_upload(V, Fc, None, c, "logsum", weight)
     try:
+        if case == "room20":
+            lf.sm_set_queue_shape(m, H, W, 4, 1, 1, 16)
         monkeypatch.setenv("LABELFUSE_TEST_SKIP_TILE", "0")
         lf.sm_fuse_frames(m, probs, "f32", None, K, T, N, H, W)   # enqueued fine; the kernel gives up
         with pytest.raises(lf.LabelFuseError) as ei:

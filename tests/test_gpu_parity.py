@@ -126,7 +126,9 @@ def small_rooms(dev):
     return rooms
 
 
-PATHS = [("image", None), ("pixel", None), ("pixel", 0)]  # (weight, queue_shape): queue / two-stream paths
+# (weight, queue_shape): image weights (two-stream path), pixel weights on the
+# two-stream path and through the work-queue kernel (c = 20 / 40)
+PATHS = [("image", None), ("pixel", 0), ("pixel", (32, 2, 1, 128))]
 
 
 @pytest.mark.parametrize("c", [40, 20, 4])
@@ -149,13 +151,13 @@ def test_dispatch_matrix(ora, small_rooms, c, dtype, rule, weight, path):
     check_against_oracle(ora, scene, cams, deq, res, rule, weight, nthreads=8)
 
 
-@pytest.mark.parametrize("shape", [(4, 0, 1, 1), (4, 1, 1, 7), (8, 2, 2, 32), (12, 1, 4, 4096), (16, 3, 1, 64),
-                                   (128, 1, 1, 32)])
+@pytest.mark.parametrize("shape", [(4, 1, 1, 1), (4, 1, 1, 7), (8, 2, 2, 32), (12, 1, 4, 4096), (16, 3, 1, 64),
+                                   (128, 1, 1, 32), (4, 4, 1, 3)])
 @pytest.mark.parametrize("rule", ["logsum", "maxsum"])
 def test_queue_shapes(ora, medium, shape, rule):
     """The work-queue kernel under uneven shapes: 24 frames of 203 x 151 in
     batches of 4 to 128 frames (a remainder batch, or one batch shorter than
-    the set length), the raster 0 to 3 batches ahead, raster items of 1 to 4
+    the set length), the raster 1 to 4 batches ahead, raster items of 1 to 4
     cull rounds, scatter items of 1 to 4096 tiles (one item per batch, and
     items that end on a batch's partial tile): results against the oracle."""
     scene, cams, probs = medium

@@ -89,3 +89,24 @@ def test_targets_by_hand():
     rows = np.array([0, 1, 1, -1])
     labels = np.array([1, 0])
     assert list(cf.targets(probs, rows, labels)) == [1.0, 1.0, 0.0, 0.0]
+
+
+def test_forward_with_bfloat16_activations():
+    """act_bf16 rounds exactly the first layer's activations: with
+    activations that are already bfloat16 values it changes nothing, and
+    otherwise it moves w by no more than the rounding can (2^-9 relative per
+    activation through the two later layers)."""
+    rng = np.random.default_rng(11)
+    params = rng.normal(0, 0.3, cf.N_PARAMS)
+    X = rng.uniform(0, 1, (400, cf.N_FEAT))
+    o, w, (_, z1, h1, z2, h2) = cf.forward(params, X)
+    o_b, w_b, (_, _, h1_b, _, _) = cf.forward(params, X, act_bf16=True)
+    assert np.array_equal(h1_b, cf.bf16_round(h1))
+    W1, b1, W2, b2, w3, b3 = cf.unpack(cf.bf16_round(params))
+    bound = (np.abs(h1) * 2.0 ** -8) @ np.abs(W2).T @ np.abs(w3)
+    assert np.all(np.abs(o_b - o) <= bound + 1e-12)
+    # a first layer whose activations are exact bfloat16 values: identical
+    p2 = params.copy()
+    p2[:cf.HID * cf.N_FEAT] = 0.0
+    p2[cf.HID * cf.N_FEAT:cf.HID * cf.N_FEAT + cf.HID] = cf.bf16_round(rng.normal(0, 1, cf.HID))
+    assert np.array_equal(cf.forward(p2, X)[0], cf.forward(p2, X, act_bf16=True)[0])

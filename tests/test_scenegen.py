@@ -2,6 +2,8 @@
 patch-aligned grids, and that patch-agnostic coarse grids really put
 triangles across class boundaries (what the coarse-mesh study relies on)."""
 import numpy as np
+import pytest
+import torch
 
 import scenegen as sg
 
@@ -121,3 +123,34 @@ def test_oracle_sees_through_a_door(ora):
     assert np.all(centre >= 0) and np.all(x[centre] > 6.0 + 1e-6)
     side = face[4:12, 0:4]                                         # 0.75 m or more beside the door
     assert np.all(side >= 0) and np.allclose(x[side], 6.0)
+
+
+def test_structured_recipe_errors_follow_view_difficulty():
+    """The "structured" recipe: the error rate grows with the grazing angle,
+    the depth beyond 2 m and the nearness to the border; the confuser class
+    is never the true class; a frame's predictions are reproducible and
+    wrong (arg max = confuser) far more often on hard pixels than on easy ones."""
+    n = 128
+    z = torch.full((n, n), 1.0, dtype=torch.float64)
+    c1 = torch.ones((n, n), dtype=torch.float64)
+    easy = sg.structured_error_rate(z, c1, n, n)
+    assert float(easy[n // 2, n // 2]) == 0.0
+    assert float(sg.structured_error_rate(z, c1 * 0.3, n, n)[n // 2, n // 2]) > 0.4   # grazing
+    assert float(sg.structured_error_rate(z * 6, c1, n, n)[n // 2, n // 2]) == pytest.approx(0.4)  # far
+    assert float(easy[0, n // 2]) == pytest.approx(0.4)                                  # on the border
+    assert float(easy[12, n // 2]) == pytest.approx(0.2)
+    H, W = 48, 64
+    for c in (4, 20, 21, 40):
+        gt = torch.arange(c)
+        assert not torch.any(sg.confuser_class(gt, c) == gt)
+    scene, cams = sg.paper_room(target_faces=20_000), sg.random_walk_poses(3, H=H, W=W, fx=58.0, fy=58.0,
+                                                                             cx=31.5, cy=23.5)
+    p1 = sg.predictions(scene, cams, "structured")
+    assert torch.equal(p1, sg.predictions(scene, cams, "structured"))
+    gt, depth, cosang = sg.ray_cast(scene, cams.K[0], cams.cam_to_world[0], H, W)
+    assert torch.equal(gt, sg.ray_cast_classes(scene, cams.K[0], cams.cam_to_world[0], H, W))
+    rate = sg.structured_error_rate(depth, cosang, H, W)
+    wrong = (p1[0].argmax(-1) == sg.confuser_class(gt, scene.n_classes)) & (gt >= 0)
+    hard, soft = rate > 0.5, (rate < 0.1) & (gt >= 0)
+    assert hard.any() and soft.any()
+    assert wrong[hard].float().mean() > 0.4 > 0.15 > wrong[soft].float().mean()
