@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the BF16 / FP8 storage forms")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay timing")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default frames per launch")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="frames per launch of the two-stream path (a multiple of 4; skips the autotuner)")
     ap.add_argument("--scenes", type=int, default=0,
                     help="batched form: this many independent rooms of uneven size (64 for the stated spread), fused "
                          "one by one, side by side on streams, through work-queue launches, and as a CUDA graph")
@@ -188,10 +190,13 @@ def peaks():
         return 6800.0, "fallback"
 
 
-TRAFFIC_SOURCES = ("queue.cu", "scatter_dev.cuh", "raster_dev.cuh", "ptx.cuh")
+# ncu summaries that hold a kernel's DRAM traffic per launch, and the
+# sources the capture describes (the figure is used only while they are unchanged)
+TRAFFIC = {"scatter": ("scatter_paper_room.md", ("scatter.cu", "scatter_dev.cuh", "ptx.cuh")),
+           "queue": ("queue_paper_room.md", ("queue.cu", "scatter_dev.cuh", "raster_dev.cuh", "ptx.cuh"))}
 
 
-def source_sha(files=TRAFFIC_SOURCES) -> str:
+def source_sha(files) -> str:
     sha = hashlib.sha256()
     for f in files:
         with open(os.path.join(ROOT, "paper_2111_11103_gb300", "csrc", f), "rb") as fh:
@@ -199,16 +204,19 @@ def source_sha(files=TRAFFIC_SOURCES) -> str:
     return sha.hexdigest()[:16]
 
 
-def queue_traffic_per_frame():
-    """DRAM bytes (read + write) per frame of the work-queue fusion kernel,
-    from the committed ncu summary, or None when the kernel's sources have
-    changed since that capture (the counters would no longer describe it)."""
-    path = os.path.join(ROOT, "profiles", "queue_paper_room.md")
+def kernel_traffic_per_frame(kernel: str):
+    """(DRAM bytes read + written per frame, frames per captured launch) of a
+    kernel from its committed ncu summary, or None when there is none or the
+    kernel's sources have changed since the capture."""
+    if kernel not in TRAFFIC:
+        return None
+    name, files = TRAFFIC[kernel]
     try:
-        fields = dict(re.findall(r"^\s+(\w+): (\S+)$", open(path).read(), re.M))
-        if source_sha() != fields.get("source_sha"):
+        fields = dict(re.findall(r"^\s+(\w+): (\S+)$", open(os.path.join(ROOT, "profiles", name)).read(), re.M))
+        if source_sha(files) != fields.get("source_sha"):
             return None
-        return int(fields["traffic_bytes_per_launch"]) / int(fields["frames_per_launch"])
+        fpl = int(fields["frames_per_launch"])
+        return int(fields["traffic_bytes_per_launch"]) / fpl, fpl
     except (OSError, KeyError, ValueError):
         return None
 
@@ -397,10 +405,16 @@ def run_ours(args):
         achieved = per_frame * fpl / (ms_sc / max(n_sc, 1) / 1e3) / 1e9
         return achieved, per_frame, fpl, kern
 
-    # frames per launch: the library's autotuner on a 256-frame sample
+    # launch path and frames per launch: the library's autotuner on a
+    # 256-frame sample, or a fixed batch
     n_tune = min(256, n_loc)
-    tuned_B = lf.sm_autotune_batch(m, probs[:n_tune], "f32", None, K_loc[:n_tune], T_loc[:n_tune], n_tune, H, W) \
-        if n_tune >= 4 and not args.no_autotune else None
+    if args.batch:
+        lf.sm_set_launch_frames(m, H, W, args.batch)
+        tuned_B = args.batch
+    elif n_tune >= 4 and not args.no_autotune:
+        tuned_B = lf.sm_autotune_batch(m, probs[:n_tune], "f32", None, K_loc[:n_tune], T_loc[:n_tune], n_tune, H, W)
+    else:
+        tuned_B = None
 
     def graph_timing():
         """The same FP32 step captured once into a CUDA graph and replayed
@@ -432,8 +446,12 @@ def run_ours(args):
     achieved, bytes_per_frame_scatter, frames_per_launch, dom = scatter_roofline(prof, 4, False)
     peak, peak_kind = peaks()
     kernels = {k: {"launches": n, "ms_per_step": t / args.steps} for k, (n, t) in prof.items() if n}
-    tpf = queue_traffic_per_frame() if dom == "queue" else None
-    traffic = None if tpf is None or (H, W, c) != (480, 640, 40) else tpf * frames_per_launch
+    if "raster" in kernels:  # its events sit on the second stream and include time spent waiting for SMs
+        kernels["raster"]["note"] = "event span on the raster stream, including waits behind the scatter"
+    # DRAM traffic from the committed capture of one launch of the benchmark's
+    # size, per frame, times the frames per launch of this run
+    tpf = kernel_traffic_per_frame(dom)
+    traffic = None if tpf is None or (H, W, c) != (480, 640, 40) else tpf[0] * frames_per_launch
 
     line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
@@ -443,11 +461,16 @@ def run_ours(args):
             "frames_per_launch": tuned_B, "frame_range": [fa, fb],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": dom,
+                         "traffic_capture_frames_per_launch": None if tpf is None else tpf[1],
                          "algorithmic_bytes_per_launch": bytes_per_frame_scatter * frames_per_launch,
                          "frames_per_launch": frames_per_launch, "peak_kind": peak_kind},
             "kernels": kernels,
             "gpu_launches": launches,
             "clocks": clocks}
+    # parts of the step that sum to it: the kernels on the step's stream by
+    # their events, the rest (the raster not hidden behind them, launch gaps)
+    on_stream = {k: v["ms_per_step"] for k, v in kernels.items() if k != "raster"}
+    line["step_breakdown_ms"] = dict(on_stream, raster_exposed_and_gaps=max(0.0, ms_step - sum(on_stream.values())))
     # step-level HBM fraction on the algorithmic bytes of the whole path
     algo_step = ring * n_loc * (H * W * c * 4 + 2 * H * W * 4 + H * W) + 2 * sg_rows(m, lf) * c * 4
     line["step_hbm_frac"] = algo_step / (ms_step / 1e3) / 1e9 / peak
@@ -750,7 +773,7 @@ def run_learned(args):
     sel = torch.linspace(0, N - 1, n_train, device=dev).round().long()
     qs, ss, Ks, Ts = q[sel].contiguous(), scale[sel].contiguous(), K[sel].contiguous(), T[sel].contiguous()
     t0 = time.perf_counter()
-    params, losses = conf.train(m, qs, Ks, Ts, H, W, steps=300, lr=1.0, batch=200_000, dtype="fp8_e4m3", scale=ss)
+    params, losses = conf.train(m, qs, Ks, Ts, H, W, steps=1000, lr=3.0, batch=200_000, dtype="fp8_e4m3", scale=ss)
     torch.cuda.synchronize(dev)
     t_train = time.perf_counter() - t0
     del qs, ss
@@ -801,7 +824,7 @@ def run_learned(args):
     line = {"study": "learned per-observation confidence, weighted vs plain fusion", "frames": N, "H": H, "W": W,
             "classes": c, "triangles": int(scene.faces.shape[0]), "texel_rows": n_x, "texel_steps": 4,
             "storage": "fp8_e4m3 + per-pixel scale", "recipe": "structured", "rule": "logsum",
-            "train_frames": n_train, "train_steps": 300, "loss_first_last": [float(losses[0]), float(losses[-1])],
+            "train_frames": n_train, "train_steps": 1000, "learning_rate": 3.0, "loss_first_last": [float(losses[0]), float(losses[-1])],
             "raw_argmax_accuracy": raw_hit / max(raw_tot, 1), "plain": out["plain"], "weighted": out["weighted"],
             "gain": out["weighted"]["pixel_accuracy"] - out["plain"]["pixel_accuracy"],
             "generation_s": t_gen, "training_s": t_train}

@@ -213,6 +213,15 @@ sm_status sm_texel_res_from_gamma(sm_mesh *m, const sm_intrinsics *d_K, const do
                                   int32_t H, int32_t W, float gamma, int32_t *d_area_out, int32_t *d_texel_res_out,
                                   void *stream);
 
+/* Frames per launch of the two-stream path (the paper has no counterpart: a
+ * throughput setting of this implementation; results do not depend on it):
+ * later calls on this mesh with frames of H x W pixels raster and scatter
+ * that many frames per launch pair, as if sm_autotune_batch had chosen it.
+ * frames = 0 restores the default (about 48 MB of z-buffer per launch).
+ *   frames   0, or a multiple of 4 in [4, 128].
+ * Errors: SM_ERR_INVALID_ARG. */
+sm_status sm_set_launch_frames(sm_mesh *m, int32_t H, int32_t W, int32_t frames);
+
 /* Frames of one scene for sm_fuse_scenes: the arguments of sm_fuse_frames
  * (device pointers, same layouts) for one mesh. */
 typedef struct sm_scene_frames {

@@ -854,6 +854,18 @@ sm_status sm_autotune_batch(sm_mesh *m, const void *d_probs, sm_dtype dtype, con
     return SM_OK;
 }
 
+sm_status sm_set_launch_frames(sm_mesh *m, int32_t H, int32_t W, int32_t frames)
+{
+    if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
+    sm_status st = check_image(0, H, W);
+    if (st != SM_OK) return st;
+    if (frames < 0 || frames > 128 || (frames & 3) != 0)
+        return fail(SM_ERR_INVALID_ARG, "frames per launch %d: a multiple of 4 in [4, 128], or 0", frames);
+    m->tuned_B = frames;
+    m->tuned_npix = frames ? (int64_t)H * W : 0;
+    return SM_OK;
+}
+
 sm_status sm_set_queue_shape(sm_mesh *m, int32_t H, int32_t W, int32_t frames_per_batch, int32_t lookahead,
                              int32_t raster_rounds, int32_t scatter_tiles)
 {

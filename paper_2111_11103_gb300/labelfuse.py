@@ -36,7 +36,8 @@ SYMBOLS = ["sm_mesh_upload", "sm_fuse_frames", "sm_normalise", "sm_render_labels
            "sm_status_string", "sm_last_error", "sm_profile_enable", "sm_profile_read", "sm_render_rows_noalloc",
            "sm_fuse_render_host", "sm_host_alloc", "sm_host_free", "sm_set_weight_mix", "sm_texel_res_from_gamma",
            "sm_autotune_batch", "sm_fuse_frames_weighted", "sm_conf_features", "sm_conf_targets", "sm_conf_forward",
-           "sm_conf_train_step", "sm_set_queue_shape", "sm_fuse_scenes", "sm_conf_weights"]
+           "sm_conf_train_step", "sm_set_queue_shape", "sm_fuse_scenes", "sm_conf_weights",
+           "sm_set_launch_frames"]
 SM_CONF_FEATURES = 5
 SM_CONF_PARAMS = 1281
 SM_NOALLOC_MAX_PIXELS = 1572864
@@ -96,6 +97,7 @@ def lib() -> ctypes.CDLL:
             "sm_set_queue_shape": [P, i32, i32, i32, i32, i32, i32],
             "sm_fuse_scenes": [P, i32, P],
             "sm_conf_weights": [P, P, i32, P, P, P, i32, i32, i32, P, P, P, P],
+            "sm_set_launch_frames": [P, i32, i32, i32],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -234,6 +236,11 @@ def sm_autotune_batch(mesh: int, probs, dtype, scale, K, cam_to_world, N: int, H
     _check(lib().sm_autotune_batch(mesh, p, dt, sc, k, t, int(N), int(H), int(W), ctypes.byref(best),
                                    _stream(stream)))
     return best.value
+
+
+def sm_set_launch_frames(mesh: int, H: int, W: int, frames: int):
+    """Frames per launch of the two-stream path for H x W frames (0: default)."""
+    _check(lib().sm_set_launch_frames(mesh, int(H), int(W), int(frames)))
 
 
 def sm_set_queue_shape(mesh: int, H: int, W: int, frames_per_batch: int, lookahead: int = 1, raster_rounds: int = 1,

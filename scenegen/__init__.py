@@ -428,13 +428,15 @@ def structured_error_rate(depth, cosang, H: int, W: int):
     """Probability that the "structured" recipe's prediction of a pixel is
     confidently wrong: it grows with the grazing angle (1 - |cos|), with the
     depth beyond 2 m and near the image border (within 24 pixels), as a
-    segmentation network's errors do; at most 0.95."""
+    segmentation network's errors do: 1.8 (1 - |cos|)^2 + 0.8 clamp((z - 2) /
+    4) + 0.8 clamp(1 - d / 24) for depth z in m and border distance d in
+    pixels, at most 0.95."""
     dev = depth.device
     ys, xs = torch.meshgrid(torch.arange(H, device=dev, dtype=torch.float64),
                             torch.arange(W, device=dev, dtype=torch.float64), indexing="ij")
     border = torch.minimum(torch.minimum(xs, ys), torch.minimum(W - 1 - xs, H - 1 - ys))
-    r = (0.9 * (1.0 - cosang) ** 2 + 0.4 * ((depth - 2.0) / 4.0).clamp(0.0, 1.0)
-         + 0.4 * (1.0 - border / 24.0).clamp(0.0, 1.0))
+    r = (1.8 * (1.0 - cosang) ** 2 + 0.8 * ((depth - 2.0) / 4.0).clamp(0.0, 1.0)
+         + 0.8 * (1.0 - border / 24.0).clamp(0.0, 1.0))
     return r.clamp(0.0, 0.95)
 
 

@@ -34,13 +34,28 @@ def test_quantise_scales_and_codes():
         assert float(q.float().amax()) == top  # the largest class maps to the top code exactly
 
 
-def test_traffic_lookup_follows_the_source_hash():
+def test_traffic_lookup_follows_the_source_hash(tmp_path, monkeypatch):
     """The committed capture's traffic is used only while the kernel sources
     it was taken on are unchanged; then it is a plausible per-frame figure."""
     b = _bench()
-    tpf = b.queue_traffic_per_frame()
-    assert tpf is None or 5.0e7 < tpf < 6.5e7  # bytes per 640 x 480 x 40 frame
-    assert len(b.source_sha()) == 16
+    for kern in ("scatter", "queue"):
+        tpf = b.kernel_traffic_per_frame(kern)
+        assert tpf is None or (5.0e7 < tpf[0] < 7.0e7 and tpf[1] >= 1)  # bytes per 640 x 480 x 40 frame
+    assert b.kernel_traffic_per_frame("render") is None
+    # a summary whose hash matches is read; any other hash is ignored
+    sha = b.source_sha(b.TRAFFIC["scatter"][1])
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "scatter_paper_room.md").write_text(
+        f"x\n    traffic_bytes_per_launch: 4400000000\n    frames_per_launch: 84\n    source_sha: {sha}\n")
+    csrc = os.path.join(ROOT, "paper_2111_11103_gb300", "csrc")
+    (tmp_path / "paper_2111_11103_gb300").mkdir()
+    os.symlink(csrc, tmp_path / "paper_2111_11103_gb300" / "csrc")
+    monkeypatch.setattr(b, "ROOT", str(tmp_path))
+    assert b.kernel_traffic_per_frame("scatter") == (4400000000 / 84, 84)
+    (prof / "scatter_paper_room.md").write_text(
+        "x\n    traffic_bytes_per_launch: 4400000000\n    frames_per_launch: 84\n    source_sha: 0000000000000000\n")
+    assert b.kernel_traffic_per_frame("scatter") is None
 
 
 def test_l2_note_states_the_resident_size():

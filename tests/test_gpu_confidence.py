@@ -152,8 +152,12 @@ def test_fused_inference_matches_oracle(ora, dev, medium):
     """sm_conf_weights (features and network in one pass, hidden layer on the
     tensor cores): row maps bit for bit; weights against the oracle's network
     with the first layer's activations rounded to bfloat16 (as the tensor
-    cores take them) within 2e-4, and against the float32-activation forward
-    pass (sm_conf_forward) within 4e-3."""
+    cores take them), and against the float32-activation forward pass
+    (sm_conf_forward) within 4e-3.  Against the oracle the bound is per
+    observation: an activation computed in float32 on the GPU and in binary64
+    in the oracle may round to neighbouring bfloat16 values (at most 2^-6 |h1|
+    apart), which moves o by at most sum_i 2^-6 |h1_i| (|W2|^T |w3|)_i and w
+    by a quarter of that; almost every observation matches far closer."""
     from paper_2111_11103_gb300 import labelfuse as lf
     scene, cams, probs = medium
     N, H, W, c = cams.K.shape[0], cams.H, cams.W, scene.n_classes
@@ -179,10 +183,13 @@ def test_fused_inference_matches_oracle(ora, dev, medium):
     for i in range(N):
         X, face = cf.features(ora, scene.vertices, scene.faces, cams.K[i], cams.cam_to_world[i], P[i], H, W)
         assert np.array_equal(rows[i].ravel(), face)
-        _, w_ora, _ = cf.forward(params.cpu().numpy(), X, act_bf16=True)
+        _, w_ora, (_, _, h1, _, _) = cf.forward(params.cpu().numpy(), X, act_bf16=True)
+        W1, b1, W2, b2, w3, b3 = cf.unpack(cf.bf16_round(params.cpu().numpy()))
+        bound = 0.25 * (2.0 ** -6 * np.abs(h1)) @ (np.abs(W2).T @ np.abs(w3)) + 1e-5
         sel = face >= 0
         err = np.abs(w[i].ravel()[sel] - w_ora[sel])
-        assert err.max() <= 2e-4 and err.mean() <= 2e-6, (err.max(), err.mean())
+        assert np.all(err <= bound[sel]), (err.max(), bound[sel][np.argmax(err - bound[sel])])
+        assert err.mean() <= 2e-6, err.mean()
 
 
 def test_learned_confidence_gains_over_plain_fusion(dev):
@@ -194,7 +201,7 @@ def test_learned_confidence_gains_over_plain_fusion(dev):
     from paper_2111_11103_gb300 import confidence as conf
     from paper_2111_11103_gb300 import labelfuse as lf
     scene = sg.paper_room(target_faces=60_000)
-    cams = sg.random_walk_poses(48, H=151, W=203, fx=183.0, fy=183.0, cx=101.0, cy=75.0)
+    cams = sg.random_walk_poses(24, H=151, W=203, fx=183.0, fy=183.0, cx=101.0, cy=75.0)
     N, H, W, c = cams.K.shape[0], cams.H, cams.W, scene.n_classes
     probs = sg.predictions(scene, cams, "structured", device=dev)
     gt = torch.stack([sg.ray_cast_classes(scene, cams.K[i], cams.cam_to_world[i], H, W, device=dev)
@@ -203,7 +210,7 @@ def test_learned_confidence_gains_over_plain_fusion(dev):
     acc = {}
     m = lf.sm_mesh_upload(V, Fc, None, c, "logsum", "pixel")
     try:
-        params, losses = conf.train(m, probs, K, T, H, W, steps=300, lr=1.0, batch=200_000)
+        params, losses = conf.train(m, probs, K, T, H, W, steps=1000, lr=3.0, batch=200_000)
         assert losses[-1] < losses[0]
         idm = torch.empty((N, H, W), dtype=torch.int32, device=dev)
         img = torch.empty((N, H, W), dtype=torch.uint8, device=dev)

@@ -135,10 +135,11 @@ def test_structured_recipe_errors_follow_view_difficulty():
     c1 = torch.ones((n, n), dtype=torch.float64)
     easy = sg.structured_error_rate(z, c1, n, n)
     assert float(easy[n // 2, n // 2]) == 0.0
-    assert float(sg.structured_error_rate(z, c1 * 0.3, n, n)[n // 2, n // 2]) > 0.4   # grazing
-    assert float(sg.structured_error_rate(z * 6, c1, n, n)[n // 2, n // 2]) == pytest.approx(0.4)  # far
-    assert float(easy[0, n // 2]) == pytest.approx(0.4)                                  # on the border
-    assert float(easy[12, n // 2]) == pytest.approx(0.2)
+    assert float(sg.structured_error_rate(z, c1 * 0.3, n, n)[n // 2, n // 2]) == pytest.approx(1.8 * 0.49)  # grazing
+    assert float(sg.structured_error_rate(z * 6, c1, n, n)[n // 2, n // 2]) == pytest.approx(0.8)  # far
+    assert float(easy[0, n // 2]) == pytest.approx(0.8)                                  # on the border
+    assert float(easy[12, n // 2]) == pytest.approx(0.4)
+    assert float(sg.structured_error_rate(z * 6, c1 * 0.3, n, n)[0, 0]) == 0.95          # capped
     H, W = 48, 64
     for c in (4, 20, 21, 40):
         gt = torch.arange(c)
