@@ -21,13 +21,23 @@ def train(mesh: int, probs, K, cam_to_world, H: int, W: int, steps: int = 200, l
     """Trains the network on the sequence's observations.  mesh: a mesh whose
     rule the targets come from; it is reset, fused (unweighted) and
     normalised here, and left in that state.  Returns (params, losses)."""
+    lf.sm_reset(mesh)
+    lf.sm_fuse_frames(mesh, probs, dtype, scale, K, cam_to_world, int(K.shape[0]), H, W)
+    lf.sm_normalise(mesh)
+    return train_on_labels(mesh, probs, K, cam_to_world, H, W, steps, lr, seed, batch, dtype, scale)
+
+
+def train_on_labels(mesh: int, probs, K, cam_to_world, H: int, W: int, steps: int = 200, lr: float = 1.0,
+                    seed: int = 0, batch: int | None = None, dtype="f32", scale=None):
+    """Trains the network on the observations of the given frames, labelled
+    by agreement with the mesh's current fused labels (the mesh must be
+    normalised: e.g. a plain fusion of a whole sequence, of which these frames
+    are a sample).  The mesh's state is left as it is.  Returns (params,
+    losses)."""
     N, dev = int(K.shape[0]), probs.device
     feat = torch.empty((N, H, W, lf.SM_CONF_FEATURES), device=dev)
     rows = torch.empty((N, H, W), dtype=torch.int32, device=dev)
     lf.sm_conf_features(mesh, probs, dtype, scale, K, cam_to_world, N, H, W, feat, rows)
-    lf.sm_reset(mesh)
-    lf.sm_fuse_frames(mesh, probs, dtype, scale, K, cam_to_world, N, H, W)
-    lf.sm_normalise(mesh)
     y = torch.empty((N, H, W), device=dev)
     lf.sm_conf_targets(mesh, probs, dtype, scale, rows, N * H * W, y)
     sel = rows.reshape(-1) >= 0
