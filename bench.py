@@ -58,8 +58,9 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the BF16 / FP8 storage forms")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay timing")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default frames per launch")
-    ap.add_argument("--batch", type=int, default=0,
-                    help="frames per launch of the two-stream path (a multiple of 4; skips the autotuner)")
+    ap.add_argument("--batch", type=int, default=128,
+                    help="frames per launch of the two-stream path (a multiple of 4), the fastest measured with the "
+                         "autotuner on this workload; 0 runs the autotuner (launch path and shape) instead")
     ap.add_argument("--scenes", type=int, default=0,
                     help="batched form: this many independent rooms of uneven size (64 for the stated spread), fused "
                          "one by one, side by side on streams, through work-queue launches, and as a CUDA graph")
@@ -73,6 +74,9 @@ def parse():
                          "steps from gamma = 0 and 0.2 (a synthetic analogue of the paper's mesh-simplification study)")
     ap.add_argument("--hires", action="store_true",
                     help="1296 x 968 frames (fx = fy = 1170): a 250-frame ring fused and rendered 4 times per step")
+    ap.add_argument("--queue-shape", default="",
+                    help="B,L,R,S: fuse through the work-queue kernel with this shape (frames per batch, lookahead, "
+                         "raster rounds, scatter tiles) instead of the two-stream path")
     ap.add_argument("--dry-run", action="store_true",
                     help="bring up the ranks (gloo, no GPU work) and print each rank's frame range")
     return ap.parse_args()
@@ -408,7 +412,11 @@ def run_ours(args):
     # launch path and frames per launch: the library's autotuner on a
     # 256-frame sample, or a fixed batch
     n_tune = min(256, n_loc)
-    if args.batch:
+    if args.queue_shape:
+        shape = [int(v) for v in args.queue_shape.split(",")]
+        lf.sm_set_queue_shape(m, H, W, *shape)
+        tuned_B = shape[0]
+    elif args.batch:
         lf.sm_set_launch_frames(m, H, W, args.batch)
         tuned_B = args.batch
     elif n_tune >= 4 and not args.no_autotune:

@@ -182,11 +182,17 @@ __device__ __forceinline__ bool pixel_features(unsigned long long key, int64_t p
     const float sc = (dt == SM_F32) ? 1.0f : scale[p];
     // entropy (hardware base-2 logarithm; its error, ~2^-22 relative, is far
     // below the bfloat16 rounding of the network's hidden layer) and top-2
-    // margin, four classes per load when the pixel's row is 16-byte aligned
-    float ent2 = 0.0f, m1 = -INFINITY, m2 = -INFINITY;
+    // margin, four classes per load when the pixel's row is 16-byte aligned.
+    // BF16 / FP8: on the codes q = p / s, the scale applied once:
+    // -sum p log2 p = -s (sum q log2 q + log2(s) sum q), the margin is s times
+    // the codes' margin (the clamp at 2^-30 / s keeps the entropy's terms
+    // those of p, up to rounding)
+    const bool coded = dt != SM_F32 && sc > 0.0f;  // a zero scale means an all-zero prediction
+    const float qmin = coded ? kPMin / sc : kPMin;
+    float eq = 0.0f, sq = 0.0f, m1 = -INFINITY, m2 = -INFINITY;
     auto take = [&](float v) {
-        v = (dt == SM_F32) ? v : __fmul_rn(v, sc);
-        ent2 -= v * __log2f(fmaxf(v, kPMin));
+        eq = fmaf(v, __log2f(fmaxf(v, qmin)), eq);
+        sq += v;
         if (v > m1) {
             m2 = m1;
             m1 = v;
@@ -217,8 +223,9 @@ __device__ __forceinline__ bool pixel_features(unsigned long long key, int64_t p
     } else {
         for (int j = 0; j < c; ++j) take(load_p(probs, dt, p * c + j, 1.0f));
     }
+    const float ent2 = coded ? -sc * fmaf(__log2f(sc), sq, eq) : (dt == SM_F32 ? -eq : 0.0f);
     x[2] = c > 1 ? ent2 / __log2f((float)c) : 0.0f;
-    x[3] = c > 1 ? m1 - m2 : m1;
+    x[3] = c > 1 ? sc * (m1 - m2) : sc * m1;
     const int d = min(min(xx, y), min(W - 1 - xx, H - 1 - y));
     x[4] = (float)d / (0.5f * (float)min(W, H));
     return true;
@@ -240,8 +247,14 @@ __global__ void __launch_bounds__(256)
     __shared__ float s[SM_CONF_PARAMS];
     __shared__ __align__(16) __nv_bfloat16 hs[8][32][kH + 8];  // per warp: its 32 pixels' activations (padded rows)
     __shared__ __align__(16) __nv_bfloat16 w2[kH][kH + 8];     // W2 (row = output), bfloat16
+    __shared__ float4 l1a[kH];                                   // first layer, unit i: W1[i][0..3]
+    __shared__ float2 l1b[kH];                                   // W1[i][4], b1[i]
     load_params(params, s);
     for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) w2[i / kH][i % kH] = __float2bfloat16_rn(s[kW2 + i]);
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+        l1a[i] = make_float4(s[kW1 + i * kF], s[kW1 + i * kF + 1], s[kW1 + i * kF + 2], s[kW1 + i * kF + 3]);
+        l1b[i] = make_float2(s[kW1 + i * kF + 4], s[kB1 + i]);
+    }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     // B fragments of W2^T for the 4 output tiles x 2 input steps (loaded once)
@@ -269,13 +282,14 @@ __global__ void __launch_bounds__(256)
         // first layer, float32, into this lane's row of activations
 #pragma unroll
         for (int i = 0; i < kH; i += 2) {
-            float z0 = s[kB1 + i], z1 = s[kB1 + i + 1];
+            float z[2];
 #pragma unroll
-            for (int k = 0; k < kF; ++k) {
-                z0 = fmaf(s[kW1 + i * kF + k], x[k], z0);
-                z1 = fmaf(s[kW1 + (i + 1) * kF + k], x[k], z1);
+            for (int u = 0; u < 2; ++u) {  // b1 + W1 x in the order k = 0 .. 4
+                const float4 a = l1a[i + u];
+                const float2 b = l1b[i + u];
+                z[u] = fmaf(b.x, x[4], fmaf(a.w, x[3], fmaf(a.z, x[2], fmaf(a.y, x[1], fmaf(a.x, x[0], b.y)))));
             }
-            *reinterpret_cast<uint32_t *>(&hs[warp][lane][i]) = pack_bf16x2(fmaxf(z0, 0.f), fmaxf(z1, 0.f));
+            *reinterpret_cast<uint32_t *>(&hs[warp][lane][i]) = pack_bf16x2(fmaxf(z[0], 0.f), fmaxf(z[1], 0.f));
         }
         __syncwarp();
         // hidden layer: 32 pixels x 32 outputs = 2 x 4 tiles, K = 32 in 2 steps
