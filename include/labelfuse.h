@@ -315,10 +315,14 @@ sm_status sm_fuse_frames_weighted(sm_mesh *m, const void *d_probs, sm_dtype dtyp
  * (1 / interpolated 1/z) / 4 m; prediction entropy -sum p ln max(p, 2^-30) /
  * ln c; top-2 margin p(1) - p(2); distance to the nearest image border /
  * (min(H, W) / 2).  Background pixels get zeros.
- * Network: 5 -> 32 -> 32 -> 1, ReLU, w = sigmoid(o); SM_CONF_PARAMS float32
+ * Network: 5 -> 32 -> 32 -> 1, ReLU, linear output o: the log-odds that the
+ * observation agrees with the fused label.  Fusion weight w = max(0, o), the
+ * log-odds weight of an independent two-way vote (Nitzan and Paroush, 1982)
+ * clipped at zero.  SM_CONF_PARAMS float32
  * parameters in the order W1 (32 x 5, row = output), b1, W2 (32 x 32), b2,
  * w3 (32), b3, used rounded to bfloat16 with float32 accumulation.
- * Training: mean binary cross-entropy against targets y in {0, 1}. */
+ * Training: mean binary cross-entropy of sigmoid(o) against targets
+ * y in {0, 1}. */
 #define SM_CONF_FEATURES 5
 #define SM_CONF_PARAMS 1281
 
@@ -335,11 +339,11 @@ sm_status sm_conf_features(sm_mesh *m, const void *d_probs, sm_dtype dtype, cons
 /* Learned confidence inference in one pass (an extension of the weighted
  * rules of Sec. 3.2.2; the paper has no counterpart): renders the N frames
  * (as sm_fuse_frames) and, per pixel, computes the five features of
- * sm_conf_features and the network's weight w = sigmoid(o) of
+ * sm_conf_features and the network's weight w = max(0, o) of
  * sm_conf_forward, without writing the features out.  The 32 x 32 hidden
  * layer runs on the tensor cores with its inputs (the first layer's ReLU
  * activations) rounded to bfloat16 and float32 accumulation, so w differs
- * from sm_conf_forward's by that rounding (about 1e-3 at most).
+ * from sm_conf_forward's by that rounding (about 4e-3 at most).
  *   d_params     SM_CONF_PARAMS float32 (device).
  *   d_w_out      N x H x W float32: w, 0 for background pixels.
  *   d_rows_out   N x H x W int32: the row map (-1 = background).
@@ -348,6 +352,24 @@ sm_status sm_conf_features(sm_mesh *m, const void *d_probs, sm_dtype dtype, cons
 sm_status sm_conf_weights(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
                           const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N, int32_t H, int32_t W,
                           const float *d_params, float *d_w_out, int32_t *d_rows_out, void *stream);
+
+/* Confidence-weighted fusion with one raster pass per frame: per batch of
+ * frames, the raster, then the weights of sm_conf_weights computed from the
+ * batch's z-buffer (the same kernel, the same w bit for bit), then the
+ * scatter of sm_fuse_frames_weighted with those weights.  The result equals
+ * sm_conf_weights followed by sm_fuse_frames_weighted (up to the order of
+ * the float32 additions), without the second raster pass and the full-size
+ * weight buffer.  Inputs as for sm_fuse_frames, plus
+ *   d_params     SM_CONF_PARAMS float32 (device).
+ *   d_w_out      optional N x H x W float32: receives w (0 for background).
+ *   d_idmap_out  optional N x H x W int32: receives the row map.
+ * Keeps one batch of weights (frames per launch x H x W float32) in the
+ * mesh's scratch.  Errors: as sm_fuse_frames_weighted, SM_ERR_INVALID_ARG
+ * for a NULL d_params. */
+sm_status sm_fuse_frames_confident(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
+                                   const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N, int32_t H,
+                                   int32_t W, const float *d_params, float *d_w_out, int32_t *d_idmap_out,
+                                   void *stream);
 
 /* Training targets: d_target_out[k] = 1 where pixel k's first arg max equals
  * the fused label of its row d_rows[k], else 0 (background, unseen rows).
@@ -359,7 +381,7 @@ sm_status sm_conf_weights(sm_mesh *m, const void *d_probs, sm_dtype dtype, const
 sm_status sm_conf_targets(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
                           const int32_t *d_rows, int64_t n_pixels, float *d_target_out, void *stream);
 
-/* Inference: d_w_out[i] = sigmoid(MLP(d_feat[i])) for n observations.
+/* Inference: d_w_out[i] = max(0, MLP(d_feat[i])) for n observations.
  * d_params SM_CONF_PARAMS float32, d_feat n x SM_CONF_FEATURES float32,
  * d_w_out n float32, all device; n == 0 is a no-op.
  * Errors: SM_ERR_INVALID_ARG (n < 0, NULL pointer), SM_ERR_CUDA. */
@@ -370,8 +392,14 @@ sm_status sm_conf_forward(const float *d_params, const float *d_feat, int64_t n,
  * with respect to the bfloat16-rounded parameters, d_loss_out (1 float,
  * required) the loss before the step, and d_params -= lr * gradient.
  * d_feat n x SM_CONF_FEATURES and d_target n float32; all device.
+ * Reproducible: the sums over observations are exact 64-bit fixed-point sums
+ * (resolution 2^-40) of per-block float32 partial sums, so the same inputs
+ * give the same gradient, loss and parameters bit for bit on one GPU model.
+ * A partial sum that is not finite, or of magnitude 2^22 or more, makes the
+ * gradient and loss NaN.  Takes (SM_CONF_PARAMS + 2) x 8 bytes from the
+ * device's stream-ordered memory pool for the duration of the call.
  * Errors: SM_ERR_INVALID_ARG (n < 0, lr NaN or outside [0, 1e6), NULL
- * pointer), SM_ERR_CUDA. */
+ * pointer), SM_ERR_OOM (the pool allocation failed), SM_ERR_CUDA. */
 sm_status sm_conf_train_step(float *d_params, const float *d_feat, const float *d_target, int64_t n, float lr,
                              float *d_grad_out, float *d_loss_out, void *stream);
 
@@ -475,7 +503,8 @@ typedef enum sm_kernel {
     SM_K_NORMALISE = 5, /* rows -> distributions and labels                    */
     SM_K_RENDER = 6,    /* row maps -> label images                            */
     SM_K_QUEUE = 7,     /* raster + scatter of a whole call in the work queue  */
-    SM_K_COUNT_KINDS = 8
+    SM_K_CONF = 8,      /* confidence weights inside sm_fuse_frames_confident  */
+    SM_K_COUNT_KINDS = 9
 } sm_kernel;
 
 sm_status sm_profile_enable(sm_mesh *m, int32_t on);

@@ -13,10 +13,17 @@ triangle is t (all computed from the oracle's own raster):
   3  top-2 margin p_(1) - p_(2) of the prediction
   4  distance to the nearest image border, min(x, y, W-1-x, H-1-y) / (min(W, H) / 2)
 
-Network 5 -> 32 -> 32 -> 1 with ReLU hidden layers and a sigmoid output
-w = sigmoid(o).  Parameters are one flat vector of 1,281 values in the order
-W1 (32 x 5, row = output), b1 (32), W2 (32 x 32), b2 (32), w3 (32), b3 (1);
-the forward pass uses them rounded to bfloat16 (round to nearest even).
+Network 5 -> 32 -> 32 -> 1 with ReLU hidden layers and a linear output o,
+read as the log-odds that the observation agrees with the fused label
+(sigmoid(o) is that probability).  The fusion weight of the observation is
+w = max(0, o): the log-odds of agreement, clipped at zero so that an
+observation no better than a coin toss gets no say.  For independent voters
+choosing between two answers, weighing each vote by the log-odds of its
+competence is the optimal decision rule (Nitzan and Paroush, Int. Econ. Rev.
+23, 1982); the weighted log-sum of Eq. w-mul is such a vote.  Parameters are one flat
+vector of 1,281 values in the order W1 (32 x 5, row = output), b1 (32),
+W2 (32 x 32), b2 (32), w3 (32), b3 (1); the forward pass uses them rounded
+to bfloat16 (round to nearest even).
 Loss: mean binary cross-entropy softplus(o) - y o against a target y in {0, 1}
 (the pixel's arg max agrees with the plain fusion's label of its row).
 """
@@ -49,7 +56,7 @@ def unpack(params):
 
 
 def forward(params, X, rounding: bool = True, act_bf16: bool = False):
-    """o and w = sigmoid(o) for observations X (n x 5), with the parameters
+    """o and the fusion weight w = max(0, o) for observations X (n x 5), with the parameters
     rounded to bfloat16 (rounding=False: as given, for finite differences);
     also returns the hidden activations for backward.  act_bf16: the first
     layer's activations are rounded to bfloat16 before the hidden layer, the
@@ -63,19 +70,20 @@ def forward(params, X, rounding: bool = True, act_bf16: bool = False):
     z2 = h1 @ W2.T + b2
     h2 = np.maximum(z2, 0.0)
     o = h2 @ w3 + b3[0]
-    w = 1.0 / (1.0 + np.exp(-o))
+    w = np.maximum(o, 0.0)
     return o, w, (X, z1, h1, z2, h2)
 
 
 def loss_and_grad(params, X, y, rounding: bool = True):
     """Mean BCE over the n observations and its gradient with respect to the
     (bfloat16-rounded) parameters, flat, in the parameter order."""
-    o, w, (X, z1, h1, z2, h2) = forward(params, X, rounding)
+    o, _, (X, z1, h1, z2, h2) = forward(params, X, rounding)
+    q = 1.0 / (1.0 + np.exp(-o))  # sigmoid(o): the predicted probability of agreement
     y = np.asarray(y, dtype=np.float64)
     n = X.shape[0]
     loss = np.mean(np.logaddexp(0.0, o) - y * o)
     W1, b1, W2, b2, w3, b3 = unpack(bf16_round(params) if rounding else params)
-    d_o = (w - y) / n
+    d_o = (q - y) / n
     g_w3 = h2.T @ d_o
     g_b3 = np.array([d_o.sum()])
     d_z2 = np.outer(d_o, w3) * (z2 > 0)

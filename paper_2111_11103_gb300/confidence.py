@@ -57,13 +57,11 @@ def train_on_labels(mesh: int, probs, K, cam_to_world, H: int, W: int, steps: in
 
 
 def fuse_with_confidence(mesh: int, params, probs, K, cam_to_world, H: int, W: int, dtype="f32", scale=None,
-                         idmap_out=None):
+                         idmap_out=None, w_out=None):
     """Fuses the frames into the mesh with each observation weighed by the
-    network's confidence (features and network in one pass, sm_conf_weights,
-    then sm_fuse_frames_weighted).  Returns the weights."""
-    N, dev = int(K.shape[0]), probs.device
-    rows = torch.empty((N, H, W), dtype=torch.int32, device=dev)
-    w = torch.empty((N, H, W), device=dev)
-    lf.sm_conf_weights(mesh, probs, dtype, scale, K, cam_to_world, N, H, W, params, w, rows)
-    lf.sm_fuse_frames_weighted(mesh, probs, dtype, scale, K, cam_to_world, N, H, W, w, idmap_out)
-    return w
+    network's confidence, one raster pass per frame (sm_fuse_frames_confident:
+    per batch the raster, the features and network, then the weighted
+    scatter).  w_out: optional N x H x W float32 tensor for the weights."""
+    N = int(K.shape[0])
+    lf.sm_fuse_frames_confident(mesh, probs, dtype, scale, K, cam_to_world, N, H, W, params, w_out, idmap_out)
+    return w_out

@@ -331,9 +331,12 @@ sm_status fuse_queue_impl(sm_mesh *m, const void *d_probs, sm_dtype dtype, const
 }
 
 // Fusion of N frames (sm_fuse_frames; d_weights: explicit per-pixel weights, or null).
+// Fusion of N frames.  d_weights: explicit per-pixel weights (replace w^(I));
+// d_conf: confidence-network parameters, the weights computed per batch from
+// the batch's z-buffer before its scatter (copied to d_w_out if given).
 sm_status fuse_impl(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale, const sm_intrinsics *d_K,
                     const double *d_cam_to_world, int32_t N, int32_t H, int32_t W, const float *d_weights,
-                    int32_t *d_idmap_out, void *stream)
+                    int32_t *d_idmap_out, void *stream, const float *d_conf = nullptr, float *d_w_out = nullptr)
 {
     if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
     sm_status st = check_image(N, H, W);
@@ -348,20 +351,22 @@ sm_status fuse_impl(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t npix = (int64_t)H * W;
     const int B = batch_frames(m, npix, N);
-    const bool image_w = m->weight == SM_WEIGHT_IMAGE && !d_weights;  // explicit weights replace w^(I)
+    const bool image_w = m->weight == SM_WEIGHT_IMAGE && !d_weights && !d_conf;  // explicit weights replace w^(I)
     const bool tma = lf::scatter_tma_supported(m->c);
     // face mode with the pipelined scatter: the scatter reads the z-buffer
     // keys itself; otherwise a resolve pass writes the row map first
     const bool from_keys = tma && !m->texel_mode;
     // face mode with pixel weights and c = 20 / 40: raster and scatter of the
     // whole call in the persistent work-queue kernel
-    if (from_keys && !image_w && !d_weights && lf::fuse_queue_supported(m->c) && m->use_queue)
+    if (from_keys && !image_w && !d_weights && !d_conf && lf::fuse_queue_supported(m->c) && m->use_queue)
         return fuse_queue_impl(m, d_probs, dtype, d_scale, d_K, d_cam_to_world, N, H, W, d_idmap_out, s);
     const bool need_ids = !from_keys || image_w;
     // the pipelined scatter reads its row map from the library's aligned buffer
     const bool ids_internal = need_ids && (!d_idmap_out || (tma && !from_keys));
     if ((st = prepare_frames(m, d_K, d_cam_to_world, N, npix, B, ids_internal, s)) != SM_OK) return st;
     if (image_w && (st = grow(&m->fcnt, &m->fcnt_cap, (int64_t)B * m->n_x, s, 0, "row histograms")) != SM_OK)
+        return st;
+    if (d_conf && (st = grow(&m->wbuf, &m->wbuf_cap, (int64_t)B * npix, s, -1, "confidence weights")) != SM_OK)
         return st;
     const size_t esz = dtype_size(dtype);
     cudaStream_t r = m->rstream;
@@ -379,6 +384,23 @@ sm_status fuse_impl(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float
         if ((st = raster_only(m, f0, nb, H, W, keys, r)) != SM_OK) return st;
         LF_CUDA(cudaEventRecord(m->ev_rast[slot], r), "event");
         LF_CUDA(cudaStreamWaitEvent(s, m->ev_rast[slot], 0), "event");
+        if (d_conf) {
+            // weights from the keys as they stand (the scatter or the resolve
+            // re-arms them afterwards)
+            {
+                ProfScope p(m, SM_K_CONF, s);
+                lf::launch_conf_weights(keys, npix * nb, H, W, m->verts, m->faces, m->F, d_K + f0,
+                                        d_cam_to_world + 16 * (int64_t)f0,
+                                        static_cast<const char *>(d_probs) + (size_t)f0 * npix * m->c * esz, dtype,
+                                        d_scale ? d_scale + (size_t)f0 * npix : nullptr, m->c, d_conf, m->wbuf,
+                                        nullptr, s);
+            }
+            LF_LAUNCHED("confidence weights");
+            if (d_w_out)
+                LF_CUDA(cudaMemcpyAsync(d_w_out + (size_t)f0 * npix, m->wbuf, (size_t)nb * npix * sizeof(float),
+                                        cudaMemcpyDeviceToDevice, s),
+                        "weights copy");
+        }
         if (!from_keys &&
             (st = resolve_only(m, f0, nb, H, W, keys, idm, s, idm != user_idm ? user_idm : nullptr)) != SM_OK)
             return st;
@@ -391,7 +413,7 @@ sm_status fuse_impl(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float
             const char *probs = static_cast<const char *>(d_probs) + (size_t)f0 * npix * m->c * esz;
             const float *scale = d_scale ? d_scale + (size_t)f0 * npix : nullptr;
             const uint32_t *fcnt = image_w ? m->fcnt : nullptr;
-            const float *wpix = d_weights ? d_weights + (size_t)f0 * npix : nullptr;
+            const float *wpix = d_conf ? m->wbuf : d_weights ? d_weights + (size_t)f0 * npix : nullptr;
             if (tma)
                 lf::launch_scatter_tma(m->rule, dtype, probs, scale, from_keys ? keys : nullptr,
                                        from_keys ? nullptr : idm, from_keys ? idm : nullptr, npix * nb, npix, m->c,
@@ -552,6 +574,16 @@ sm_status sm_fuse_frames_weighted(sm_mesh *m, const void *d_probs, sm_dtype dtyp
 {
     if (N > 0 && !d_weights) return fail(SM_ERR_INVALID_ARG, "weights are NULL");
     return fuse_impl(m, d_probs, dtype, d_scale, d_K, d_cam_to_world, N, H, W, d_weights, d_idmap_out, stream);
+}
+
+sm_status sm_fuse_frames_confident(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
+                                   const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N, int32_t H,
+                                   int32_t W, const float *d_params, float *d_w_out, int32_t *d_idmap_out,
+                                   void *stream)
+{
+    if (!d_params && N > 0) return fail(SM_ERR_INVALID_ARG, "NULL confidence parameters");
+    return fuse_impl(m, d_probs, dtype, d_scale, d_K, d_cam_to_world, N, H, W, nullptr, d_idmap_out, stream, d_params,
+                     d_w_out);
 }
 
 sm_status sm_fuse_scenes(const sm_scene_frames *scenes, int32_t n, void *stream)
@@ -951,8 +983,15 @@ sm_status sm_conf_weights(sm_mesh *m, const void *d_probs, sm_dtype dtype, const
                                 d_cam_to_world + 16 * (int64_t)f0,
                                 static_cast<const char *>(d_probs) + (size_t)f0 * npix * m->c * esz, dtype,
                                 d_scale ? d_scale + (size_t)f0 * npix : nullptr, m->c, d_params,
-                                d_w_out + (size_t)f0 * npix, d_rows_out + (int64_t)f0 * npix, s);
+                                d_w_out + (size_t)f0 * npix, m->texel_mode ? nullptr : d_rows_out + (int64_t)f0 * npix,
+                                s);
         LF_LAUNCHED("confidence weights");
+        // texel mode: the row of a pixel is its texel's (the resolve pass
+        // writes it and re-arms the keys); face mode: the kernel wrote the
+        // triangle and re-armed the keys itself
+        if (m->texel_mode &&
+            (st = resolve_only(m, f0, nb, H, W, m->keys, d_rows_out + (int64_t)f0 * npix, s)) != SM_OK)
+            return st;
     }
     return SM_OK;
 }
@@ -991,9 +1030,13 @@ sm_status sm_conf_train_step(float *d_params, const float *d_feat, const float *
     if (!(lr >= 0.0f && lr < 1.0e6f)) return fail(SM_ERR_INVALID_ARG, "learning rate %g", (double)lr);
     if (!d_params || !d_grad_out || !d_loss_out || (n > 0 && (!d_feat || !d_target)))
         return fail(SM_ERR_INVALID_ARG, "NULL pointer");
-    lf::launch_conf_train_step(d_params, d_feat, d_target, n, lr, d_grad_out, d_loss_out,
-                               static_cast<cudaStream_t>(stream));
-    LF_LAUNCHED("confidence training step");
+    const cudaError_t e = lf::launch_conf_train_step(d_params, d_feat, d_target, n, lr, d_grad_out, d_loss_out,
+                                                     static_cast<cudaStream_t>(stream));
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(SM_ERR_OOM, "confidence training step: stream-ordered allocation of its sums");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "confidence training step");
     return SM_OK;
 }
 
@@ -1168,7 +1211,7 @@ sm_status sm_mesh_free(sm_mesh *m)
         DeviceGuard g(m->device);
         cudaDeviceSynchronize();
         void *bufs[] = {m->verts, m->faces,  m->row0,   m->texinfo, m->acc,     m->cnt,    m->labels8,
-                        m->err,   m->cams,   m->keys,   m->idbuf,   m->fcnt,    m->bounds, m->hstage,
+                        m->err,   m->cams,   m->keys,   m->idbuf,   m->wbuf,   m->fcnt,    m->bounds, m->hstage,
                         m->hids,  m->hlabels, m->hcam,  m->clist,   m->ccount, m->area,    m->qctr};
         for (void *b : bufs)
             if (b) cudaFree(b);

@@ -7,11 +7,18 @@
 //    between the visible triangle's normal and the pixel's viewing ray, depth
 //    (1 / interpolated 1/z, / 4 m), prediction entropy (/ ln c), top-2
 //    margin, distance to the image border (/ half the smaller side).
-//  * k_conf_forward: 5 -> 32 -> 32 -> 1 MLP, ReLU, sigmoid output, the
-//    parameters rounded to bfloat16, float32 accumulation.
+//  * k_conf_forward: 5 -> 32 -> 32 -> 1 MLP, ReLU, the parameters rounded to
+//    bfloat16, float32 accumulation.  Its output o is the log-odds that the
+//    observation agrees with the fused label (trained with the binary
+//    cross-entropy of sigmoid(o)); the fusion weight is w = max(0, o), the
+//    optimal weight of an independent two-way vote (Nitzan and Paroush,
+//    1982) clipped at zero.
 //  * k_conf_grad + k_conf_update: one step of gradient descent on the mean
 //    binary cross-entropy; each block reduces its observations' gradients in
-//    shared memory before one atomic add per parameter.
+//    shared memory (fixed order), converts the sums to 64-bit fixed point
+//    (2^-40) and adds them with integer atomics, so the step's gradient does
+//    not depend on the order in which blocks finish: training runs are
+//    reproducible bit for bit.
 //  * k_conf_targets: 1 where a pixel's arg max equals its row's fused label.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -232,11 +239,12 @@ __device__ __forceinline__ bool pixel_features(unsigned long long key, int64_t p
 }
 
 // One thread per pixel of a rasterised batch, one warp per 32 pixels: the
-// features, then w = sigmoid(network) with the bfloat16 parameters; the
+// features, then w = max(0, network) with the bfloat16 parameters; the
 // first layer in float32, the 32 x 32 hidden layer as 16 tensor-core tiles
 // per warp (activations rounded to bfloat16, float32 accumulation), the
-// output layer in float32.  Writes w (0 for background) and the row map, and
-// re-arms the z-buffer.
+// output layer in float32.  Writes w (0 for background) and, when rows_out
+// is given, the triangle of every pixel (-1 for background), re-arming the
+// z-buffer; without rows_out the keys are left as they are.
 __global__ void __launch_bounds__(256)
     k_conf_weights(unsigned long long *__restrict__ keys, int64_t total, int H, int W, const float4 *__restrict__ V,
                    const int4 *__restrict__ faces, int64_t F, const sm_intrinsics *__restrict__ K,
@@ -274,10 +282,12 @@ __global__ void __launch_bounds__(256)
         int32_t row = -1;
         if (p < total) {
             const unsigned long long key = keys[p];
-            keys[p] = kEmptyKey;
             fg = pixel_features(key, p, H, W, V, faces, F, K, T, probs, dt, scale, c, x);
-            if (fg) row = (int32_t)(unsigned int)key;
-            rows_out[p] = row;
+            if (rows_out) {  // else the keys stay for the scatter or the resolve pass
+                keys[p] = kEmptyKey;
+                if (fg) row = (int32_t)(unsigned int)key;
+                rows_out[p] = row;
+            }
         }
         // first layer, float32, into this lane's row of activations
 #pragma unroll
@@ -332,7 +342,7 @@ __global__ void __launch_bounds__(256)
         const float o0 = __shfl_sync(0xffffffffu, o[0][0], src), o1 = __shfl_sync(0xffffffffu, o[0][1], src);
         const float o2 = __shfl_sync(0xffffffffu, o[1][0], src), o3 = __shfl_sync(0xffffffffu, o[1][1], src);
         const float ol = mt == 0 ? (r < 8 ? o0 : o1) : (r < 8 ? o2 : o3);
-        if (p < total) w_out[p] = fg ? 1.0f / (1.0f + expf(-ol)) : 0.0f;
+        if (p < total) w_out[p] = fg ? fmaxf(ol, 0.0f) : 0.0f;
         __syncwarp();  // the activations are rewritten by the next pixels
     }
 }
@@ -348,16 +358,36 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int k = 0; k < kF; ++k) x[k] = feat[i * kF + k];
     const float o = mlp_forward(s, x, z1, z2);
-    w[i] = 1.0f / (1.0f + expf(-o));
+    w[i] = fmaxf(o, 0.0f);
 }
 
 constexpr int kObs = 128;  // observations per block in the gradient kernel
+constexpr float kFixed = 1099511627776.0f;          // 2^40: resolution of the fixed-point sums
+constexpr float kFixedMax = 4.611686018427388e18f;  // 2^62
+
+// acc[i] += v * 2^40 rounded to an integer (two's complement in 64 bits,
+// exact and associative); a non-finite v, or |v| >= 2^22 (a block's share of
+// a mean gradient: only a diverged run gets there), is counted in
+// acc[SM_CONF_PARAMS + 1] instead.
+__device__ __forceinline__ void add_fixed(unsigned long long *acc, int i, float v)
+{
+    const float x = v * kFixed;
+    if (fabsf(x) < kFixedMax)
+        atomicAdd(acc + i, (unsigned long long)__float2ll_rn(x));
+    else
+        atomicAdd(acc + SM_CONF_PARAMS + 1, 1ull);
+}
+
+__device__ __forceinline__ float from_fixed(unsigned long long a)
+{
+    return (float)((double)(long long)a * (1.0 / 1099511627776.0));
+}
 // per-observation vectors kept for the block's reduction: x, h1, d_z1, h2, d_z2, d_o
 constexpr int kRow = kF + 4 * kH + 1;
 
 __global__ void __launch_bounds__(kObs)
     k_conf_grad(const float *__restrict__ params, const float *__restrict__ feat, const float *__restrict__ target,
-                int64_t n, float *__restrict__ grad, float *__restrict__ loss)
+                int64_t n, unsigned long long *__restrict__ acc)
 {
     extern __shared__ float sm[];
     float *s = sm;                          // SM_CONF_PARAMS (bf16-rounded)
@@ -391,7 +421,7 @@ __global__ void __launch_bounds__(kObs)
     }
     // block sum of the loss
     for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, l);
+    if ((threadIdx.x & 31) == 0) add_fixed(acc, SM_CONF_PARAMS, l);
     __syncthreads();
     // each thread sums some parameters' gradients over the block's observations
     for (int q = threadIdx.x; q < SM_CONF_PARAMS; q += blockDim.x) {
@@ -407,14 +437,25 @@ __global__ void __launch_bounds__(kObs)
             else v = rt[kF + 4 * kH];                                                          // b3
             g += v;
         }
-        atomicAdd(grad + q, g);
+        add_fixed(acc, q, g);
     }
 }
 
-__global__ void k_conf_update(float *__restrict__ params, const float *__restrict__ grad, float lr)
+// acc: SM_CONF_PARAMS gradient sums, the loss, a count of non-finite partial
+// sums; converts them to float32 (NaN everywhere once a partial sum was not
+// finite) and takes the step.
+__global__ void k_conf_update(float *__restrict__ params, const unsigned long long *__restrict__ acc, float lr,
+                              float *__restrict__ grad, float *__restrict__ loss)
 {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < SM_CONF_PARAMS) params[q] -= lr * grad[q];
+    const bool bad = acc[SM_CONF_PARAMS + 1] != 0ull;
+    if (q < SM_CONF_PARAMS) {
+        const float g = bad ? __int_as_float(0x7fc00000) : from_fixed(acc[q]);
+        grad[q] = g;
+        params[q] -= lr * g;
+    } else if (q == SM_CONF_PARAMS) {
+        *loss = bad ? __int_as_float(0x7fc00000) : from_fixed(acc[q]);
+    }
 }
 
 __global__ void __launch_bounds__(256)
@@ -470,19 +511,26 @@ void launch_conf_forward(const float *params, const float *feat, int64_t n, floa
     k_conf_forward<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(params, feat, n, w);
 }
 
-void launch_conf_train_step(float *params, const float *feat, const float *target, int64_t n, float lr, float *grad,
-                            float *loss, cudaStream_t s)
+cudaError_t launch_conf_train_step(float *params, const float *feat, const float *target, int64_t n, float lr,
+                                   float *grad, float *loss, cudaStream_t s)
 {
-    cudaMemsetAsync(grad, 0, SM_CONF_PARAMS * sizeof(float), s);
-    cudaMemsetAsync(loss, 0, sizeof(float), s);
+    // fixed-point sums: SM_CONF_PARAMS gradients, the loss, the non-finite count
+    constexpr size_t kAccBytes = (SM_CONF_PARAMS + 2) * sizeof(unsigned long long);
+    unsigned long long *acc = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&acc), kAccBytes, s);
+    if (e != cudaSuccess) return e;
+    cudaMemsetAsync(acc, 0, kAccBytes, s);
     if (n > 0) {
         const size_t smem = (SM_CONF_PARAMS + 3 + (size_t)kObs * kRow) * sizeof(float);
         static PerDeviceOnce configured;
         if (configured.first(current_device()))
             cudaFuncSetAttribute(k_conf_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_conf_grad<<<(unsigned)((n + kObs - 1) / kObs), kObs, smem, s>>>(params, feat, target, n, grad, loss);
+        k_conf_grad<<<(unsigned)((n + kObs - 1) / kObs), kObs, smem, s>>>(params, feat, target, n, acc);
     }
-    k_conf_update<<<(SM_CONF_PARAMS + 255) / 256, 256, 0, s>>>(params, grad, lr);
+    k_conf_update<<<(SM_CONF_PARAMS + 1 + 255) / 256, 256, 0, s>>>(params, acc, lr, grad, loss);
+    e = cudaGetLastError();
+    const cudaError_t ef = cudaFreeAsync(acc, s);
+    return e != cudaSuccess ? e : ef;
 }
 
 void launch_conf_targets(const void *probs, sm_dtype dt, const float *scale, int c, const int32_t *rows, int64_t n,

@@ -155,8 +155,8 @@ void launch_conf_forward(const float *params, const float *feat, int64_t n, floa
 void launch_conf_weights(unsigned long long *keys, int64_t total, int H, int W, const float4 *V, const int4 *faces,
                          int64_t F, const sm_intrinsics *K, const double *T, const void *probs, sm_dtype dt,
                          const float *scale, int c, const float *params, float *w, int32_t *rows, cudaStream_t s);
-void launch_conf_train_step(float *params, const float *feat, const float *target, int64_t n, float lr, float *grad,
-                            float *loss, cudaStream_t s);
+cudaError_t launch_conf_train_step(float *params, const float *feat, const float *target, int64_t n, float lr,
+                                   float *grad, float *loss, cudaStream_t s);
 void launch_conf_targets(const void *probs, sm_dtype dt, const float *scale, int c, const int32_t *rows, int64_t n,
                          const uint8_t *labels8, int64_t n_x, float *y, cudaStream_t s);
 void launch_normalise(sm_rule rule, const float *acc, const uint32_t *cnt, int64_t n_x, int c, float *dist,
@@ -218,6 +218,8 @@ struct sm_mesh {
     int64_t area_cap = 0;
     int32_t *idbuf = nullptr;
     int64_t idbuf_cap = 0;
+    float *wbuf = nullptr;  // one batch of per-pixel confidence weights
+    int64_t wbuf_cap = 0;
     uint32_t *fcnt = nullptr;
     int64_t fcnt_cap = 0;
     uint32_t *qctr = nullptr;  // work-queue head, completion counts and abort flag

@@ -27,7 +27,7 @@ SM_RULE = {"sum": 0, "logsum": 1, "maxsum": 2, "vote": 3}
 SM_WEIGHT = {"pixel": 0, "image": 1}
 SM_DTYPE = {"f32": 0, "bf16": 1, "fp8_e4m3": 2}
 SM_KERNEL = {"project": 0, "raster": 1, "resolve": 2, "count": 3, "scatter": 4, "normalise": 5, "render": 6,
-             "queue": 7}
+             "queue": 7, "conf": 8}
 SM_OK = 0
 SM_ERR_INVALID_ARG = 1
 SM_MAX_CLASSES = 254
@@ -37,7 +37,7 @@ SYMBOLS = ["sm_mesh_upload", "sm_fuse_frames", "sm_normalise", "sm_render_labels
            "sm_fuse_render_host", "sm_host_alloc", "sm_host_free", "sm_set_weight_mix", "sm_texel_res_from_gamma",
            "sm_autotune_batch", "sm_fuse_frames_weighted", "sm_conf_features", "sm_conf_targets", "sm_conf_forward",
            "sm_conf_train_step", "sm_set_queue_shape", "sm_fuse_scenes", "sm_conf_weights",
-           "sm_set_launch_frames"]
+           "sm_set_launch_frames", "sm_fuse_frames_confident"]
 SM_CONF_FEATURES = 5
 SM_CONF_PARAMS = 1281
 SM_NOALLOC_MAX_PIXELS = 1572864
@@ -90,6 +90,7 @@ def lib() -> ctypes.CDLL:
             "sm_texel_res_from_gamma": [P, P, P, i32, i32, i32, ctypes.c_float, P, P, P],
             "sm_autotune_batch": [P, P, i32, P, P, P, i32, i32, i32, ctypes.POINTER(i32), P],
             "sm_fuse_frames_weighted": [P, P, i32, P, P, P, i32, i32, i32, P, P, P],
+            "sm_fuse_frames_confident": [P, P, i32, P, P, P, i32, i32, i32, P, P, P, P],
             "sm_conf_features": [P, P, i32, P, P, P, i32, i32, i32, P, P, P],
             "sm_conf_targets": [P, P, i32, P, P, i64, P, P],
             "sm_conf_forward": [P, P, i64, P, P],
@@ -272,6 +273,16 @@ def sm_fuse_frames_weighted(mesh: int, probs, dtype, scale, K, cam_to_world, N: 
     _check(lib().sm_fuse_frames_weighted(mesh, p, dt, sc, k, t, int(N), int(H), int(W),
                                          _arg(weights, "weights", 4 * n), _arg(idmap_out, "idmap_out", 4 * n),
                                          _stream(stream)))
+
+
+def sm_fuse_frames_confident(mesh: int, probs, dtype, scale, K, cam_to_world, N: int, H: int, W: int, params,
+                             w_out=None, idmap_out=None, stream=None):
+    dt = _enum(SM_DTYPE, dtype)
+    p, sc, k, t = _frames_args(mesh, probs, dt, scale, K, cam_to_world, N, H, W)
+    n = max(0, N * H * W)
+    _check(lib().sm_fuse_frames_confident(mesh, p, dt, sc, k, t, int(N), int(H), int(W),
+                                          _arg(params, "params", 4 * SM_CONF_PARAMS), _arg(w_out, "w_out", 4 * n),
+                                          _arg(idmap_out, "idmap_out", 4 * n), _stream(stream)))
 
 
 def sm_conf_features(mesh: int, probs, dtype, scale, K, cam_to_world, N: int, H: int, W: int, feat_out, rows_out,

@@ -99,6 +99,7 @@ def test_every_mesh_call_rejects_a_null_handle(libpath):
         "sm_conf_targets": (None, None, 0, None, None, 16, None, None),
         "sm_set_queue_shape": (None, 4, 4, 8, 1, 1, 32),
         "sm_conf_weights": (None, None, 0, None, None, None, 1, 4, 4, None, None, None, None),
+        "sm_fuse_frames_confident": (None, None, 0, None, None, None, 1, 4, 4, None, None, None, None),
         "sm_set_launch_frames": (None, 4, 4, 8),
     }
     queries = {"sm_num_rows", "sm_num_classes", "sm_mesh_free"}  # -1, -1 and a no-op for NULL

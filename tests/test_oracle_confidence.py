@@ -31,10 +31,19 @@ def test_gradient_matches_finite_differences():
 
 def test_forward_closed_forms():
     p = np.zeros(cf.N_PARAMS)
-    p[-1] = 0.75  # b3
-    _, w, _ = cf.forward(p, np.ones((3, cf.N_FEAT)))
-    assert np.allclose(w, 1 / (1 + np.exp(-0.75)), rtol=0, atol=1e-15)
-    # one path through: o = relu(relu(x0)) -> w = sigmoid(x0) for x0 >= 0, 0.5 for x0 < 0
+    p[-1] = 0.75  # b3: o = 0.75 for every input, the weight is the log-odds itself
+    o, w, _ = cf.forward(p, np.ones((3, cf.N_FEAT)))
+    assert np.array_equal(o, [0.75] * 3) and np.array_equal(w, [0.75] * 3)
+    p[-1] = -0.75  # below even odds: no weight
+    o, w, _ = cf.forward(p, np.ones((3, cf.N_FEAT)))
+    assert np.array_equal(o, [-0.75] * 3) and np.array_equal(w, [0.0] * 3)
+    # the loss at o = b3 is the BCE of the constant probability sigmoid(b3)
+    y = np.array([1.0, 0.0, 1.0])
+    l, g = cf.loss_and_grad(p, np.ones((3, cf.N_FEAT)), y)
+    q = 1 / (1 + np.exp(0.75))
+    assert abs(l - np.mean(-(y * np.log(q) + (1 - y) * np.log(1 - q)))) <= 1e-15
+    assert abs(g[-1] - np.mean(q - y)) <= 1e-15  # d loss / d b3
+    # one path through: o = relu(relu(x0)) = x0 for x0 >= 0, 0 for x0 < 0
     W1, b1, W2, b2, w3, b3 = cf.unpack(np.zeros(cf.N_PARAMS))
     q = np.zeros(cf.N_PARAMS)
     q[0] = 1.0                                   # W1[0, 0]
