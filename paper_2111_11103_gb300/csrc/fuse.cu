@@ -41,44 +41,85 @@ __device__ __forceinline__ float load_prob(const void *base, int64_t idx)
 
 // |K_i ∩ K_x| for every frame i of the batch and row x: histogram of the row
 // map, or of the z-buffer keys (face mode, row = triangle) when idmap is null.
-__global__ void k_count(const int32_t *__restrict__ idmap, const unsigned long long *__restrict__ keys,
-                        int64_t total, int64_t npix, uint32_t *__restrict__ fcnt, int64_t n_x)
+// kPixUnroll pixels per thread (see kPixThreads); the pixels of one run of a
+// row within a warp add their count with one atomic.
+__global__ void __launch_bounds__(kPixThreads) k_count(const int32_t *__restrict__ idmap,
+                                                       const unsigned long long *__restrict__ keys, int64_t total,
+                                                       int64_t npix, uint32_t *__restrict__ fcnt, int64_t n_x)
 {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= total) return;
-    int64_t row;
-    if (idmap) {
-        row = idmap[p];
-    } else {
-        const unsigned long long key = keys[p];
-        row = (key == kEmptyKey) ? -1 : (int64_t)(unsigned int)key;
+    const int64_t base = (int64_t)blockIdx.x * kPixPerBlock;
+    const int lane = threadIdx.x & 31;
+    int32_t row[kPixUnroll];
+#pragma unroll
+    for (int j = 0; j < kPixUnroll; ++j) {
+        const int64_t p = base + j * kPixThreads + threadIdx.x;
+        row[j] = -1;
+        if (p < total) {
+            if (idmap) {
+                row[j] = idmap[p];
+            } else {
+                const unsigned long long key = keys[p];
+                row[j] = (key == kEmptyKey) ? -1 : (int32_t)(unsigned int)key;
+            }
+        }
     }
-    if (row >= 0 && row < n_x) atomicAdd(fcnt + (p / npix) * n_x + row, 1u);
+    FrameCursor fc(base, npix);
+#pragma unroll
+    for (int j = 0; j < kPixUnroll; ++j) {
+        const int64_t p = base + j * kPixThreads + threadIdx.x;
+        const int64_t f = fc.at(p < total ? p : total - 1);
+        const int n = warp_run_length(((unsigned long long)f << 32) | (unsigned int)row[j], lane);
+        if (n && row[j] >= 0 && row[j] < n_x) atomicAdd(fcnt + f * n_x + row[j], (uint32_t)n);
+    }
 }
 
-__global__ void k_count_reset(const int32_t *__restrict__ idmap, int64_t total, int64_t npix,
-                              uint32_t *__restrict__ fcnt, int64_t n_x)
+__global__ void __launch_bounds__(kPixThreads) k_count_reset(const int32_t *__restrict__ idmap, int64_t total,
+                                                             int64_t npix, uint32_t *__restrict__ fcnt, int64_t n_x)
 {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= total) return;
-    const int32_t row = idmap[p];
-    if (row >= 0 && row < n_x) fcnt[(p / npix) * n_x + row] = 0u;
+    const int64_t base = (int64_t)blockIdx.x * kPixPerBlock;
+    const int lane = threadIdx.x & 31;
+    int32_t row[kPixUnroll];
+#pragma unroll
+    for (int j = 0; j < kPixUnroll; ++j) {
+        const int64_t p = base + j * kPixThreads + threadIdx.x;
+        row[j] = p < total ? idmap[p] : -1;
+    }
+    FrameCursor fc(base, npix);
+#pragma unroll
+    for (int j = 0; j < kPixUnroll; ++j) {
+        const int64_t p = base + j * kPixThreads + threadIdx.x;
+        const int64_t f = fc.at(p < total ? p : total - 1);
+        const int n = warp_run_length(((unsigned long long)f << 32) | (unsigned int)row[j], lane);
+        if (n && row[j] >= 0 && row[j] < n_x) fcnt[f * n_x + row[j]] = 0u;
+    }
 }
 
 // Visible-area pre-pass of the texel steps (Sec. 3.1; a_t read as the most
-// pixels a triangle is visible on in one frame).  One thread per pixel of a
-// batch's z-buffers: the winning triangle's per-frame count + 1, and the key
-// re-armed for the next batch.
-__global__ void k_area_count(unsigned long long *__restrict__ keys, int64_t total, int64_t npix,
-                             uint32_t *__restrict__ fcnt, int64_t F)
+// pixels a triangle is visible on in one frame).  kPixUnroll pixels of a
+// batch's z-buffers per thread: the winning triangle's per-frame count grows
+// by its pixels (one atomic per run within a warp), and the key is re-armed
+// for the next batch.
+__global__ void __launch_bounds__(kPixThreads) k_area_count(unsigned long long *__restrict__ keys, int64_t total,
+                                                            int64_t npix, uint32_t *__restrict__ fcnt, int64_t F)
 {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= total) return;
-    const unsigned long long key = keys[p];
-    if (key == kEmptyKey) return;
-    keys[p] = kEmptyKey;
-    const int64_t f = (int64_t)(unsigned int)key;
-    if (f < F) atomicAdd(fcnt + (p / npix) * F + f, 1u);
+    const int64_t base = (int64_t)blockIdx.x * kPixPerBlock;
+    const int lane = threadIdx.x & 31;
+    unsigned long long key[kPixUnroll];
+#pragma unroll
+    for (int j = 0; j < kPixUnroll; ++j) {
+        const int64_t p = base + j * kPixThreads + threadIdx.x;
+        key[j] = p < total ? keys[p] : kEmptyKey;
+    }
+    FrameCursor fc(base, npix);
+#pragma unroll
+    for (int j = 0; j < kPixUnroll; ++j) {
+        const int64_t p = base + j * kPixThreads + threadIdx.x;
+        if (key[j] != kEmptyKey) keys[p] = kEmptyKey;
+        const int64_t f = fc.at(p < total ? p : total - 1);
+        const int32_t t = key[j] == kEmptyKey ? -1 : (int32_t)(unsigned int)key[j];
+        const int n = warp_run_length(((unsigned long long)f << 32) | (unsigned int)t, lane);
+        if (n && t >= 0 && t < F) atomicAdd(fcnt + f * F + t, (uint32_t)n);
+    }
 }
 
 // One thread per triangle: the largest of its nb per-frame counts folded into
@@ -270,14 +311,16 @@ void launch_count(const int32_t *idmap, const unsigned long long *keys, int64_t 
 {
     const int64_t total = npix * nb;
     if (total <= 0) return;
-    k_count<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(idmap, keys, total, npix, fcnt, n_x);
+    k_count<<<(unsigned)((total + kPixPerBlock - 1) / kPixPerBlock), kPixThreads, 0, s>>>(idmap, keys, total, npix,
+                                                                                           fcnt, n_x);
 }
 
 void launch_area_count(unsigned long long *keys, int64_t npix, int nb, uint32_t *fcnt, int64_t F, cudaStream_t s)
 {
     const int64_t total = npix * nb;
     if (total <= 0) return;
-    k_area_count<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(keys, total, npix, fcnt, F);
+    k_area_count<<<(unsigned)((total + kPixPerBlock - 1) / kPixPerBlock), kPixThreads, 0, s>>>(keys, total, npix,
+                                                                                                fcnt, F);
 }
 
 void launch_area_max(uint32_t *fcnt, int nb, int64_t F, int32_t *area, cudaStream_t s)
@@ -296,7 +339,8 @@ void launch_count_reset(const int32_t *idmap, int64_t npix, int nb, uint32_t *fc
 {
     const int64_t total = npix * nb;
     if (total <= 0) return;
-    k_count_reset<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(idmap, total, npix, fcnt, n_x);
+    k_count_reset<<<(unsigned)((total + kPixPerBlock - 1) / kPixPerBlock), kPixThreads, 0, s>>>(idmap, total, npix,
+                                                                                                 fcnt, n_x);
 }
 
 void launch_scatter(sm_rule rule, sm_dtype dtype, const void *probs, const float *scale, const int32_t *idmap,

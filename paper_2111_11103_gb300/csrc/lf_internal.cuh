@@ -24,6 +24,45 @@ constexpr float kSnapLimit = 536870912.0f;  // |snapped coordinate| <= 2^29 (int
 constexpr float kPMin = 9.31322574615478515625e-10f;  // 2^-30, lower clamp before log
 constexpr unsigned long long kEmptyKey = ~0ull;
 
+// Per-pixel kernels over a batch of frames (resolve, row histograms): a block
+// of kPixThreads threads takes kPixUnroll * kPixThreads consecutive pixels,
+// thread t the pixels base + j * kPixThreads + t (j < kPixUnroll), so every
+// load is one coalesced warp access and kPixUnroll of them are in flight per
+// thread before any result is used (one load per thread leaves a memory-bound
+// kernel far below the HBM bandwidth).
+constexpr int kPixThreads = 256;
+constexpr int kPixUnroll = 8;
+constexpr int64_t kPixPerBlock = (int64_t)kPixThreads * kPixUnroll;
+
+#ifdef __CUDACC__
+// Frame of pixel p for non-decreasing p (no division per pixel).
+struct FrameCursor {
+    int64_t f, end, npix;
+    __device__ __forceinline__ FrameCursor(int64_t p, int64_t npix_) : f(p / npix_), end((p / npix_ + 1) * npix_), npix(npix_) {}
+    __device__ __forceinline__ int64_t at(int64_t p)
+    {
+        while (p >= end) {
+            ++f;
+            end += npix;
+        }
+        return f;
+    }
+};
+
+// Runs of equal keys over a warp's 32 lanes (lane = consecutive pixel): the
+// length of the run that starts at this lane, 0 if the lane does not start
+// one.  Every lane of the warp must call it.
+__device__ __forceinline__ int warp_run_length(unsigned long long key, int lane)
+{
+    const unsigned long long prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const bool start = lane == 0 || key != prev;
+    const unsigned int S = __ballot_sync(0xffffffffu, start);
+    if (!start) return 0;
+    const unsigned int above = lane == 31 ? 0u : S & ~((2u << lane) - 1u);
+    return (above ? __ffs(above) - 1 : 32) - lane;
+}
+#endif
+
 // Error codes latched by kernels (first one wins).
 enum DeviceError : int32_t {
     kErrNone = 0,

@@ -139,56 +139,75 @@ __global__ void __launch_bounds__(256, 4) k_raster_list(const float4 *__restrict
 // beta_k = (float)E_k * iz_k / ((w0 + w1) + w2); u, v are the barycentrics of
 // the vertices after the uv origin; the texel cell (i, j) is
 // (floor(s u), floor(s v)) clamped into the triangle and id_x = T(i + j) + j.
-__global__ void __launch_bounds__(256) k_resolve(unsigned long long *__restrict__ keys, int64_t total, int H, int W,
-                                                 const int32_t *__restrict__ row0,
-                                                 const int32_t *__restrict__ texinfo,
-                                                 const float4 *__restrict__ V, const int4 *__restrict__ faces,
-                                                 const Camera *__restrict__ cams, int frame0,
-                                                 int32_t *__restrict__ idmap, int32_t *__restrict__ idmap2)
+// Row of pixel p of the batch whose nearest surface is triangle f, in texel
+// mode (called per pixel, kept out of line so that the resolve loop stays
+// small).
+__device__ __noinline__ int32_t texel_row(int f, int64_t p, int H, int W, const int32_t *__restrict__ row0,
+                                          const int32_t *__restrict__ texinfo, const float4 *__restrict__ V,
+                                          const int4 *__restrict__ faces, const Camera *__restrict__ cams, int frame0)
 {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= total) return;
-    const unsigned long long key = keys[p];
-    keys[p] = kEmptyKey;
-    int32_t row = -1;
-    if (key != kEmptyKey) {
-        const int f = (int)(unsigned int)key;
-        if (!row0) {
-            row = f;
-        } else {
-            const int info = texinfo[f];
-            const int s = info & 0xFFFF;
-            const int o = info >> 16;
-            int idx = 0;
-            if (s > 1) {
-                const int64_t npix = (int64_t)H * W;
-                const int b = (int)(p / npix);
-                const int64_t q = p - (int64_t)b * npix;
-                const int py = (int)(q / W), px = (int)(q - (int64_t)py * W);
-                const float *A = cams[frame0 + b].a;
-                Tri t;
-                setup_triangle(A, V, faces[f], t);
-                float w[3];
+    const int info = texinfo[f];
+    const int s = info & 0xFFFF;
+    const int o = info >> 16;
+    int idx = 0;
+    if (s > 1) {
+        const int64_t npix = (int64_t)H * W;
+        const int b = (int)(p / npix);
+        const int64_t q = p - (int64_t)b * npix;
+        const int py = (int)(q / W), px = (int)(q - (int64_t)py * W);
+        const float *A = cams[frame0 + b].a;
+        Tri t;
+        setup_triangle(A, V, faces[f], t);
+        float w[3];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) w[k] = fmul(i2f(edge_at(t, k, 256LL * px, 256LL * py)), t.iz[k]);
-                const float num = fadd(fadd(w[0], w[1]), w[2]);
-                float beta[3];
-                beta[0] = fdiv(w[0], num);
-                beta[t.swapped ? 2 : 1] = fdiv(w[1], num);
-                beta[t.swapped ? 1 : 2] = fdiv(w[2], num);
-                const float u = beta[(o + 1) % 3], v = beta[(o + 2) % 3];
-                const float fs = (float)s;
-                int i = (int)floorf(fmul(fs, u));
-                i = min(max(i, 0), s - 1);
-                int j = (int)floorf(fmul(fs, v));
-                j = min(max(j, 0), s - 1 - i);
-                idx = (i + j) * (i + j + 1) / 2 + j;
+        for (int k = 0; k < 3; ++k) w[k] = fmul(i2f(edge_at(t, k, 256LL * px, 256LL * py)), t.iz[k]);
+        const float num = fadd(fadd(w[0], w[1]), w[2]);
+        float beta[3];
+        beta[0] = fdiv(w[0], num);
+        beta[t.swapped ? 2 : 1] = fdiv(w[1], num);
+        beta[t.swapped ? 1 : 2] = fdiv(w[2], num);
+        const float u = beta[(o + 1) % 3], v = beta[(o + 2) % 3];
+        const float fs = (float)s;
+        int i = (int)floorf(fmul(fs, u));
+        i = min(max(i, 0), s - 1);
+        int j = (int)floorf(fmul(fs, v));
+        j = min(max(j, 0), s - 1 - i);
+        idx = (i + j) * (i + j + 1) / 2 + j;
+    }
+    return row0[f] + idx;
+}
+
+// kPixUnroll pixels per thread (see kPixThreads): the keys are loaded first,
+// then resolved; keys left empty by the raster are not written again.
+template <bool TEXEL>
+__global__ void __launch_bounds__(kPixThreads) k_resolve(unsigned long long *__restrict__ keys, int64_t total, int H,
+                                                         int W, const int32_t *__restrict__ row0,
+                                                         const int32_t *__restrict__ texinfo,
+                                                         const float4 *__restrict__ V, const int4 *__restrict__ faces,
+                                                         const Camera *__restrict__ cams, int frame0,
+                                                         int32_t *__restrict__ idmap, int32_t *__restrict__ idmap2)
+{
+    const int64_t base = (int64_t)blockIdx.x * kPixPerBlock;
+    unsigned long long key[kPixUnroll];
+#pragma unroll
+    for (int j = 0; j < kPixUnroll; ++j) {
+        const int64_t p = base + j * kPixThreads + threadIdx.x;
+        key[j] = p < total ? keys[p] : kEmptyKey;
+    }
+#pragma unroll
+    for (int j = 0; j < kPixUnroll; ++j) {
+        const int64_t p = base + j * kPixThreads + threadIdx.x;
+        if (p < total) {
+            int32_t row = -1;
+            if (key[j] != kEmptyKey) {
+                keys[p] = kEmptyKey;
+                const int f = (int)(unsigned int)key[j];
+                row = TEXEL ? texel_row(f, p, H, W, row0, texinfo, V, faces, cams, frame0) : f;
             }
-            row = row0[f] + idx;
+            idmap[p] = row;
+            if (idmap2) idmap2[p] = row;
         }
     }
-    idmap[p] = row;
-    if (idmap2) idmap2[p] = row;
 }
 
 // ---- raster for the allocation-free entry point (sm_render_rows_noalloc) ----
@@ -273,8 +292,8 @@ cudaError_t launch_render_rows_noalloc(const float *V, int64_t nV, const int32_t
     for (int i = 0; i < N; ++i) {
         if (F > 0) k_raster_flat<<<(unsigned)((F + 255) / 256), 256, 0, s>>>(V, nV, faces, F, cams + i, H, W, keys);
         // resolve in face mode (row = triangle); re-arms the z-buffer
-        k_resolve<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(keys, npix, H, W, nullptr, nullptr, nullptr, nullptr,
-                                                                  cams, i, idmap + (int64_t)i * npix, nullptr);
+        k_resolve<false><<<(unsigned)((npix + kPixPerBlock - 1) / kPixPerBlock), kPixThreads, 0, s>>>(
+            keys, npix, H, W, nullptr, nullptr, nullptr, nullptr, cams, i, idmap + (int64_t)i * npix, nullptr);
     }
     return cudaGetLastError();
 }
@@ -312,8 +331,13 @@ void launch_resolve(unsigned long long *keys, int nb, int H, int W, const int32_
 {
     const int64_t total = (int64_t)nb * H * W;
     if (total <= 0) return;
-    k_resolve<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(keys, total, H, W, row0, texinfo, V, faces, cams,
-                                                                frame0, idmap, idmap2);
+    const unsigned g = (unsigned)((total + kPixPerBlock - 1) / kPixPerBlock);
+    if (row0)
+        k_resolve<true><<<g, kPixThreads, 0, s>>>(keys, total, H, W, row0, texinfo, V, faces, cams, frame0, idmap,
+                                                    idmap2);
+    else
+        k_resolve<false><<<g, kPixThreads, 0, s>>>(keys, total, H, W, row0, texinfo, V, faces, cams, frame0, idmap,
+                                                     idmap2);
 }
 
 }  // namespace lf
