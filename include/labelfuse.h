@@ -316,9 +316,10 @@ sm_status sm_fuse_frames_weighted(sm_mesh *m, const void *d_probs, sm_dtype dtyp
  * ln c; top-2 margin p(1) - p(2); distance to the nearest image border /
  * (min(H, W) / 2).  Background pixels get zeros.
  * Network: 5 -> 32 -> 32 -> 1, ReLU, linear output o: the log-odds that the
- * observation agrees with the fused label.  Fusion weight w = max(0, o), the
- * log-odds weight of an independent two-way vote (Nitzan and Paroush, 1982)
- * clipped at zero.  SM_CONF_PARAMS float32
+ * observation agrees with the fused label.  Fusion weight w = max(o, 1/16),
+ * the log-odds weight of an independent two-way vote (Nitzan and Paroush,
+ * 1982) clipped at a small floor (a row whose every observation is predicted
+ * below even odds keeps the plain vote).  SM_CONF_PARAMS float32
  * parameters in the order W1 (32 x 5, row = output), b1, W2 (32 x 32), b2,
  * w3 (32), b3, used rounded to bfloat16 with float32 accumulation.
  * Training: mean binary cross-entropy of sigmoid(o) against targets
@@ -339,7 +340,7 @@ sm_status sm_conf_features(sm_mesh *m, const void *d_probs, sm_dtype dtype, cons
 /* Learned confidence inference in one pass (an extension of the weighted
  * rules of Sec. 3.2.2; the paper has no counterpart): renders the N frames
  * (as sm_fuse_frames) and, per pixel, computes the five features of
- * sm_conf_features and the network's weight w = max(0, o) of
+ * sm_conf_features and the network's weight w = max(o, 1/16) of
  * sm_conf_forward, without writing the features out.  The 32 x 32 hidden
  * layer runs on the tensor cores with its inputs (the first layer's ReLU
  * activations) rounded to bfloat16 and float32 accumulation, so w differs
@@ -381,7 +382,7 @@ sm_status sm_fuse_frames_confident(sm_mesh *m, const void *d_probs, sm_dtype dty
 sm_status sm_conf_targets(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
                           const int32_t *d_rows, int64_t n_pixels, float *d_target_out, void *stream);
 
-/* Inference: d_w_out[i] = max(0, MLP(d_feat[i])) for n observations.
+/* Inference: d_w_out[i] = max(MLP(d_feat[i]), 1/16) for n observations.
  * d_params SM_CONF_PARAMS float32, d_feat n x SM_CONF_FEATURES float32,
  * d_w_out n float32, all device; n == 0 is a no-op.
  * Errors: SM_ERR_INVALID_ARG (n < 0, NULL pointer), SM_ERR_CUDA. */

@@ -16,8 +16,10 @@ triangle is t (all computed from the oracle's own raster):
 Network 5 -> 32 -> 32 -> 1 with ReLU hidden layers and a linear output o,
 read as the log-odds that the observation agrees with the fused label
 (sigmoid(o) is that probability).  The fusion weight of the observation is
-w = max(0, o): the log-odds of agreement, clipped at zero so that an
-observation no better than a coin toss gets no say.  For independent voters
+w = max(o, 1/16): the log-odds of agreement, clipped at a small floor so that
+an observation no better than a coin toss has almost no say, while a row
+whose every observation is predicted below even odds still takes the plain
+vote of its observations instead of a tie.  For independent voters
 choosing between two answers, weighing each vote by the log-odds of its
 competence is the optimal decision rule (Nitzan and Paroush, Int. Econ. Rev.
 23, 1982); the weighted log-sum of Eq. w-mul is such a vote.  Parameters are one flat
@@ -32,6 +34,7 @@ from __future__ import annotations
 import numpy as np
 
 N_FEAT, HID = 5, 32
+W_FLOOR = 0.0625  # 1/16: the least fusion weight of an observation
 N_PARAMS = HID * N_FEAT + HID + HID * HID + HID + HID + 1
 P_MIN = 2.0 ** -30
 
@@ -56,7 +59,7 @@ def unpack(params):
 
 
 def forward(params, X, rounding: bool = True, act_bf16: bool = False):
-    """o and the fusion weight w = max(0, o) for observations X (n x 5), with the parameters
+    """o and the fusion weight w = max(o, 1/16) for observations X (n x 5), with the parameters
     rounded to bfloat16 (rounding=False: as given, for finite differences);
     also returns the hidden activations for backward.  act_bf16: the first
     layer's activations are rounded to bfloat16 before the hidden layer, the
@@ -70,7 +73,7 @@ def forward(params, X, rounding: bool = True, act_bf16: bool = False):
     z2 = h1 @ W2.T + b2
     h2 = np.maximum(z2, 0.0)
     o = h2 @ w3 + b3[0]
-    w = np.maximum(o, 0.0)
+    w = np.maximum(o, W_FLOOR)
     return o, w, (X, z1, h1, z2, h2)
 
 

@@ -10,9 +10,10 @@
 //  * k_conf_forward: 5 -> 32 -> 32 -> 1 MLP, ReLU, the parameters rounded to
 //    bfloat16, float32 accumulation.  Its output o is the log-odds that the
 //    observation agrees with the fused label (trained with the binary
-//    cross-entropy of sigmoid(o)); the fusion weight is w = max(0, o), the
-//    optimal weight of an independent two-way vote (Nitzan and Paroush,
-//    1982) clipped at zero.
+//    cross-entropy of sigmoid(o)); the fusion weight is w = max(o, 1/16),
+//    the optimal weight of an independent two-way vote (Nitzan and Paroush,
+//    1982) clipped at a small floor, so that a row whose every observation
+//    is predicted below even odds keeps the plain vote instead of a tie.
 //  * k_conf_grad + k_conf_update: one step of gradient descent on the mean
 //    binary cross-entropy; each block reduces its observations' gradients in
 //    shared memory (fixed order), converts the sums to 64-bit fixed point
@@ -27,6 +28,8 @@
 #include "lf_internal.cuh"
 
 namespace lf {
+
+constexpr float kWeightFloor = 0.0625f;  // 1/16: the least fusion weight of an observation
 namespace {
 
 constexpr int kF = SM_CONF_FEATURES;  // 5
@@ -56,7 +59,7 @@ __global__ void __launch_bounds__(256)
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= total) return;
     const int64_t npix = (int64_t)H * W;
-    const int b = (int)(p / npix);
+    const int b = (int)frame_of(p, npix);
     const int64_t q = p - (int64_t)b * npix;
     const int y = (int)(q / W), x = (int)(q - (int64_t)y * W);
     float *out = feat + p * kF;
@@ -166,7 +169,7 @@ __device__ __forceinline__ bool pixel_features(unsigned long long key, int64_t p
                                                const float *__restrict__ scale, int c, float (&x)[kF])
 {
     const int64_t npix = (int64_t)H * W;
-    const int b = (int)(p / npix);
+    const int b = (int)frame_of(p, npix);
     const int64_t q = p - (int64_t)b * npix;
     const int y = (int)(q / W), xx = (int)(q - (int64_t)y * W);
     const int64_t f = (int64_t)(unsigned int)key;
@@ -239,7 +242,7 @@ __device__ __forceinline__ bool pixel_features(unsigned long long key, int64_t p
 }
 
 // One thread per pixel of a rasterised batch, one warp per 32 pixels: the
-// features, then w = max(0, network) with the bfloat16 parameters; the
+// features, then w = max(network, 1/16) with the bfloat16 parameters; the
 // first layer in float32, the 32 x 32 hidden layer as 16 tensor-core tiles
 // per warp (activations rounded to bfloat16, float32 accumulation), the
 // output layer in float32.  Writes w (0 for background) and, when rows_out
@@ -342,7 +345,7 @@ __global__ void __launch_bounds__(256)
         const float o0 = __shfl_sync(0xffffffffu, o[0][0], src), o1 = __shfl_sync(0xffffffffu, o[0][1], src);
         const float o2 = __shfl_sync(0xffffffffu, o[1][0], src), o3 = __shfl_sync(0xffffffffu, o[1][1], src);
         const float ol = mt == 0 ? (r < 8 ? o0 : o1) : (r < 8 ? o2 : o3);
-        if (p < total) w_out[p] = fg ? fmaxf(ol, 0.0f) : 0.0f;
+        if (p < total) w_out[p] = fg ? fmaxf(ol, kWeightFloor) : 0.0f;
         __syncwarp();  // the activations are rewritten by the next pixels
     }
 }
@@ -358,7 +361,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int k = 0; k < kF; ++k) x[k] = feat[i * kF + k];
     const float o = mlp_forward(s, x, z1, z2);
-    w[i] = fmaxf(o, 0.0f);
+    w[i] = fmaxf(o, kWeightFloor);
 }
 
 constexpr int kObs = 128;  // observations per block in the gradient kernel

@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256)
     }
     float w = 1.0f;
     if (wpix) w = wpix[p];
-    else if (fcnt) w = image_weight(alpha, fcnt[(p / npix) * n_x + row]);
+    else if (fcnt) w = image_weight(alpha, fcnt[frame_of(p, npix) * n_x + row]);
     const float sc = (DT == SM_F32) ? 1.0f : scale[p];
     float *a = acc + (int64_t)row * c;
     const int64_t base = p * c;

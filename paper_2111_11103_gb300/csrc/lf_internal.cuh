@@ -35,6 +35,14 @@ constexpr int kPixUnroll = 8;
 constexpr int64_t kPixPerBlock = (int64_t)kPixThreads * kPixUnroll;
 
 #ifdef __CUDACC__
+// Frame of pixel p of a batch: a 32-bit division where both fit (several
+// times cheaper than the 64-bit one).
+__device__ __forceinline__ int64_t frame_of(int64_t p, int64_t npix)
+{
+    if (((uint64_t)p | (uint64_t)npix) <= 0xffffffffull) return (int64_t)((uint32_t)p / (uint32_t)npix);
+    return p / npix;
+}
+
 // Frame of pixel p for non-decreasing p (no division per pixel).
 struct FrameCursor {
     int64_t f, end, npix;

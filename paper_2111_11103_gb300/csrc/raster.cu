@@ -152,7 +152,7 @@ __device__ __noinline__ int32_t texel_row(int f, int64_t p, int H, int W, const 
     int idx = 0;
     if (s > 1) {
         const int64_t npix = (int64_t)H * W;
-        const int b = (int)(p / npix);
+        const int b = (int)frame_of(p, npix);
         const int64_t q = p - (int64_t)b * npix;
         const int py = (int)(q / W), px = (int)(q - (int64_t)py * W);
         const float *A = cams[frame0 + b].a;

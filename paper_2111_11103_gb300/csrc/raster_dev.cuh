@@ -141,8 +141,8 @@ __device__ __forceinline__ void raster_box(const Tri &t, int x0, int x1, int y0,
         const int bb = (k + 1) % 3, cc = (k + 2) % 3;
         const T dx = (T)(t.x[cc] - t.x[bb]), dy = (T)(t.y[cc] - t.y[bb]);
         tl[k] = top_left(t, k);
-        // stepped with the fill-rule bias folded in: inside iff every biased value > 0
-        e_row[k] = dx * ((T)256 * y0 - t.y[bb]) - dy * ((T)256 * x0 - t.x[bb]) + (T)tl[k];
+        // inside iff every value + its fill-rule bias > 0, i.e. value >= 1 - bias
+        e_row[k] = dx * ((T)256 * y0 - t.y[bb]) - dy * ((T)256 * x0 - t.x[bb]);
         sx[k] = (T)-256 * dy;
         sy[k] = (T)256 * dx;
     }
@@ -153,17 +153,18 @@ __device__ __forceinline__ void raster_box(const Tri &t, int x0, int x1, int y0,
     // near plane.  One division per triangle instead of one per pixel.
     const float farea = i2f(t.area2);
     const float rcp = fdiv(1.0f, farea);
+    const T th0 = (T)(1 - tl[0]), th1 = (T)(1 - tl[1]), th2 = (T)(1 - tl[2]);
     for (int py = y0; py <= y1; ++py) {
         T e0 = e_row[0], e1 = e_row[1], e2 = e_row[2];
         unsigned long long *row_keys = frame_keys + (int64_t)py * W;
         bool in_run = false;  // the covered samples of a row form one run (a convex face)
         for (int px = x0; px <= x1; ++px) {
-            const bool inside = e0 > 0 && e1 > 0 && e2 > 0;
+            const bool inside = e0 >= th0 && e1 >= th1 && e2 >= th2;
             if (!inside && in_run) break;
             if (inside) {
                 in_run = true;
-                const float num = fadd(fadd(fmul(to_float(e0 - tl[0]), t.iz[0]), fmul(to_float(e1 - tl[1]), t.iz[1])),
-                                       fmul(to_float(e2 - tl[2]), t.iz[2]));
+                const float num = fadd(fadd(fmul(to_float(e0), t.iz[0]), fmul(to_float(e1), t.iz[1])),
+                                       fmul(to_float(e2), t.iz[2]));
                 const float q = fmul(num, rcp);
                 const float inv_z = __fmaf_rn(__fmaf_rn(-farea, q, num), rcp, q);
                 const unsigned long long key = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(inv_z)) << 32) | fid;

@@ -120,7 +120,7 @@ __device__ __forceinline__ void pixel_info(const ScatterArgs &a, int64_t p, int 
         atomicCAS(a.err, 0, (int32_t)kErrRowRange);
         row = -1;
     }
-    if (IMAGE && row >= 0) w = a.wpix ? a.wpix[p] : image_weight(a.alpha, a.fcnt[(p / a.npix) * a.n_x + row]);
+    if (IMAGE && row >= 0) w = a.wpix ? a.wpix[p] : image_weight(a.alpha, a.fcnt[frame_of(p, a.npix) * a.n_x + row]);
     if (DT != SM_F32) sc = sscale ? sscale[i] : a.scale[p];
 }
 

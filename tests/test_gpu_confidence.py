@@ -166,7 +166,7 @@ def test_fused_inference_matches_oracle(ora, dev, medium):
     (sm_conf_forward) within 1.6e-2.  Against the oracle the bound is per
     observation: an activation computed in float32 on the GPU and in binary64
     in the oracle may round to neighbouring bfloat16 values (at most 2^-6 |h1|
-    apart), which moves o, and so w = max(0, o), by at most
+    apart), which moves o, and so w = max(o, 1/16), by at most
     sum_i 2^-6 |h1_i| (|W2|^T |w3|)_i; almost every observation matches far
     closer."""
     from paper_2111_11103_gb300 import labelfuse as lf
@@ -251,7 +251,7 @@ def test_one_pass_confident_fusion(ora, dev, medium, mode, rule):
     idm = idm_b.cpu().numpy()
     assert np.array_equal(idm, rows_o)
     w = w_b.cpu().numpy()
-    assert np.all(w[idm < 0] == 0.0) and np.all(w[idm >= 0] >= 0.0)
+    assert np.all(w[idm < 0] == 0.0) and np.all(w[idm >= 0] >= 0.0625)
     A, cnt = ora.accumulate(rule, rows_o, probs.cpu().numpy(), mesh.n_x, weights=w.astype(np.float64))
     assert np.array_equal(cnt_b.cpu().numpy().astype(np.int64), cnt)
     assert_acc_close(acc_b.cpu().numpy(), A)
@@ -262,8 +262,8 @@ def test_learned_confidence_gains_over_plain_fusion(dev):
     "structured" recipe: confidently wrong more often at grazing angles, far
     away and near the image border).  The network is trained on agreement
     with the plain fused labels; the render-back pixel accuracy against the
-    synthetic ground truth of the weighted fusion (weights max(0, o), the
-    clipped log-odds of agreement) must beat plain fusion by half a point,
+    synthetic ground truth of the weighted fusion (weights max(o, 1/16), the
+    floored log-odds of agreement) must beat plain fusion by half a point,
     for each of three training seeds (initial parameters and minibatches)."""
     from paper_2111_11103_gb300 import confidence as conf
     from paper_2111_11103_gb300 import labelfuse as lf

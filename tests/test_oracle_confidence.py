@@ -34,16 +34,16 @@ def test_forward_closed_forms():
     p[-1] = 0.75  # b3: o = 0.75 for every input, the weight is the log-odds itself
     o, w, _ = cf.forward(p, np.ones((3, cf.N_FEAT)))
     assert np.array_equal(o, [0.75] * 3) and np.array_equal(w, [0.75] * 3)
-    p[-1] = -0.75  # below even odds: no weight
+    p[-1] = -0.75  # below even odds: the floor of 1/16
     o, w, _ = cf.forward(p, np.ones((3, cf.N_FEAT)))
-    assert np.array_equal(o, [-0.75] * 3) and np.array_equal(w, [0.0] * 3)
+    assert np.array_equal(o, [-0.75] * 3) and np.array_equal(w, [0.0625] * 3)
     # the loss at o = b3 is the BCE of the constant probability sigmoid(b3)
     y = np.array([1.0, 0.0, 1.0])
     l, g = cf.loss_and_grad(p, np.ones((3, cf.N_FEAT)), y)
     q = 1 / (1 + np.exp(0.75))
     assert abs(l - np.mean(-(y * np.log(q) + (1 - y) * np.log(1 - q)))) <= 1e-15
     assert abs(g[-1] - np.mean(q - y)) <= 1e-15  # d loss / d b3
-    # one path through: o = relu(relu(x0)) = x0 for x0 >= 0, 0 for x0 < 0
+    # one path through: o = relu(relu(x0)) = x0 for x0 >= 0, 0 for x0 < 0; w = max(o, 1/16)
     W1, b1, W2, b2, w3, b3 = cf.unpack(np.zeros(cf.N_PARAMS))
     q = np.zeros(cf.N_PARAMS)
     q[0] = 1.0                                   # W1[0, 0]
@@ -51,7 +51,7 @@ def test_forward_closed_forms():
     q[cf.N_PARAMS - 1 - cf.HID] = 1.0            # w3[0]
     X = np.array([[0.5, 9, 9, 9, 9], [-2.0, 1, 1, 1, 1]])
     o, w, _ = cf.forward(q, X)
-    assert np.array_equal(o, [0.5, 0.0])
+    assert np.array_equal(o, [0.5, 0.0]) and np.array_equal(w, [0.5, 0.0625])
 
 
 def test_bf16_rounding_matches_torch():

@@ -87,8 +87,9 @@ MUTANTS = {
                                        "j->T + 16 * (int64_t)i, j->H, j->W, j->idmaps_out, NULL, NULL) < 0)"),
     # learned confidence
     "conf_sigmoid_sign": (PY, "q = 1.0 / (1.0 + np.exp(-o))", "q = 1.0 / (1.0 + np.exp(o))"),
-    "conf_weight_unclipped": (PY, "w = np.maximum(o, 0.0)", "w = np.abs(o)"),
-    "conf_weight_is_probability": (PY, "w = np.maximum(o, 0.0)", "w = 1.0 / (1.0 + np.exp(-o))"),
+    "conf_weight_unclipped": (PY, "w = np.maximum(o, W_FLOOR)", "w = np.abs(o)"),
+    "conf_weight_is_probability": (PY, "w = np.maximum(o, W_FLOOR)", "w = 1.0 / (1.0 + np.exp(-o))"),
+    "conf_weight_floor_zero": (PY, "w = np.maximum(o, W_FLOOR)", "w = np.maximum(o, 0.0)"),
     "conf_loss_sign": (PY, "loss = np.mean(np.logaddexp(0.0, o) - y * o)", "loss = np.mean(np.logaddexp(0.0, o) + y * o)"),
     "conf_depth_scale": (PY, "1.0 / np.where(invz > 0, invz, 1.0), 0.0) / 4.0", "1.0 / np.where(invz > 0, invz, 1.0), 0.0) / 2.0"),
     "conf_cos_not_absolute": (PY, "cos = np.abs((n * ray).sum(1))", "cos = ((n * ray).sum(1))"),
