@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the BF16 / FP8 storage forms")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay timing")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default frames per launch")
-    ap.add_argument("--batch", type=int, default=128,
+    ap.add_argument("--batch", type=int, default=512,
                     help="frames per launch of the two-stream path (a multiple of 4), the fastest measured with the "
                          "autotuner on this workload; 0 runs the autotuner (launch path and shape) instead")
     ap.add_argument("--scenes", type=int, default=0,
@@ -69,6 +69,9 @@ def parse():
                     help="learned-confidence form: the 4M-triangle apartment, --frames frames (5000 by default), "
                          "4 texel steps, plain against confidence-weighted fusion")
     ap.add_argument("--train-frames", type=int, default=400, help="--learned: frames whose observations train the net")
+    ap.add_argument("--infer", action="store_true",
+                    help="the confidence inference alone (sm_conf_weights) on the paper-shaped room's first --frames "
+                         "frames (20 by default), FP8 storage, a seeded network")
     ap.add_argument("--coarse", action="store_true",
                     help="pixel accuracy of the fused render-back for meshes of 500k to 5k triangles, with texel "
                          "steps from gamma = 0 and 0.2 (a synthetic analogue of the paper's mesh-simplification study)")
@@ -908,6 +911,50 @@ def run_coarse(args):
                       "rule": "logsum", "weight": "image", "results": results}), flush=True)
 
 
+def run_infer(args):
+    """The learned-confidence inference alone: sm_conf_weights (raster, the
+    five features, the network with its hidden layer on the tensor cores,
+    the weights) over the paper-shaped room's first --frames frames, whose
+    "structured" predictions are stored as FP8 E4M3 with a per-pixel scale,
+    with a seeded network.  Three untimed calls, then one timed with CUDA
+    events; prints the time per frame."""
+    from paper_2111_11103_gb300 import labelfuse as lf
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    N = args.frames
+    scene = sg.paper_room(target_faces=args.faces)
+    cams = sg.random_walk_poses(N)
+    H, W, c = cams.H, cams.W, scene.n_classes
+    q = torch.empty((N, H, W, c), dtype=torch.float8_e4m3fn, device=dev)
+    scale = torch.empty((N, H, W), dtype=torch.float32, device=dev)
+    for a in range(0, N, 25):
+        b = min(N, a + 25)
+        p = sg.predictions(scene, cams, "structured", frames=range(a, b), device=dev)
+        q[a:b], scale[a:b] = quantise(p, "fp8_e4m3")
+        del p
+    K = torch.as_tensor(cams.K, device=dev)
+    T = torch.as_tensor(cams.cam_to_world.reshape(N, 16), device=dev)
+    m = lf.sm_mesh_upload(torch.as_tensor(scene.vertices, device=dev), torch.as_tensor(scene.faces, device=dev),
+                          None, c, "logsum", "pixel")
+    g = torch.Generator().manual_seed(2111)
+    params = (torch.randn(lf.SM_CONF_PARAMS, generator=g) * 0.2).to(dev)
+    w = torch.empty((N, H, W), device=dev)
+    rows = torch.empty((N, H, W), dtype=torch.int32, device=dev)
+    for _ in range(3):
+        lf.sm_conf_weights(m, q, "fp8_e4m3", scale, K, T, N, H, W, params, w, rows)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    lf.sm_conf_weights(m, q, "fp8_e4m3", scale, K, T, N, H, W, params, w, rows)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    lf.sm_check(m)
+    lf.sm_mesh_free(m)
+    print(json.dumps({"study": "confidence inference (sm_conf_weights, raster included)", "frames": N, "H": H,
+                      "W": W, "classes": c, "storage": "fp8_e4m3 + per-pixel scale",
+                      "us_per_frame": 1e3 * e0.elapsed_time(e1) / N}), flush=True)
+
+
 def main():
     args = parse()
     launch_ranks(args)
@@ -924,6 +971,11 @@ def main():
         return
     if args.scenes:
         run_scenes(args)
+        return
+    if args.infer:
+        if args.frames == 1000:
+            args.frames = 20
+        run_infer(args)
         return
     if args.hires and args.frames == 1000:
         args.frames = 250  # the ring of the high-resolution workload (50 GB of FP32 predictions)

@@ -218,7 +218,7 @@ sm_status sm_texel_res_from_gamma(sm_mesh *m, const sm_intrinsics *d_K, const do
  * later calls on this mesh with frames of H x W pixels raster and scatter
  * that many frames per launch pair, as if sm_autotune_batch had chosen it.
  * frames = 0 restores the default (about 48 MB of z-buffer per launch).
- *   frames   0, or a multiple of 4 in [4, 128].
+ *   frames   0, or a multiple of 4 in [4, 1024].
  * Errors: SM_ERR_INVALID_ARG. */
 sm_status sm_set_launch_frames(sm_mesh *m, int32_t H, int32_t W, int32_t frames);
 
@@ -279,8 +279,9 @@ sm_status sm_set_queue_shape(sm_mesh *m, int32_t H, int32_t W, int32_t frames_pe
 /* Autotuner of the launch path and shape (the paper has no counterpart: a
  * throughput setting of this implementation).  Tunes the frames per launch
  * of the two-stream path: fuses the given frames twice per candidate batch
- * size (multiples of 4 up to 128 frames, both z-buffer slots within 1 GB; the
- * first pass sizes the scratch buffers) and times the second on `stream`
+ * size (4 to 1,024 frames spaced by about a quarter, whole launches of at
+ * most N frames, both z-buffer slots within 8 GB; the first pass sizes the
+ * scratch buffers) and times the second on `stream`
  * with CUDA events.  For a mesh that the work-queue path applies to (see
  * sm_set_queue_shape) it then tunes the queue's shape one parameter at a
  * time from its defaults (frames per batch in {8, 16, 24, 32, 48, 64},
@@ -291,7 +292,9 @@ sm_status sm_set_queue_shape(sm_mesh *m, int32_t H, int32_t W, int32_t frames_pe
  * accumulators (P and counts are zero afterwards).  *best_out, if not NULL,
  * receives the chosen frames per launch (or per batch of the queue).
  *   d_probs ...  N >= 4 frames as for sm_fuse_frames (a representative
- *                sample: 2-4 x 128 frames is plenty).
+ *                sample; a launch size is timed only on whole launches,
+ *                so sizes near N are timed without the overlap of
+ *                consecutive launches).
  * Errors: SM_ERR_INVALID_ARG, SM_ERR_OOM, SM_ERR_CUDA. */
 sm_status sm_autotune_batch(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
                             const sm_intrinsics *d_K, const double *d_cam_to_world, int32_t N, int32_t H, int32_t W,

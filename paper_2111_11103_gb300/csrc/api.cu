@@ -121,6 +121,10 @@ size_t dtype_size(sm_dtype d) { return d == SM_F32 ? 4 : (d == SM_BF16 ? 2 : 1);
 // the streaming scatter launches long enough to fill the GPU, which matters
 // more than keeping both z-buffer slots in L2; the per-frame row histograms
 // of the image weights stay within ~512 MB.
+// Most frames per launch pair: each pair costs about 36 us of pipeline fill
+// and drain, so longer launches pay even when a batch's z-buffers leave L2.
+constexpr int kMaxLaunchFrames = 1024;
+
 int batch_frames(const sm_mesh *m, int64_t npix, int N, bool tuned = true)
 {
     int64_t B = (tuned && m->tuned_B > 0 && m->tuned_npix == npix) ? m->tuned_B : (int64_t)(48u << 20) / (npix * 8);
@@ -129,7 +133,7 @@ int batch_frames(const sm_mesh *m, int64_t npix, int N, bool tuned = true)
         if (Bi < B) B = Bi;
     }
     if (B < 1) B = 1;
-    if (B > 128) B = 128;
+    if (B > kMaxLaunchFrames) B = kMaxLaunchFrames;
     // multiples of 4 frames keep every batch's probability, scale and row-map
     // base 16-byte aligned for the bulk copies (4 H W c bytes is a multiple
     // of 16 for c % 4 == 0)
@@ -811,8 +815,12 @@ sm_status sm_autotune_batch(sm_mesh *m, const void *d_probs, sm_dtype dtype, con
         m->use_queue = false;
         const int saved_B = m->tuned_B;
         const int64_t saved_npix = m->tuned_npix;
-        // candidates: multiples of 4 frames whose two z-buffer slots stay within 1 GB
-        for (int B = 4; B <= 128 && B <= N && (int64_t)B * npix * 16 <= (1024ll << 20); B += 4) {
+        // candidates: multiples of 4 frames, spaced by about a quarter, whose two
+        // z-buffer slots stay within 8 GB
+        static const int kCandidates[] = {4,   8,   12,  16,  20,  24,  32,  40,  48,  64,  80,
+                                          96,  128, 160, 192, 256, 320, 384, 512, 640, 768, 1024};
+        for (const int B : kCandidates) {
+            if (B > kMaxLaunchFrames || B > N || (int64_t)B * npix * 16 > (8192ll << 20)) break;
             m->tuned_B = B;
             m->tuned_npix = npix;
             float ms = 0.0f;
@@ -891,8 +899,9 @@ sm_status sm_set_launch_frames(sm_mesh *m, int32_t H, int32_t W, int32_t frames)
     if (!m) return fail(SM_ERR_INVALID_ARG, "mesh is NULL");
     sm_status st = check_image(0, H, W);
     if (st != SM_OK) return st;
-    if (frames < 0 || frames > 128 || (frames & 3) != 0)
-        return fail(SM_ERR_INVALID_ARG, "frames per launch %d: a multiple of 4 in [4, 128], or 0", frames);
+    if (frames < 0 || frames > kMaxLaunchFrames || (frames & 3) != 0)
+        return fail(SM_ERR_INVALID_ARG, "frames per launch %d: a multiple of 4 in [4, %d], or 0", frames,
+                    kMaxLaunchFrames);
     m->tuned_B = frames;
     m->tuned_npix = frames ? (int64_t)H * W : 0;
     return SM_OK;
