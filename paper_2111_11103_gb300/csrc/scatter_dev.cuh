@@ -362,6 +362,15 @@ __device__ __forceinline__ void warp_tile_q(const ScatterArgs &a, const uint8_t 
     const int start = active ? (32 * g) / G : 0;
     const int len = active ? (32 * (g + 1)) / G - start : 0;
     const uint8_t *pb = base + (px0 + start) * pstride;
+    // register slot m of the lane holds quad qd[m]; odd groups take their
+    // quads in the other order, so that the groups of a quarter-warp (whose
+    // pixels lie 5-6 pixels apart) spread their 16-byte words over more
+    // shared-memory banks: for c = 40 a warp tile's loads take 64 instead of
+    // 84 quarter-warp passes (FP32), 44 instead of 64 (BF16), 22 instead of
+    // 44 (FP8)
+    int qd[QPL];
+#pragma unroll
+    for (int m = 0; m < QPL; ++m) qd[m] = q + LPP * ((m + g) % QPL);
 
     // the lane's quads of every step's pixel (a stage holds the whole tile;
     // the ragged tile in global memory is read only where a pixel exists)
@@ -375,8 +384,13 @@ __device__ __forceinline__ void warp_tile_q(const ScatterArgs &a, const uint8_t 
 #pragma unroll
         for (int m = 0; m < QPL; ++m) {
             v[u][m] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (SMEM || rk >= 0) {
-                v[u][m] = load_quad<DT, SMEM>(pb + u * pstride, 4 * (q + LPP * m));
+            // FP32 from the stage: only steps inside the group's range are read
+            // (an idle lane would take shared-memory bank cycles from its
+            // quarter-warp; the values of the other steps are never stored).
+            // BF16 / FP8 read every step: there the predicate costs more in
+            // branching around the decode than it saves (measured)
+            if (SMEM ? (DT != SM_F32 || (active && u < len)) : rk >= 0) {
+                v[u][m] = load_quad<DT, SMEM>(pb + u * pstride, 4 * qd[m]);
                 if (SCALED && PROD) v[u][m] = scale4(v[u][m], sv[u]);
             }
         }
@@ -446,17 +460,25 @@ __device__ __forceinline__ void warp_tile_q(const ScatterArgs &a, const uint8_t 
                 s[m].w = st ? c.w : s[m].w * c.w;
             }
         } else {
-            // maximum and first arg max of the whole pixel: each lane scans its
-            // quads in class order, then the group combines (lowest class on ties)
+            // maximum and first arg max of the whole pixel: each lane takes the
+            // lowest class among its own maxima (its slots need not be in class
+            // order), then the group combines (lowest class on ties); max-sum
+            // needs the maximum only
             float mx = -INFINITY;
             int am = 0x7fffffff;
+            auto take = [&](float val, int idx) {
+                if (val > mx || (RULE == SM_RULE_VOTE && val == mx && idx < am)) {
+                    mx = val;
+                    am = idx;
+                }
+            };
 #pragma unroll
             for (int m = 0; m < QPL; ++m) {
-                const int j = q + LPP * m;
-                if (v[u][m].x > mx) { mx = v[u][m].x; am = 4 * j; }
-                if (v[u][m].y > mx) { mx = v[u][m].y; am = 4 * j + 1; }
-                if (v[u][m].z > mx) { mx = v[u][m].z; am = 4 * j + 2; }
-                if (v[u][m].w > mx) { mx = v[u][m].w; am = 4 * j + 3; }
+                const int j = qd[m];
+                take(v[u][m].x, 4 * j);
+                take(v[u][m].y, 4 * j + 1);
+                take(v[u][m].z, 4 * j + 2);
+                take(v[u][m].w, 4 * j + 3);
             }
             float gm = mx;
             int ga = am;
@@ -472,7 +494,7 @@ __device__ __forceinline__ void warp_tile_q(const ScatterArgs &a, const uint8_t 
             const float gv = SCALED ? __fmul_rn(gm, sv[u]) : gm;  // the kept maximum, scaled once
 #pragma unroll
             for (int m = 0; m < QPL; ++m) {
-                const int j = q + LPP * m;
+                const int j = qd[m];
                 float4 c;
                 if (RULE == SM_RULE_MAXSUM) {
                     c = make_float4(v[u][m].x == gm ? gv : 0.f, v[u][m].y == gm ? gv : 0.f,
@@ -489,7 +511,7 @@ __device__ __forceinline__ void warp_tile_q(const ScatterArgs &a, const uint8_t 
         }
         if (inf & 64) {
 #pragma unroll
-            for (int m = 0; m < QPL; ++m) queue[(inf & 31) * Q + q + LPP * m] = s[m];
+            for (int m = 0; m < QPL; ++m) queue[(inf & 31) * Q + qd[m]] = s[m];
         }
     }
     __syncwarp();
