@@ -9,6 +9,8 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>  // driver types of the virtual-memory calls (entry points fetched at run time)
+
 #include "lf_internal.cuh"
 
 namespace {
@@ -98,6 +100,129 @@ cudaError_t device_alloc(void **p, size_t bytes)
     return cudaMalloc(p, bytes);
 }
 
+// Compressible device memory (the GPU's compute data compression) for the
+// z-buffer.  Between two uses of a slot its keys are re-armed to all-ones and
+// written back to DRAM, and the next raster's atomics read them back: two
+// transfers of constant data per pixel and use, which the memory system
+// stores compressed in compressible memory.  The allocation goes through the
+// driver's virtual-memory calls (cuMemCreate with generic compression, then
+// reserve, map and grant access), fetched from the runtime at run time so
+// that the library has no link-time dependency on the driver library.  Where
+// the device or driver offers no compression (or LABELFUSE_ZBUF_COMPRESSION=0),
+// the z-buffer is ordinary stream-ordered device memory.
+struct VmmApi {
+    decltype(&cuDeviceGet) device_get = nullptr;
+    decltype(&cuDeviceGetAttribute) device_attr = nullptr;
+    decltype(&cuMemGetAllocationGranularity) granularity = nullptr;
+    decltype(&cuMemCreate) create = nullptr;
+    decltype(&cuMemGetAllocationPropertiesFromHandle) props = nullptr;
+    decltype(&cuMemAddressReserve) reserve = nullptr;
+    decltype(&cuMemMap) map = nullptr;
+    decltype(&cuMemSetAccess) access = nullptr;
+    decltype(&cuMemUnmap) unmap = nullptr;
+    decltype(&cuMemAddressFree) addr_free = nullptr;
+    decltype(&cuMemRelease) release = nullptr;
+    bool ok = false;
+};
+
+const VmmApi &vmm_api()
+{
+    static const VmmApi api = [] {
+        VmmApi a;
+        auto get = [](const char *name, void **fn) {
+            cudaDriverEntryPointQueryResult q{};
+            if (cudaGetDriverEntryPointByVersion(name, fn, CUDA_VERSION, cudaEnableDefault, &q) != cudaSuccess ||
+                q != cudaDriverEntryPointSuccess) {
+                cudaGetLastError();
+                *fn = nullptr;
+                return false;
+            }
+            return *fn != nullptr;
+        };
+        a.ok = get("cuDeviceGet", (void **)&a.device_get) && get("cuDeviceGetAttribute", (void **)&a.device_attr) &&
+               get("cuMemGetAllocationGranularity", (void **)&a.granularity) &&
+               get("cuMemCreate", (void **)&a.create) &&
+               get("cuMemGetAllocationPropertiesFromHandle", (void **)&a.props) &&
+               get("cuMemAddressReserve", (void **)&a.reserve) && get("cuMemMap", (void **)&a.map) &&
+               get("cuMemSetAccess", (void **)&a.access) && get("cuMemUnmap", (void **)&a.unmap) &&
+               get("cuMemAddressFree", (void **)&a.addr_free) && get("cuMemRelease", (void **)&a.release);
+        return a;
+    }();
+    return api;
+}
+
+bool zbuf_compression_wanted()
+{
+    const char *v = getenv("LABELFUSE_ZBUF_COMPRESSION");
+    return !(v && v[0] == '0');
+}
+
+// Maps `bytes` (rounded up to the allocation granularity, returned in
+// *mapped) of compressible memory on device `dev`; false, with nothing held,
+// if compression is unavailable or not granted.
+bool compressible_alloc(int dev, size_t bytes, void **ptr, size_t *mapped, unsigned long long *handle)
+{
+    const VmmApi &api = vmm_api();
+    if (!api.ok || !zbuf_compression_wanted() || injected_alloc_failure()) return false;
+    CUdevice d;
+    int supported = 0;
+    if (api.device_get(&d, dev) != CUDA_SUCCESS ||
+        api.device_attr(&supported, CU_DEVICE_ATTRIBUTE_GENERIC_COMPRESSION_SUPPORTED, d) != CUDA_SUCCESS ||
+        !supported)
+        return false;
+    CUmemAllocationProp prop;
+    memset(&prop, 0, sizeof prop);
+    prop.type = CU_MEM_ALLOCATION_TYPE_PINNED;
+    prop.location.type = CU_MEM_LOCATION_TYPE_DEVICE;
+    prop.location.id = d;
+    prop.allocFlags.compressionType = CU_MEM_ALLOCATION_COMP_GENERIC;
+    size_t gran = 0;
+    if (api.granularity(&gran, &prop, CU_MEM_ALLOC_GRANULARITY_RECOMMENDED) != CUDA_SUCCESS || gran == 0) return false;
+    const size_t size = (bytes + gran - 1) / gran * gran;
+    CUmemGenericAllocationHandle h;
+    if (api.create(&h, size, &prop, 0) != CUDA_SUCCESS) return false;
+    CUmemAllocationProp got;
+    memset(&got, 0, sizeof got);
+    if (api.props(&got, h) != CUDA_SUCCESS || got.allocFlags.compressionType != CU_MEM_ALLOCATION_COMP_GENERIC) {
+        api.release(h);
+        return false;
+    }
+    CUdeviceptr va = 0;
+    if (api.reserve(&va, size, gran, 0, 0) != CUDA_SUCCESS) {
+        api.release(h);
+        return false;
+    }
+    CUmemAccessDesc acc;
+    memset(&acc, 0, sizeof acc);
+    acc.location = prop.location;
+    acc.flags = CU_MEM_ACCESS_FLAGS_PROT_READWRITE;
+    if (api.map(va, size, 0, h, 0) != CUDA_SUCCESS) {
+        api.addr_free(va, size);
+        api.release(h);
+        return false;
+    }
+    if (api.access(va, size, &acc, 1) != CUDA_SUCCESS) {
+        api.unmap(va, size);
+        api.addr_free(va, size);
+        api.release(h);
+        return false;
+    }
+    *ptr = reinterpret_cast<void *>(va);
+    *mapped = size;
+    *handle = (unsigned long long)h;
+    return true;
+}
+
+// Releases a block of compressible_alloc; no work on the device may still use it.
+void compressible_free(void *ptr, size_t mapped, unsigned long long handle)
+{
+    const VmmApi &api = vmm_api();
+    const CUdeviceptr va = reinterpret_cast<CUdeviceptr>(ptr);
+    api.unmap(va, mapped);
+    api.addr_free(va, mapped);
+    api.release((CUmemGenericAllocationHandle)handle);
+}
+
 template <class T>
 sm_status grow(T **buf, int64_t *cap, int64_t need, cudaStream_t s, int fill, const char *what)
 {
@@ -111,6 +236,48 @@ sm_status grow(T **buf, int64_t *cap, int64_t need, cudaStream_t s, int fill, co
     if (fill >= 0) LF_CUDA(cudaMemsetAsync(p, fill, (size_t)need * sizeof(T), s), what);
     *buf = static_cast<T *>(p);
     *cap = need;
+    return SM_OK;
+}
+
+// z-buffer room for `need` keys, all empty, in compressible memory where the
+// device offers it (compressible_alloc).  A compressible block is released
+// only once the device is idle; inside a stream capture, where that wait is
+// not allowed, the old block is kept until the mesh is freed and the new one
+// is stream-ordered device memory.
+sm_status grow_keys(sm_mesh *m, int64_t need, cudaStream_t s)
+{
+    if (m->keys_cap >= need) return SM_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    LF_CUDA(cudaStreamIsCapturing(s, &cs), "z-buffer");
+    const bool capturing = cs != cudaStreamCaptureStatusNone;
+    if (m->keys) {
+        if (!m->keys_vmm) {
+            LF_CUDA(cudaFreeAsync(m->keys, s), "z-buffer");
+        } else if (capturing) {
+            m->keys_retired.push_back({m->keys, m->keys_mapped, m->keys_handle});
+        } else {
+            LF_CUDA(cudaDeviceSynchronize(), "z-buffer");
+            compressible_free(m->keys, m->keys_mapped, m->keys_handle);
+        }
+    }
+    m->keys = nullptr;
+    m->keys_cap = 0;
+    m->keys_vmm = false;
+    const size_t bytes = (size_t)need * sizeof(unsigned long long);
+    void *p = nullptr;
+    size_t mapped = 0;
+    unsigned long long h = 0;
+    if (!capturing && compressible_alloc(m->device, bytes, &p, &mapped, &h)) {
+        m->keys_vmm = true;
+        m->keys_mapped = mapped;
+        m->keys_handle = h;
+    } else {
+        if (injected_alloc_failure()) return cuda_fail(cudaErrorMemoryAllocation, "z-buffer");
+        LF_CUDA(cudaMallocAsync(&p, bytes, s), "z-buffer");
+    }
+    m->keys = static_cast<unsigned long long *>(p);
+    m->keys_cap = need;
+    LF_CUDA(cudaMemsetAsync(p, 0xFF, bytes, s), "z-buffer");
     return SM_OK;
 }
 
@@ -197,7 +364,7 @@ sm_status prepare_frames(sm_mesh *m, const sm_intrinsics *d_K, const double *d_T
     sm_status st;
     if ((st = grow(&m->cams, &m->cams_cap, N, s, -1, "camera buffer")) != SM_OK) return st;
     // (two slots for the stream path: raster of batch b+1 beside the scatter of batch b)
-    if ((st = grow(&m->keys, &m->keys_cap, slots * slot_stride(B, npix), s, 0xFF, "z-buffer")) != SM_OK) return st;
+    if ((st = grow_keys(m, slots * slot_stride(B, npix), s)) != SM_OK) return st;
     if (need_idbuf && (st = grow(&m->idbuf, &m->idbuf_cap, (int64_t)B * npix, s, -1, "row-map buffer")) != SM_OK)
         return st;
     {
@@ -1220,10 +1387,12 @@ sm_status sm_mesh_free(sm_mesh *m)
         DeviceGuard g(m->device);
         cudaDeviceSynchronize();
         void *bufs[] = {m->verts, m->faces,  m->row0,   m->texinfo, m->acc,     m->cnt,    m->labels8,
-                        m->err,   m->cams,   m->keys,   m->idbuf,   m->wbuf,   m->fcnt,    m->bounds, m->hstage,
-                        m->hids,  m->hlabels, m->hcam,  m->clist,   m->ccount, m->area,    m->qctr};
+                        m->err,   m->cams,   m->keys_vmm ? nullptr : m->keys, m->idbuf, m->wbuf, m->fcnt,
+                        m->bounds, m->hstage, m->hids, m->hlabels, m->hcam, m->clist, m->ccount, m->area, m->qctr};
         for (void *b : bufs)
             if (b) cudaFree(b);
+        if (m->keys && m->keys_vmm) compressible_free(m->keys, m->keys_mapped, m->keys_handle);
+        for (const auto &r : m->keys_retired) compressible_free(r.p, r.mapped, r.handle);
         if (m->rstream) cudaStreamDestroy(m->rstream);
         for (cudaStream_t cs : m->cstream)
             if (cs) cudaStreamDestroy(cs);

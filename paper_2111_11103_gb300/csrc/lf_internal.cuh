@@ -257,6 +257,17 @@ struct sm_mesh {
     int64_t cams_cap = 0;
     unsigned long long *keys = nullptr;
     int64_t keys_cap = 0;
+    // the keys in compressible memory (api.cu grow_keys): its mapping, and
+    // blocks replaced during a stream capture, released with the mesh
+    bool keys_vmm = false;
+    size_t keys_mapped = 0;
+    unsigned long long keys_handle = 0;
+    struct VmmBlock {
+        void *p;
+        size_t mapped;
+        unsigned long long handle;
+    };
+    std::vector<VmmBlock> keys_retired;
     int32_t *clist = nullptr;   // visible-cluster lists of one raster batch
     int64_t clist_cap = 0;
     uint32_t *ccount = nullptr;  // their lengths
