@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the BF16 / FP8 storage forms")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay timing")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default frames per launch")
+    ap.add_argument("--plain-buffers", action="store_true",
+                    help="row maps and label images in torch memory instead of the library's compressible memory")
     ap.add_argument("--batch", type=int, default=512,
                     help="frames per launch of the two-stream path (a multiple of 4), the fastest measured with the "
                          "autotuner on this workload; 0 runs the autotuner (launch path and shape) instead")
@@ -350,8 +352,17 @@ def run_ours(args):
     V = torch.as_tensor(scene.vertices, device=dev)
     Fc = torch.as_tensor(scene.faces, device=dev)
     m = lf.sm_mesh_upload(V, Fc, None, c, args.rule, args.weight)
-    idmaps = torch.empty((n_loc, H, W), dtype=torch.int32, device=dev)
-    images = torch.empty((n_loc, H, W), dtype=torch.uint8, device=dev)
+    # the row maps (kept from fusion to render-back) and label images in the
+    # library's compressible device memory: runs of equal values, which the
+    # memory system stores compressed (--plain-buffers: ordinary torch memory)
+    if args.plain_buffers:
+        idmaps = torch.empty((n_loc, H, W), dtype=torch.int32, device=dev)
+        images = torch.empty((n_loc, H, W), dtype=torch.uint8, device=dev)
+        buffers = "plain"
+    else:
+        idmaps = lf.device_empty((n_loc, H, W), torch.int32, dev)
+        images = lf.device_empty((n_loc, H, W), torch.uint8, dev)
+        buffers = "compressible" if idmaps.lf_compressed else "plain (no compression offered)"
     stream = torch.cuda.current_stream(dev)
 
     def barrier():
@@ -469,6 +480,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(args, int(scene.faces.shape[0]), N, ring, H, W, c, ws),
             "l2": l2_note(probs.numel() * probs.element_size()),
+            "row_map_and_label_buffers": buffers,
             "frames_per_launch": tuned_B, "frame_range": [fa, fb],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": dom,

@@ -417,6 +417,26 @@ sm_status sm_conf_train_step(float *d_params, const float *d_feat, const float *
 sm_status sm_host_alloc(uint64_t bytes, void **out);
 sm_status sm_host_free(void *p);
 
+/* Device memory for the buffers the path writes and later reads in runs of
+ * equal or similar values -- the row maps kept between sm_fuse_frames and
+ * sm_render_idmap, and label images -- in compressible memory (the paper has
+ * no counterpart: this is plumbing of the memory system).  With
+ * SM_DEVICE_COMPRESSIBLE, and where the GPU and driver offer compute data
+ * compression, the memory system keeps such data compressed in DRAM, so
+ * writing and reading it moves fewer bytes; otherwise (or with flags 0) the
+ * block is ordinary device memory.  *out receives `bytes` > 0 bytes on
+ * `device`, uninitialised, owned by the caller until sm_device_free(*out);
+ * *compressed_out (may be NULL) is 1 if the block is compressible.  Any
+ * kernel, copy or memset may use the block.  Both calls are synchronous;
+ * sm_device_free first waits for the block's device to be idle (no work may
+ * still use the block), so neither belongs inside a stream capture.
+ * Errors: SM_ERR_INVALID_ARG (NULL out, bytes == 0, unknown flags, no such
+ * device, a pointer that sm_device_alloc did not return), SM_ERR_OOM,
+ * SM_ERR_CUDA. */
+#define SM_DEVICE_COMPRESSIBLE 1
+sm_status sm_device_alloc(int32_t device, uint64_t bytes, int32_t flags, void **out, int32_t *compressed_out);
+sm_status sm_device_free(void *p);
+
 /* Zeroes the accumulators and observation counts (enqueued on `stream`).
  * Errors: SM_ERR_INVALID_ARG (NULL mesh), SM_ERR_CUDA. */
 sm_status sm_reset(sm_mesh *m, void *stream);

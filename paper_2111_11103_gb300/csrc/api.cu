@@ -6,7 +6,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include <cuda.h>  // driver types of the virtual-memory calls (entry points fetched at run time)
@@ -239,45 +241,47 @@ sm_status grow(T **buf, int64_t *cap, int64_t need, cudaStream_t s, int fill, co
     return SM_OK;
 }
 
-// z-buffer room for `need` keys, all empty, in compressible memory where the
-// device offers it (compressible_alloc).  A compressible block is released
-// only once the device is idle; inside a stream capture, where that wait is
-// not allowed, the old block is kept until the mesh is freed and the new one
-// is stream-ordered device memory.
-sm_status grow_keys(sm_mesh *m, int64_t need, cudaStream_t s)
+// Room for `need` elements in *buf, in compressible memory where the device
+// offers it (compressible_alloc), else stream-ordered device memory; fill >= 0
+// sets every byte.  The z-buffer (re-armed to all-ones between uses) and the
+// host path's row maps and label images (runs of equal values) compress.  A
+// compressible block is released only once the device is idle; inside a
+// stream capture, where that wait is not allowed, the old block is kept until
+// the mesh is freed and the new one is stream-ordered memory.
+template <typename T>
+sm_status grow_compressible(sm_mesh *m, T **buf, int64_t *cap, sm_mesh::VmmBlock *blk, int64_t need, cudaStream_t s,
+                            int fill, const char *what)
 {
-    if (m->keys_cap >= need) return SM_OK;
+    if (*cap >= need) return SM_OK;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    LF_CUDA(cudaStreamIsCapturing(s, &cs), "z-buffer");
+    LF_CUDA(cudaStreamIsCapturing(s, &cs), what);
     const bool capturing = cs != cudaStreamCaptureStatusNone;
-    if (m->keys) {
-        if (!m->keys_vmm) {
-            LF_CUDA(cudaFreeAsync(m->keys, s), "z-buffer");
+    if (*buf) {
+        if (!blk->p) {
+            LF_CUDA(cudaFreeAsync(*buf, s), what);
         } else if (capturing) {
-            m->keys_retired.push_back({m->keys, m->keys_mapped, m->keys_handle});
+            m->retired.push_back(*blk);
         } else {
-            LF_CUDA(cudaDeviceSynchronize(), "z-buffer");
-            compressible_free(m->keys, m->keys_mapped, m->keys_handle);
+            LF_CUDA(cudaDeviceSynchronize(), what);
+            compressible_free(blk->p, blk->mapped, blk->handle);
         }
     }
-    m->keys = nullptr;
-    m->keys_cap = 0;
-    m->keys_vmm = false;
-    const size_t bytes = (size_t)need * sizeof(unsigned long long);
+    *buf = nullptr;
+    *cap = 0;
+    *blk = sm_mesh::VmmBlock{};
+    const size_t bytes = (size_t)need * sizeof(T);
     void *p = nullptr;
     size_t mapped = 0;
     unsigned long long h = 0;
     if (!capturing && compressible_alloc(m->device, bytes, &p, &mapped, &h)) {
-        m->keys_vmm = true;
-        m->keys_mapped = mapped;
-        m->keys_handle = h;
+        *blk = sm_mesh::VmmBlock{p, mapped, h};
     } else {
-        if (injected_alloc_failure()) return cuda_fail(cudaErrorMemoryAllocation, "z-buffer");
-        LF_CUDA(cudaMallocAsync(&p, bytes, s), "z-buffer");
+        if (injected_alloc_failure()) return cuda_fail(cudaErrorMemoryAllocation, what);
+        LF_CUDA(cudaMallocAsync(&p, bytes, s), what);
     }
-    m->keys = static_cast<unsigned long long *>(p);
-    m->keys_cap = need;
-    LF_CUDA(cudaMemsetAsync(p, 0xFF, bytes, s), "z-buffer");
+    *buf = static_cast<T *>(p);
+    *cap = need;
+    if (fill >= 0) LF_CUDA(cudaMemsetAsync(p, fill, bytes, s), what);
     return SM_OK;
 }
 
@@ -364,7 +368,9 @@ sm_status prepare_frames(sm_mesh *m, const sm_intrinsics *d_K, const double *d_T
     sm_status st;
     if ((st = grow(&m->cams, &m->cams_cap, N, s, -1, "camera buffer")) != SM_OK) return st;
     // (two slots for the stream path: raster of batch b+1 beside the scatter of batch b)
-    if ((st = grow_keys(m, slots * slot_stride(B, npix), s)) != SM_OK) return st;
+    if ((st = grow_compressible(m, &m->keys, &m->keys_cap, &m->keys_blk, slots * slot_stride(B, npix), s, 0xFF,
+                                "z-buffer")) != SM_OK)
+        return st;
     if (need_idbuf && (st = grow(&m->idbuf, &m->idbuf_cap, (int64_t)B * npix, s, -1, "row-map buffer")) != SM_OK)
         return st;
     {
@@ -1236,6 +1242,74 @@ sm_status sm_host_free(void *p)
     return e == cudaSuccess ? SM_OK : cuda_fail(e, "cudaFreeHost");
 }
 
+namespace {
+// Blocks of sm_device_alloc: compressible mappings need their size and handle
+// to be released, plain blocks only their device.
+struct DeviceBlock {
+    int device;
+    sm_mesh::VmmBlock vmm;
+};
+std::mutex g_blocks_mu;
+std::unordered_map<void *, DeviceBlock> g_blocks;
+}  // namespace
+
+sm_status sm_device_alloc(int32_t device, uint64_t bytes, int32_t flags, void **out, int32_t *compressed_out)
+{
+    if (compressed_out) *compressed_out = 0;
+    if (out) *out = nullptr;
+    if (!out || bytes == 0) return fail(SM_ERR_INVALID_ARG, "sm_device_alloc: NULL out or zero bytes");
+    if (flags & ~SM_DEVICE_COMPRESSIBLE) return fail(SM_ERR_INVALID_ARG, "sm_device_alloc: unknown flags 0x%x", flags);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        ndev = 0;
+    }
+    if (device < 0 || device >= ndev) return fail(SM_ERR_INVALID_ARG, "sm_device_alloc: no device %d", device);
+    DeviceGuard g(device);
+    DeviceBlock blk{device, {}};
+    void *p = nullptr;
+    size_t mapped = 0;
+    unsigned long long h = 0;
+    if ((flags & SM_DEVICE_COMPRESSIBLE) && compressible_alloc(device, (size_t)bytes, &p, &mapped, &h)) {
+        blk.vmm = sm_mesh::VmmBlock{p, mapped, h};
+        if (compressed_out) *compressed_out = 1;
+    } else {
+        const cudaError_t e = device_alloc(&p, (size_t)bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_fail(e, "sm_device_alloc");
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_blocks_mu);
+        g_blocks[p] = blk;
+    }
+    *out = p;
+    return SM_OK;
+}
+
+sm_status sm_device_free(void *p)
+{
+    if (!p) return SM_OK;
+    DeviceBlock blk;
+    {
+        std::lock_guard<std::mutex> lk(g_blocks_mu);
+        auto it = g_blocks.find(p);
+        if (it == g_blocks.end()) return fail(SM_ERR_INVALID_ARG, "sm_device_free: not a block of sm_device_alloc");
+        blk = it->second;
+        g_blocks.erase(it);
+    }
+    DeviceGuard g(blk.device);
+    if (!blk.vmm.p) {
+        const cudaError_t e = cudaFree(p);
+        return e == cudaSuccess ? SM_OK : cuda_fail(e, "sm_device_free");
+    }
+    // a mapping is released only once no work on the device can still use it
+    const cudaError_t e = cudaDeviceSynchronize();
+    compressible_free(blk.vmm.p, blk.vmm.mapped, blk.vmm.handle);
+    return e == cudaSuccess ? SM_OK : cuda_fail(e, "sm_device_free");
+}
+
 sm_status sm_fuse_render_host(sm_mesh *m, const void *h_probs, sm_dtype dtype, const float *h_scale,
                               const sm_intrinsics *h_K, const double *h_cam_to_world, int32_t N, int32_t H, int32_t W,
                               uint8_t *h_labels_out, void *stream)
@@ -1257,8 +1331,12 @@ sm_status sm_fuse_render_host(sm_mesh *m, const void *h_probs, sm_dtype dtype, c
     const size_t probs_slot = ((size_t)B * frame_bytes + 255) & ~(size_t)255;
     const size_t slot_bytes = probs_slot + (dtype != SM_F32 ? (((size_t)B * npix * 4 + 255) & ~(size_t)255) : 0);
     if ((st = grow(&m->hstage, &m->hstage_cap, 2 * (int64_t)slot_bytes, s, -1, "host staging")) != SM_OK) return st;
-    if ((st = grow(&m->hids, &m->hids_cap, (int64_t)N * npix, s, -1, "row maps")) != SM_OK) return st;
-    if ((st = grow(&m->hlabels, &m->hlabels_cap, (int64_t)N * npix, s, -1, "label images")) != SM_OK) return st;
+    if ((st = grow_compressible(m, &m->hids, &m->hids_cap, &m->hids_blk, (int64_t)N * npix, s, -1, "row maps")) !=
+        SM_OK)
+        return st;
+    if ((st = grow_compressible(m, &m->hlabels, &m->hlabels_cap, &m->hlabels_blk, (int64_t)N * npix, s, -1,
+                                "label images")) != SM_OK)
+        return st;
     if ((st = grow(&m->hcam, &m->hcam_cap, 20 * (int64_t)N, s, -1, "cameras")) != SM_OK) return st;
     sm_intrinsics *d_K = reinterpret_cast<sm_intrinsics *>(m->hcam);
     double *d_T = m->hcam + 4 * (int64_t)N;
@@ -1386,13 +1464,15 @@ sm_status sm_mesh_free(sm_mesh *m)
     {
         DeviceGuard g(m->device);
         cudaDeviceSynchronize();
-        void *bufs[] = {m->verts, m->faces,  m->row0,   m->texinfo, m->acc,     m->cnt,    m->labels8,
-                        m->err,   m->cams,   m->keys_vmm ? nullptr : m->keys, m->idbuf, m->wbuf, m->fcnt,
-                        m->bounds, m->hstage, m->hids, m->hlabels, m->hcam, m->clist, m->ccount, m->area, m->qctr};
+        void *bufs[] = {m->verts, m->faces, m->row0, m->texinfo, m->acc, m->cnt, m->labels8, m->err, m->cams,
+                        m->keys_blk.p ? nullptr : m->keys, m->idbuf, m->wbuf, m->fcnt, m->bounds, m->hstage,
+                        m->hids_blk.p ? nullptr : m->hids, m->hlabels_blk.p ? nullptr : m->hlabels, m->hcam,
+                        m->clist, m->ccount, m->area, m->qctr};
         for (void *b : bufs)
             if (b) cudaFree(b);
-        if (m->keys && m->keys_vmm) compressible_free(m->keys, m->keys_mapped, m->keys_handle);
-        for (const auto &r : m->keys_retired) compressible_free(r.p, r.mapped, r.handle);
+        for (const sm_mesh::VmmBlock &b : {m->keys_blk, m->hids_blk, m->hlabels_blk})
+            if (b.p) compressible_free(b.p, b.mapped, b.handle);
+        for (const auto &r : m->retired) compressible_free(r.p, r.mapped, r.handle);
         if (m->rstream) cudaStreamDestroy(m->rstream);
         for (cudaStream_t cs : m->cstream)
             if (cs) cudaStreamDestroy(cs);

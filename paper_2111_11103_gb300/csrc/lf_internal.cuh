@@ -257,17 +257,14 @@ struct sm_mesh {
     int64_t cams_cap = 0;
     unsigned long long *keys = nullptr;
     int64_t keys_cap = 0;
-    // the keys in compressible memory (api.cu grow_keys): its mapping, and
-    // blocks replaced during a stream capture, released with the mesh
-    bool keys_vmm = false;
-    size_t keys_mapped = 0;
-    unsigned long long keys_handle = 0;
+    // a buffer in compressible memory (api.cu grow_compressible): its mapping
+    // (p == nullptr: the buffer is stream-ordered device memory)
     struct VmmBlock {
-        void *p;
-        size_t mapped;
-        unsigned long long handle;
+        void *p = nullptr;
+        size_t mapped = 0;
+        unsigned long long handle = 0;
     };
-    std::vector<VmmBlock> keys_retired;
+    VmmBlock keys_blk;
     int32_t *clist = nullptr;   // visible-cluster lists of one raster batch
     int64_t clist_cap = 0;
     uint32_t *ccount = nullptr;  // their lengths
@@ -298,6 +295,8 @@ struct sm_mesh {
     int64_t hids_cap = 0;
     uint8_t *hlabels = nullptr;  // label images of all frames of the call
     int64_t hlabels_cap = 0;
+    VmmBlock hids_blk, hlabels_blk;
+    std::vector<VmmBlock> retired;  // compressible blocks replaced during a stream capture
     double *hcam = nullptr;      // N x (4 + 16) camera parameters
     int64_t hcam_cap = 0;
 

@@ -30,11 +30,12 @@ SM_KERNEL = {"project": 0, "raster": 1, "resolve": 2, "count": 3, "scatter": 4, 
              "queue": 7, "conf": 8}
 SM_OK = 0
 SM_ERR_INVALID_ARG = 1
+SM_ERR_INTERNAL = 6
 SM_MAX_CLASSES = 254
 SYMBOLS = ["sm_mesh_upload", "sm_fuse_frames", "sm_normalise", "sm_render_labels", "sm_render_idmap", "sm_reset",
            "sm_read_state", "sm_load_state", "sm_check", "sm_num_rows", "sm_num_classes", "sm_mesh_free",
            "sm_status_string", "sm_last_error", "sm_profile_enable", "sm_profile_read", "sm_render_rows_noalloc",
-           "sm_fuse_render_host", "sm_host_alloc", "sm_host_free", "sm_set_weight_mix", "sm_texel_res_from_gamma",
+           "sm_fuse_render_host", "sm_host_alloc", "sm_host_free", "sm_device_alloc", "sm_device_free", "sm_set_weight_mix", "sm_texel_res_from_gamma",
            "sm_autotune_batch", "sm_fuse_frames_weighted", "sm_conf_features", "sm_conf_targets", "sm_conf_forward",
            "sm_conf_train_step", "sm_set_queue_shape", "sm_fuse_scenes", "sm_conf_weights",
            "sm_set_launch_frames", "sm_fuse_frames_confident"]
@@ -42,6 +43,7 @@ SM_CONF_FEATURES = 5
 SM_CONF_PARAMS = 1281
 SM_NOALLOC_MAX_PIXELS = 1572864
 SM_NOALLOC_MAX_FRAMES = 1024
+SM_DEVICE_COMPRESSIBLE = 1
 
 
 class SceneFrames(ctypes.Structure):
@@ -86,6 +88,8 @@ def lib() -> ctypes.CDLL:
             "sm_profile_read": [P, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)],
             "sm_host_alloc": [ctypes.c_uint64, ctypes.POINTER(P)],
             "sm_host_free": [P],
+            "sm_device_alloc": [i32, ctypes.c_uint64, i32, ctypes.POINTER(P), ctypes.POINTER(i32)],
+            "sm_device_free": [P],
             "sm_set_weight_mix": [P, ctypes.c_float],
             "sm_texel_res_from_gamma": [P, P, P, i32, i32, i32, ctypes.c_float, P, P, P],
             "sm_autotune_batch": [P, P, i32, P, P, P, i32, i32, i32, ctypes.POINTER(i32), P],
@@ -362,6 +366,65 @@ def pinned_empty(shape, dtype):
     buf = (ctypes.c_uint8 * nbytes).from_address(block.ptr)
     buf._block = block  # the block lives as long as the buffer, which the tensor keeps
     return torch.frombuffer(buf, dtype=torch.uint8).view(dtype)[: math.prod(shape)].view(shape)
+
+
+def sm_device_alloc(device: int, nbytes: int, compressible: bool = True) -> tuple[int, bool]:
+    """(pointer, whether the block is compressible) of nbytes of device memory."""
+    p = ctypes.c_void_p()
+    comp = ctypes.c_int32(0)
+    _check(lib().sm_device_alloc(int(device), int(nbytes), SM_DEVICE_COMPRESSIBLE if compressible else 0,
+                                 ctypes.byref(p), ctypes.byref(comp)))
+    return p.value, bool(comp.value)
+
+
+def sm_device_free(p: int):
+    _check(lib().sm_device_free(p))
+
+
+_TYPESTR = {"torch.int32": "<i4", "torch.uint8": "|u1", "torch.float32": "<f4", "torch.int64": "<i8",
+            "torch.int8": "|i1", "torch.bfloat16": "<V2", "torch.float16": "<f2"}
+
+
+class _DeviceBlock:
+    """Owns one sm_device_alloc block and exposes it as a CUDA array; the
+    tensor made from it keeps it alive, and the block is freed with the last
+    reference (sm_device_free waits for the device to be idle)."""
+
+    def __init__(self, device: int, shape, dtype, compressible: bool):
+        import math
+        import torch
+        self.ptr = None
+        n = math.prod(shape)
+        esize = torch.empty((), dtype=dtype).element_size()
+        self.ptr, self.compressed = sm_device_alloc(device, max(1, n) * esize, compressible)
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": _TYPESTR[str(dtype)],
+                                         "data": (self.ptr, False), "version": 2, "strides": None}
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            lib().sm_device_free(self.ptr)
+            self.ptr = None
+
+
+def device_empty(shape, dtype, device=None, compressible: bool = True):
+    """Uninitialised CUDA tensor in memory from sm_device_alloc: compressible
+    where the GPU offers it (for row maps and label images, whose runs of equal
+    values the memory system stores compressed).  The memory is released with
+    the tensor."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    if dev.type != "cuda":
+        raise ValueError("device_empty: a CUDA device is required")
+    if str(dtype) not in _TYPESTR or dtype == torch.bfloat16:
+        raise ValueError(f"device_empty: unsupported dtype {dtype}")
+    shape = tuple(int(d) for d in shape)
+    block = _DeviceBlock(dev.index if dev.index is not None else torch.cuda.current_device(), shape, dtype,
+                         compressible)
+    t = torch.as_tensor(block, device=dev)
+    if t.data_ptr() != block.ptr:
+        raise LabelFuseError(SM_ERR_INTERNAL, "device_empty: the tensor does not view the block")
+    t.lf_compressed = block.compressed  # whether the memory is compressible
+    return t
 
 
 def sm_reset(mesh: int, stream=None):

@@ -42,10 +42,12 @@ def to_dev(scene, cams, texel_res=None, dev="cuda"):
 
 
 def run_gpu(scene, cams, probs, rule, weight, texel_res=None, dtype="f32", scale=None, reraster=True,
-            n_classes=None, alpha=None, queue_shape=None):
+            n_classes=None, alpha=None, queue_shape=None, buffers="torch"):
     """Fuses, normalises and renders through the C ABI.  queue_shape: None
     (the library's choice), 0 (the two-stream path) or (frames per batch,
-    lookahead, raster rounds, scatter tiles) of the work-queue path."""
+    lookahead, raster rounds, scatter tiles) of the work-queue path.
+    buffers: "torch" or "compressible" (row maps and label images in the
+    library's sm_device_alloc memory)."""
     from paper_2111_11103_gb300 import labelfuse as lf
     dev = probs.device
     N, H, W = cams.K.shape[0], cams.H, cams.W
@@ -58,7 +60,10 @@ def run_gpu(scene, cams, probs, rule, weight, texel_res=None, dtype="f32", scale
         if queue_shape is not None:
             lf.sm_set_queue_shape(m, H, W, *((0,) if queue_shape == 0 else tuple(queue_shape)))
         n_x = lf.sm_num_rows(m)
-        idm = torch.full((N, H, W), -7, dtype=torch.int32, device=dev)
+        if buffers == "compressible":
+            idm = lf.device_empty((N, H, W), torch.int32, dev).fill_(-7)
+        else:
+            idm = torch.full((N, H, W), -7, dtype=torch.int32, device=dev)
         lf.sm_fuse_frames(m, probs, dtype, scale, K, T, N, H, W, idm)
         acc = torch.empty((max(n_x, 1), c), dtype=torch.float32, device=dev)
         cnt = torch.empty(max(n_x, 1), dtype=torch.int32, device=dev)
@@ -66,7 +71,10 @@ def run_gpu(scene, cams, probs, rule, weight, texel_res=None, dtype="f32", scale
         dist = torch.empty((max(n_x, 1), c), dtype=torch.float32, device=dev)
         labels = torch.empty(max(n_x, 1), dtype=torch.int32, device=dev)
         lf.sm_normalise(m, dist, labels)
-        img = torch.empty((N, H, W), dtype=torch.uint8, device=dev)
+        if buffers == "compressible":
+            img = lf.device_empty((N, H, W), torch.uint8, dev)
+        else:
+            img = torch.empty((N, H, W), dtype=torch.uint8, device=dev)
         lf.sm_render_idmap(m, idm, N * H * W, img)
         img2 = None
         if reraster:

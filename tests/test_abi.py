@@ -143,6 +143,15 @@ def test_argument_ranges_rejected_on_host(libpath):
     assert L.sm_conf_train_step(P, None, P, 4, 0.1, P, P, None) == 1
     assert L.sm_host_alloc(0, ctypes.byref(h)) == 1
     assert L.sm_host_free(None) == 0
+    comp = ctypes.c_int32(7)
+    assert L.sm_device_alloc(0, 0, 1, ctypes.byref(h), ctypes.byref(comp)) == 1  # zero bytes
+    assert comp.value == 0 and not h.value
+    assert L.sm_device_alloc(0, 64, 1, None, None) == 1                          # out NULL
+    assert L.sm_device_alloc(0, 64, 2, ctypes.byref(h), None) == 1               # unknown flag
+    assert L.sm_device_alloc(-1, 64, 1, ctypes.byref(h), None) == 1              # no such device
+    assert L.sm_device_free(None) == 0
+    assert L.sm_device_free(P) == 1                                               # not a block of the library
+    assert "sm_device_alloc" in lf.sm_last_error()
 
 
 def test_binding_checks_buffers_before_the_call(libpath):

@@ -77,6 +77,32 @@ def test_medium_paper_room(ora, medium, rule, weight):
     assert (res.idmaps >= 0).mean() > 0.99
 
 
+@pytest.mark.parametrize("rule", ["logsum", "vote"])
+def test_compressible_row_maps_and_labels(ora, medium, rule):
+    """Row maps and label images in the library's compressible device memory
+    (sm_device_alloc), the z-buffer in its own: the same results as the
+    oracle, bit for bit where the acceptance rules say so."""
+    scene, cams, probs = medium
+    res = run_gpu(scene, cams, probs, rule, "pixel", reraster=False, buffers="compressible")
+    check_against_oracle(ora, scene, cams, probs.cpu().numpy(), res, rule, "pixel", nthreads=8)
+
+
+def test_device_alloc_blocks(dev):
+    """sm_device_alloc blocks hold what is written into them, are freed once,
+    and a pointer that is not a block is refused."""
+    from paper_2111_11103_gb300 import labelfuse as lf
+    for comp in (True, False):
+        p, got = lf.sm_device_alloc(0, 1 << 22, comp)
+        assert p and (got is False or comp)
+        t = lf.device_empty((1 << 20,), torch.int32, dev, compressible=comp)
+        t.copy_(torch.arange(1 << 20, dtype=torch.int32, device=dev) // 7)
+        assert torch.equal(t.cpu(), torch.arange(1 << 20, dtype=torch.int32) // 7)
+        del t
+        lf.sm_device_free(p)
+        with pytest.raises(lf.LabelFuseError):
+            lf.sm_device_free(p)  # freed already: not a block any more
+
+
 def test_medium_texels_s4(ora, medium):
     """Four texel steps per triangle (10 texels each) on the paper-shaped room."""
     scene, cams, probs = medium
