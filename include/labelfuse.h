@@ -424,7 +424,9 @@ sm_status sm_host_free(void *p);
  * SM_DEVICE_COMPRESSIBLE, and where the GPU and driver offer compute data
  * compression, the memory system keeps such data compressed in DRAM, so
  * writing and reading it moves fewer bytes; otherwise (or with flags 0) the
- * block is ordinary device memory.  *out receives `bytes` > 0 bytes on
+ * block is ordinary device memory.  The library holds its own z-buffer, row
+ * histograms and internal row maps in the same memory; with the environment
+ * variable LABELFUSE_COMPRESSIBLE_MEMORY=0 it uses ordinary memory everywhere.  *out receives `bytes` > 0 bytes on
  * `device`, uninitialised, owned by the caller until sm_device_free(*out);
  * *compressed_out (may be NULL) is 1 if the block is compressible.  Any
  * kernel, copy or memset may use the block.  Both calls are synchronous;

@@ -102,16 +102,18 @@ cudaError_t device_alloc(void **p, size_t bytes)
     return cudaMalloc(p, bytes);
 }
 
-// Compressible device memory (the GPU's compute data compression) for the
-// z-buffer.  Between two uses of a slot its keys are re-armed to all-ones and
-// written back to DRAM, and the next raster's atomics read them back: two
-// transfers of constant data per pixel and use, which the memory system
-// stores compressed in compressible memory.  The allocation goes through the
-// driver's virtual-memory calls (cuMemCreate with generic compression, then
-// reserve, map and grant access), fetched from the runtime at run time so
-// that the library has no link-time dependency on the driver library.  Where
-// the device or driver offers no compression (or LABELFUSE_ZBUF_COMPRESSION=0),
-// the z-buffer is ordinary stream-ordered device memory.
+// Compressible device memory (the GPU's compute data compression) for
+// buffers that hold long runs of equal values.  Between two uses of a z-buffer
+// slot its keys are re-armed to all-ones and written back to DRAM, and the
+// next raster's atomics read them back: two transfers of constant data per
+// pixel and use, which the memory system stores compressed in compressible
+// memory; row maps, label images and the mostly-zero per-frame row histograms
+// compress as well.  The allocation goes through the driver's virtual-memory
+// calls (cuMemCreate with generic compression, then reserve, map and grant
+// access), fetched from the runtime at run time so that the library has no
+// link-time dependency on the driver library.  Where the device or driver
+// offers no compression (or with LABELFUSE_COMPRESSIBLE_MEMORY=0 in the
+// environment) these buffers are ordinary device memory.
 struct VmmApi {
     decltype(&cuDeviceGet) device_get = nullptr;
     decltype(&cuDeviceGetAttribute) device_attr = nullptr;
@@ -153,9 +155,9 @@ const VmmApi &vmm_api()
     return api;
 }
 
-bool zbuf_compression_wanted()
+bool compression_wanted()
 {
-    const char *v = getenv("LABELFUSE_ZBUF_COMPRESSION");
+    const char *v = getenv("LABELFUSE_COMPRESSIBLE_MEMORY");
     return !(v && v[0] == '0');
 }
 
@@ -165,7 +167,7 @@ bool zbuf_compression_wanted()
 bool compressible_alloc(int dev, size_t bytes, void **ptr, size_t *mapped, unsigned long long *handle)
 {
     const VmmApi &api = vmm_api();
-    if (!api.ok || !zbuf_compression_wanted() || injected_alloc_failure()) return false;
+    if (!api.ok || !compression_wanted() || injected_alloc_failure()) return false;
     CUdevice d;
     int supported = 0;
     if (api.device_get(&d, dev) != CUDA_SUCCESS ||
@@ -243,8 +245,9 @@ sm_status grow(T **buf, int64_t *cap, int64_t need, cudaStream_t s, int fill, co
 
 // Room for `need` elements in *buf, in compressible memory where the device
 // offers it (compressible_alloc), else stream-ordered device memory; fill >= 0
-// sets every byte.  The z-buffer (re-armed to all-ones between uses) and the
-// host path's row maps and label images (runs of equal values) compress.  A
+// sets every byte.  The z-buffer (re-armed to all-ones between uses), the row
+// maps and label images (runs of equal values) and the per-frame row
+// histograms (mostly zero) compress.  A
 // compressible block is released only once the device is idle; inside a
 // stream capture, where that wait is not allowed, the old block is kept until
 // the mesh is freed and the new one is stream-ordered memory.
@@ -371,7 +374,8 @@ sm_status prepare_frames(sm_mesh *m, const sm_intrinsics *d_K, const double *d_T
     if ((st = grow_compressible(m, &m->keys, &m->keys_cap, &m->keys_blk, slots * slot_stride(B, npix), s, 0xFF,
                                 "z-buffer")) != SM_OK)
         return st;
-    if (need_idbuf && (st = grow(&m->idbuf, &m->idbuf_cap, (int64_t)B * npix, s, -1, "row-map buffer")) != SM_OK)
+    if (need_idbuf && (st = grow_compressible(m, &m->idbuf, &m->idbuf_cap, &m->idbuf_blk, (int64_t)B * npix, s, -1,
+                                              "row-map buffer")) != SM_OK)
         return st;
     {
         ProfScope p(m, SM_K_PROJECT, s);
@@ -541,7 +545,8 @@ sm_status fuse_impl(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float
     // the pipelined scatter reads its row map from the library's aligned buffer
     const bool ids_internal = need_ids && (!d_idmap_out || (tma && !from_keys));
     if ((st = prepare_frames(m, d_K, d_cam_to_world, N, npix, B, ids_internal, s)) != SM_OK) return st;
-    if (image_w && (st = grow(&m->fcnt, &m->fcnt_cap, (int64_t)B * m->n_x, s, 0, "row histograms")) != SM_OK)
+    if (image_w && (st = grow_compressible(m, &m->fcnt, &m->fcnt_cap, &m->fcnt_blk, (int64_t)B * m->n_x, s, 0,
+                                           "row histograms")) != SM_OK)
         return st;
     if (d_conf && (st = grow(&m->wbuf, &m->wbuf_cap, (int64_t)B * npix, s, -1, "confidence weights")) != SM_OK)
         return st;
@@ -928,7 +933,9 @@ sm_status sm_texel_res_from_gamma(sm_mesh *m, const sm_intrinsics *d_K, const do
         const int B = batch_frames(m, npix, N);
         if ((st = prepare_frames(m, d_K, d_cam_to_world, N, npix, B, false, s)) != SM_OK) return st;
         // per-frame counts share the w^(I) histogram buffer (zero between uses)
-        if ((st = grow(&m->fcnt, &m->fcnt_cap, (int64_t)B * F, s, 0, "per-frame counts")) != SM_OK) return st;
+        if ((st = grow_compressible(m, &m->fcnt, &m->fcnt_cap, &m->fcnt_blk, (int64_t)B * F, s, 0,
+                                    "per-frame counts")) != SM_OK)
+            return st;
         for (int f0 = 0; f0 < N; f0 += B) {
             const int nb = (N - f0 < B) ? N - f0 : B;
             if ((st = raster_only(m, f0, nb, H, W, m->keys, s)) != SM_OK) return st;
@@ -1465,12 +1472,13 @@ sm_status sm_mesh_free(sm_mesh *m)
         DeviceGuard g(m->device);
         cudaDeviceSynchronize();
         void *bufs[] = {m->verts, m->faces, m->row0, m->texinfo, m->acc, m->cnt, m->labels8, m->err, m->cams,
-                        m->keys_blk.p ? nullptr : m->keys, m->idbuf, m->wbuf, m->fcnt, m->bounds, m->hstage,
+                        m->keys_blk.p ? nullptr : m->keys, m->idbuf_blk.p ? nullptr : m->idbuf, m->wbuf,
+                        m->fcnt_blk.p ? nullptr : m->fcnt, m->bounds, m->hstage,
                         m->hids_blk.p ? nullptr : m->hids, m->hlabels_blk.p ? nullptr : m->hlabels, m->hcam,
                         m->clist, m->ccount, m->area, m->qctr};
         for (void *b : bufs)
             if (b) cudaFree(b);
-        for (const sm_mesh::VmmBlock &b : {m->keys_blk, m->hids_blk, m->hlabels_blk})
+        for (const sm_mesh::VmmBlock &b : {m->keys_blk, m->idbuf_blk, m->fcnt_blk, m->hids_blk, m->hlabels_blk})
             if (b.p) compressible_free(b.p, b.mapped, b.handle);
         for (const auto &r : m->retired) compressible_free(r.p, r.mapped, r.handle);
         if (m->rstream) cudaStreamDestroy(m->rstream);

@@ -264,7 +264,7 @@ struct sm_mesh {
         size_t mapped = 0;
         unsigned long long handle = 0;
     };
-    VmmBlock keys_blk;
+    VmmBlock keys_blk, idbuf_blk, fcnt_blk;
     int32_t *clist = nullptr;   // visible-cluster lists of one raster batch
     int64_t clist_cap = 0;
     uint32_t *ccount = nullptr;  // their lengths
