@@ -287,28 +287,46 @@ struct EntryLayout {
 // evict-last: the rows a trajectory keeps revisiting stay in L2 while the
 // prediction stream passes through) and their lengths into the observation
 // counts.  The whole warp takes part, 32 quads per instruction.
-template <int C, int RULE, bool IMAGE>
+// PAIRED: two quads per lane and iteration, both loaded before either is
+// used, so that their shared-memory and logarithm latencies overlap (measured
+// faster for FP32 storage, slower for FP8, where the one-quad loop is kept).
+template <int C, int RULE, bool IMAGE, bool PAIRED>
 __device__ __forceinline__ void drain(const ScatterArgs &a, const float4 *queue, const EntryMeta &meta, int E, int lane)
 {
     constexpr int Q = C / 4;
     const uint64_t keep = l2_evict_last();
-    for (int k = lane; k < E * Q; k += 32) {
-        const int e = k / Q;
-        const int r = meta.row[e];
+    auto one = [&](int k, int r, float4 v, float we) {
         if ((uint64_t)(int64_t)r >= (uint64_t)a.n_x) {  // never for a consistent layout: latch, skip
             atomicCAS(a.err, 0, (int32_t)kErrRowRange);
-            continue;
+            return;
         }
-        float4 v = queue[k];
         if (RULE == SM_RULE_LOGSUM) {
             // sum_k w log p_k = w ln 2 log2 prod_k p_k
-            const float wl = (IMAGE ? meta.w[e] : 1.0f) * kLn2;
+            const float wl = (IMAGE ? we : 1.0f) * kLn2;
             v = make_float4(lg2_ftz(v.x) * wl, lg2_ftz(v.y) * wl, lg2_ftz(v.z) * wl, lg2_ftz(v.w) * wl);
         } else if (IMAGE) {
-            const float we = meta.w[e];
             v = make_float4(v.x * we, v.y * we, v.z * we, v.w * we);
         }
-        red_add_v4(a.acc + (int64_t)r * C + 4 * (k - e * Q), v, keep);
+        red_add_v4(a.acc + (int64_t)r * C + 4 * (k - (k / Q) * Q), v, keep);
+    };
+    const int n = E * Q;
+    if (PAIRED) {
+        for (int k = lane; k < n; k += 64) {
+            const int k2 = k + 32;
+            const bool two = k2 < n;
+            const int e = k / Q, e2 = two ? k2 / Q : e;
+            const int r = meta.row[e], r2 = meta.row[e2];
+            const float we = IMAGE ? meta.w[e] : 1.0f, we2 = IMAGE ? meta.w[e2] : 1.0f;
+            const float4 v = queue[k];
+            const float4 v2 = two ? queue[k2] : v;
+            one(k, r, v, we);
+            if (two) one(k2, r2, v2, we2);
+        }
+    } else {
+        for (int k = lane; k < n; k += 32) {
+            const int e = k / Q;
+            one(k, meta.row[e], queue[k], IMAGE ? meta.w[e] : 1.0f);
+        }
     }
     if (lane < E && (uint64_t)(int64_t)meta.row[lane] < (uint64_t)a.n_x)
         red_add_u32(a.cnt + meta.row[lane], meta.n[lane], keep);
@@ -518,7 +536,7 @@ __device__ __forceinline__ void warp_tile_q(const ScatterArgs &a, const uint8_t 
 
     // 3. drain, then hand the stage back (the entries written into it by
     // plain stores must be ordered before the copy engine's next refill)
-    drain<C, RULE, IMAGE>(a, queue, meta, E, lane);
+    drain<C, RULE, IMAGE, DT == SM_F32>(a, queue, meta, E, lane);
     if (release) {
         fence_proxy_async_smem();
         __syncwarp();

@@ -87,6 +87,21 @@ def test_compressible_row_maps_and_labels(ora, medium, rule):
     check_against_oracle(ora, scene, cams, probs.cpu().numpy(), res, rule, "pixel", nthreads=8)
 
 
+def test_ordinary_memory_fallback(ora, medium, monkeypatch):
+    """With compressible memory turned off (LABELFUSE_COMPRESSIBLE_MEMORY=0, as
+    on a GPU without compute data compression) the z-buffer, histograms and
+    row maps are ordinary device memory and the results are the oracle's."""
+    monkeypatch.setenv("LABELFUSE_COMPRESSIBLE_MEMORY", "0")
+    from paper_2111_11103_gb300 import labelfuse as lf
+    p, comp = lf.sm_device_alloc(0, 1 << 20, True)
+    lf.sm_device_free(p)
+    assert comp is False
+    scene, cams, probs = medium
+    for weight in ("pixel", "image"):
+        res = run_gpu(scene, cams, probs, "logsum", weight, reraster=False, buffers="compressible")
+        check_against_oracle(ora, scene, cams, probs.cpu().numpy(), res, "logsum", weight, nthreads=8)
+
+
 def test_device_alloc_blocks(dev):
     """sm_device_alloc blocks hold what is written into them, are freed once,
     and a pointer that is not a block is refused."""
