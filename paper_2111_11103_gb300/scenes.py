@@ -70,18 +70,17 @@ def fuse_scenes(jobs: list[SceneJob], streams: int = 4) -> None:
     pool = _pool(max(1, min(streams, len(jobs))))
     for st in pool:
         st.wait_stream(cur)
+    capturing = torch.cuda.is_current_stream_capturing()
     for i, j in enumerate(jobs):
         st = pool[i % len(pool)]
         n = int(j.K.shape[0])
         lf.sm_fuse_frames(j.mesh, j.probs, j.dtype, j.scale, j.K, j.cam_to_world, n, j.H, j.W, j.idmap_out, st)
         if j.dist_out is not None or j.labels_out is not None:
             lf.sm_normalise(j.mesh, j.dist_out, j.labels_out, st)
+        if not capturing:  # (a graph keeps its tensors alive itself)
+            # the caller's tensors were used on this job's stream
+            for t in (j.probs, j.K, j.cam_to_world, j.scale, j.idmap_out, j.dist_out, j.labels_out):
+                if t is not None:
+                    t.record_stream(st)
     for st in pool:
         cur.wait_stream(st)
-    if torch.cuda.is_current_stream_capturing():
-        return  # a graph keeps its tensors alive itself
-    for j in jobs:  # the caller's tensors were used on the pool's streams
-        for t in (j.probs, j.K, j.cam_to_world, j.scale, j.idmap_out, j.dist_out, j.labels_out):
-            if t is not None:
-                for st in pool:
-                    t.record_stream(st)
