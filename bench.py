@@ -624,7 +624,25 @@ def e2e(args, lf, scene, probs, K, T, dev, stream, h_probs=None):
     lf.sm_mesh_free(m)
     hb = h_probs.numel() * h_probs.element_size() + h_K.numel() * 8 + h_T.numel() * 8
     return {"value": N / dt, "unit": "frames/s", "h2d_bytes_per_step": hb, "d2h_bytes_per_step": N * H * W,
-            "steps": steps, "call": "sm_fuse_render_host"}
+            "steps": steps, "call": "sm_fuse_render_host", "link": host_link_rate(h_probs, dev)}
+
+
+def host_link_rate(h_buf, dev, chunk_bytes=1 << 30):
+    """Host -> device rate of the same page-locked buffer with plain chunked
+    copies into one device block (no library, no kernels): what the host side
+    of the link gives this process on this machine, beside the e2e figure."""
+    flat = h_buf.view(-1).view(torch.uint8)
+    n = flat.numel()
+    chunk = min(chunk_bytes, n)
+    dst = torch.empty(chunk, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        dst[:b - a].copy_(flat[a:b], non_blocking=True)
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    return {"h2d_gbs": n / dt / 1e9, "bytes": n, "chunk_bytes": chunk}
 
 
 def run_scenes(args):
