@@ -468,9 +468,7 @@ def run_ours(args):
     value = ring * N / (ms_step / 1e3)  # the whole sequence (x ring), split over the ranks
     achieved, bytes_per_frame_scatter, frames_per_launch, dom = scatter_roofline(prof, 4, False)
     peak, peak_kind = peaks()
-    kernels = {k: {"launches": n, "ms_per_step": t / args.steps} for k, (n, t) in prof.items() if n}
-    if "raster" in kernels:  # its events sit on the second stream and include time spent waiting for SMs
-        kernels["raster"]["note"] = "event span on the raster stream, including waits behind the scatter"
+    kernels, raster_stream = split_kernel_times(prof, args.steps)
     # DRAM traffic from the committed capture of one launch of the benchmark's
     # size, per frame, times the frames per launch of this run
     tpf = kernel_traffic_per_frame(dom)
@@ -489,11 +487,12 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": bytes_per_frame_scatter * frames_per_launch,
                          "frames_per_launch": frames_per_launch, "peak_kind": peak_kind},
             "kernels": kernels,
+            "raster_stream": raster_stream,
             "gpu_launches": launches,
             "clocks": clocks}
     # parts of the step that sum to it: the kernels on the step's stream by
     # their events, the rest (the raster not hidden behind them, launch gaps)
-    on_stream = {k: v["ms_per_step"] for k, v in kernels.items() if k != "raster"}
+    on_stream = {k: v["ms_per_step"] for k, v in kernels.items()}
     line["step_breakdown_ms"] = dict(on_stream, raster_exposed_and_gaps=max(0.0, ms_step - sum(on_stream.values())))
     # step-level HBM fraction on the algorithmic bytes of the whole path
     algo_step = ring * n_loc * (H * W * c * 4 + 2 * H * W * 4 + H * W) + 2 * sg_rows(m, lf) * c * 4
@@ -574,11 +573,24 @@ def storage_forms(probs, timed, scatter_roofline, peak, N, steps):
                      "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                   "frac": achieved / peak, "kernel": dom,
                                   "algorithmic_bytes_per_frame": per_frame, "frames_per_launch": fpl},
-                     "kernels": {k: {"launches": n, "ms_per_step": t / steps} for k, (n, t) in prof.items() if n},
-                     "clocks": clocks}
+                     "kernels": split_kernel_times(prof, steps)[0], "clocks": clocks}
         del q, scale
         torch.cuda.empty_cache()
     return out
+
+
+def split_kernel_times(prof, steps):
+    """Per-kernel device time per step from the library's CUDA events: the
+    kernels on the step's stream (they run one after another, so their times
+    add up to at most the step), and apart from them the raster's launches,
+    whose events sit on the second stream and span the time its launches wait
+    for SMs behind the scatter (an event span, not device time: the raster's
+    device time is in the committed launch list)."""
+    kernels = {k: {"launches": n, "ms_per_step": t / steps} for k, (n, t) in prof.items() if n and k != "raster"}
+    n, t = prof.get("raster", (0, 0.0))
+    raster = {"launches": n, "event_span_ms_per_step": t / steps,
+              "note": "event span on the raster stream, including waits behind the scatter"} if n else None
+    return kernels, raster
 
 
 def sg_rows(m, lf):

@@ -116,3 +116,16 @@ def test_gpus_flag_must_match_the_launcher():
     r = subprocess.run([sys.executable, "bench.py", "--gpus", "2", "--dry-run"], cwd=root, capture_output=True,
                        text=True, timeout=600, env=env)
     assert r.returncode != 0 and "WORLD_SIZE=4" in r.stderr
+
+
+def test_kernel_times_on_the_step_stream_stay_within_the_step():
+    """The per-kernel breakdown holds only the kernels on the step's stream;
+    the raster's event span (second stream, waits included) is reported apart."""
+    prof = {"project": (1, 0.2), "raster": (4, 160.0), "scatter": (2, 190.0), "normalise": (1, 0.4),
+            "render": (1, 5.6), "resolve": (0, 0.0)}
+    bench = _bench()
+    kernels, raster = bench.split_kernel_times(prof, 20)
+    assert set(kernels) == {"project", "scatter", "normalise", "render"}
+    assert abs(sum(v["ms_per_step"] for v in kernels.values()) - (0.2 + 190.0 + 0.4 + 5.6) / 20) < 1e-12
+    assert raster["launches"] == 4 and raster["event_span_ms_per_step"] == 8.0 and "span" in raster["note"]
+    assert bench.split_kernel_times({"scatter": (1, 1.0)}, 1)[1] is None
