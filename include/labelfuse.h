@@ -131,6 +131,13 @@ sm_status sm_mesh_upload(const float *d_vertices, int64_t V, const int32_t *d_fa
  * lower triangle index.  Accumulation is float32 with atomics, so results
  * agree with an exact sum up to rounding.  The rows' observation counts are
  * kept alongside the accumulators.
+ * Scratch: the mesh keeps a z-buffer (two slots of one launch's frames, 8
+ * bytes per pixel) and, for image weights, per-frame row histograms, grown on
+ * demand and in compressible device memory where the GPU offers compute data
+ * compression (see sm_device_alloc).  Replacing a compressible buffer by a
+ * larger one waits for the device to be idle (only when a call needs more
+ * than every earlier call on the mesh); inside a stream capture the library
+ * takes stream-ordered memory instead.
  * Errors: SM_ERR_INVALID_ARG, SM_ERR_OOM, SM_ERR_CUDA, SM_ERR_STATE (mesh
  * freed). */
 sm_status sm_fuse_frames(sm_mesh *m, const void *d_probs, sm_dtype dtype, const float *d_scale,
