@@ -414,6 +414,22 @@ sm_status sm_conf_forward(const float *d_params, const float *d_feat, int64_t n,
 sm_status sm_conf_train_step(float *d_params, const float *d_feat, const float *d_target, int64_t n, float lr,
                              float *d_grad_out, float *d_loss_out, void *stream);
 
+/* The same step on a minibatch given by indices (a stochastic-gradient step
+ * over the observations the agreement targets label; the paper has no
+ * counterpart): the i-th observation of the minibatch (i < m) is observation
+ * d_idx[i] of the n_obs rows of d_feat (n_obs x SM_CONF_FEATURES float32) and
+ * d_target (n_obs float32), and the loss and gradient are means over the m.
+ * d_idx: m int64 indices, device, drawn by the caller (repeats allowed).  The
+ * rows are read where they lie, so the call gives bit for bit what
+ * sm_conf_train_step gives on the gathered rows.  An index outside [0,
+ * n_obs) is not read and makes the step's gradient and loss NaN, as a
+ * non-finite partial sum does.
+ * Errors: SM_ERR_INVALID_ARG (m < 0, n_obs < 0, m > 0 with n_obs = 0, lr NaN
+ * or outside [0, 1e6), NULL pointer), SM_ERR_OOM, SM_ERR_CUDA. */
+sm_status sm_conf_train_step_indexed(float *d_params, const float *d_feat, const float *d_target, int64_t n_obs,
+                                     const int64_t *d_idx, int64_t m, float lr, float *d_grad_out, float *d_loss_out,
+                                     void *stream);
+
 /* Page-locked host memory for the host buffers of sm_fuse_render_host (the
  * paper has no counterpart: this is plumbing of the host path).  Memory from
  * here is copied to the device at the host link's full rate in one piece,
@@ -433,8 +449,9 @@ sm_status sm_host_free(void *p);
  * writing and reading it moves fewer bytes; otherwise (or with flags 0) the
  * block is ordinary device memory.  The library holds its own z-buffer, row
  * histograms and internal row maps in the same memory; with the environment
- * variable LABELFUSE_COMPRESSIBLE_MEMORY=0 it uses ordinary memory everywhere.  *out receives `bytes` > 0 bytes on
- * `device`, uninitialised, owned by the caller until sm_device_free(*out);
+ * variable LABELFUSE_COMPRESSIBLE_MEMORY=0 it uses ordinary memory
+ * everywhere.  *out receives `bytes` > 0 bytes on `device`, uninitialised,
+ * owned by the caller until sm_device_free(*out);
  * *compressed_out (may be NULL) is 1 if the block is compressible.  Any
  * kernel, copy or memset may use the block.  Both calls are synchronous;
  * sm_device_free first waits for the block's device to be idle (no work may

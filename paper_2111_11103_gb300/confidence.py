@@ -48,11 +48,12 @@ def train_on_labels(mesh: int, probs, K, cam_to_world, H: int, W: int, steps: in
     g = torch.Generator(device=dev).manual_seed(seed)
     for s in range(steps):
         if batch and batch < X.shape[0]:
+            # the minibatch's indices are drawn here (random numbers are the
+            # step's input); the step reads the observations where they lie
             idx = torch.randint(0, X.shape[0], (batch,), device=dev, generator=g)
-            xb, yb = X[idx].contiguous(), Y[idx].contiguous()
+            lf.sm_conf_train_step_indexed(params, X, Y, X.shape[0], idx, batch, lr, grad, loss[s:s + 1])
         else:
-            xb, yb = X, Y
-        lf.sm_conf_train_step(params, xb, yb, xb.shape[0], lr, grad, loss[s:s + 1])
+            lf.sm_conf_train_step(params, X, Y, X.shape[0], lr, grad, loss[s:s + 1])
     return params, loss.cpu().numpy()
 
 

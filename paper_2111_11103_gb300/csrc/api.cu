@@ -1229,6 +1229,25 @@ sm_status sm_conf_train_step(float *d_params, const float *d_feat, const float *
     return SM_OK;
 }
 
+sm_status sm_conf_train_step_indexed(float *d_params, const float *d_feat, const float *d_target, int64_t n_obs,
+                                     const int64_t *d_idx, int64_t m, float lr, float *d_grad_out, float *d_loss_out,
+                                     void *stream)
+{
+    if (m < 0 || n_obs < 0) return fail(SM_ERR_INVALID_ARG, "m < 0 or n_obs < 0");
+    if (m > 0 && n_obs == 0) return fail(SM_ERR_INVALID_ARG, "indices into an empty set of observations");
+    if (!(lr >= 0.0f && lr < 1.0e6f)) return fail(SM_ERR_INVALID_ARG, "learning rate %g", (double)lr);
+    if (!d_params || !d_grad_out || !d_loss_out || (m > 0 && (!d_feat || !d_target || !d_idx)))
+        return fail(SM_ERR_INVALID_ARG, "NULL pointer");
+    const cudaError_t e = lf::launch_conf_train_step(d_params, d_feat, d_target, m, lr, d_grad_out, d_loss_out,
+                                                     static_cast<cudaStream_t>(stream), d_idx, n_obs);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(SM_ERR_OOM, "confidence training step: stream-ordered allocation of its sums");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "confidence training step");
+    return SM_OK;
+}
+
 sm_status sm_host_alloc(uint64_t bytes, void **out)
 {
     if (!out || bytes == 0) return fail(SM_ERR_INVALID_ARG, "sm_host_alloc: NULL out or zero bytes");

@@ -390,7 +390,7 @@ constexpr int kRow = kF + 4 * kH + 1;
 
 __global__ void __launch_bounds__(kObs)
     k_conf_grad(const float *__restrict__ params, const float *__restrict__ feat, const float *__restrict__ target,
-                int64_t n, unsigned long long *__restrict__ acc)
+                int64_t n, const int64_t *__restrict__ idx, int64_t n_obs, unsigned long long *__restrict__ acc)
 {
     extern __shared__ float sm[];
     float *s = sm;                          // SM_CONF_PARAMS (bf16-rounded)
@@ -399,12 +399,24 @@ __global__ void __launch_bounds__(kObs)
     const int64_t i = (int64_t)blockIdx.x * kObs + threadIdx.x;
     float *r = rows + threadIdx.x * kRow;
     float l = 0.0f;
-    if (i < n) {
+    // the minibatch's i-th observation: i itself, or idx[i] (an index outside
+    // [0, n_obs) counts as a non-finite partial sum: the step's gradient and
+    // loss become NaN, and the observation is not read)
+    int64_t j = i;
+    bool valid = i < n;
+    if (valid && idx) {
+        j = idx[i];
+        if (j < 0 || j >= n_obs) {
+            atomicAdd(acc + SM_CONF_PARAMS + 1, 1ull);
+            valid = false;
+        }
+    }
+    if (valid) {
         float x[kF], z1[kH], z2[kH];
 #pragma unroll
-        for (int k = 0; k < kF; ++k) x[k] = feat[i * kF + k];
+        for (int k = 0; k < kF; ++k) x[k] = feat[j * kF + k];
         const float o = mlp_forward(s, x, z1, z2);
-        const float y = target[i];
+        const float y = target[j];
         l = (fmaxf(o, 0.0f) + log1pf(expf(-fabsf(o))) - y * o) / (float)n;  // softplus(o) - y o
         const float d_o = (1.0f / (1.0f + expf(-o)) - y) / (float)n;
         for (int k = 0; k < kF; ++k) r[k] = x[k];
@@ -515,7 +527,7 @@ void launch_conf_forward(const float *params, const float *feat, int64_t n, floa
 }
 
 cudaError_t launch_conf_train_step(float *params, const float *feat, const float *target, int64_t n, float lr,
-                                   float *grad, float *loss, cudaStream_t s)
+                                   float *grad, float *loss, cudaStream_t s, const int64_t *idx, int64_t n_obs)
 {
     // fixed-point sums: SM_CONF_PARAMS gradients, the loss, the non-finite count
     constexpr size_t kAccBytes = (SM_CONF_PARAMS + 2) * sizeof(unsigned long long);
@@ -528,7 +540,7 @@ cudaError_t launch_conf_train_step(float *params, const float *feat, const float
         static PerDeviceOnce configured;
         if (configured.first(current_device()))
             cudaFuncSetAttribute(k_conf_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_conf_grad<<<(unsigned)((n + kObs - 1) / kObs), kObs, smem, s>>>(params, feat, target, n, acc);
+        k_conf_grad<<<(unsigned)((n + kObs - 1) / kObs), kObs, smem, s>>>(params, feat, target, n, idx, n_obs, acc);
     }
     k_conf_update<<<(SM_CONF_PARAMS + 1 + 255) / 256, 256, 0, s>>>(params, acc, lr, grad, loss);
     e = cudaGetLastError();

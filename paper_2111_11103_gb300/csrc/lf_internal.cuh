@@ -203,7 +203,8 @@ void launch_conf_weights(unsigned long long *keys, int64_t total, int H, int W, 
                          int64_t F, const sm_intrinsics *K, const double *T, const void *probs, sm_dtype dt,
                          const float *scale, int c, const float *params, float *w, int32_t *rows, cudaStream_t s);
 cudaError_t launch_conf_train_step(float *params, const float *feat, const float *target, int64_t n, float lr,
-                                   float *grad, float *loss, cudaStream_t s);
+                                   float *grad, float *loss, cudaStream_t s, const int64_t *idx = nullptr,
+                                   int64_t n_obs = 0);
 void launch_conf_targets(const void *probs, sm_dtype dt, const float *scale, int c, const int32_t *rows, int64_t n,
                          const uint8_t *labels8, int64_t n_x, float *y, cudaStream_t s);
 void launch_normalise(sm_rule rule, const float *acc, const uint32_t *cnt, int64_t n_x, int c, float *dist,

@@ -38,7 +38,7 @@ SYMBOLS = ["sm_mesh_upload", "sm_fuse_frames", "sm_normalise", "sm_render_labels
            "sm_fuse_render_host", "sm_host_alloc", "sm_host_free", "sm_device_alloc", "sm_device_free", "sm_set_weight_mix", "sm_texel_res_from_gamma",
            "sm_autotune_batch", "sm_fuse_frames_weighted", "sm_conf_features", "sm_conf_targets", "sm_conf_forward",
            "sm_conf_train_step", "sm_set_queue_shape", "sm_fuse_scenes", "sm_conf_weights",
-           "sm_set_launch_frames", "sm_fuse_frames_confident"]
+           "sm_set_launch_frames", "sm_fuse_frames_confident", "sm_conf_train_step_indexed"]
 SM_CONF_FEATURES = 5
 SM_CONF_PARAMS = 1281
 SM_NOALLOC_MAX_PIXELS = 1572864
@@ -99,6 +99,7 @@ def lib() -> ctypes.CDLL:
             "sm_conf_targets": [P, P, i32, P, P, i64, P, P],
             "sm_conf_forward": [P, P, i64, P, P],
             "sm_conf_train_step": [P, P, P, i64, ctypes.c_float, P, P, P],
+            "sm_conf_train_step_indexed": [P, P, P, i64, P, i64, ctypes.c_float, P, P, P],
             "sm_set_queue_shape": [P, i32, i32, i32, i32, i32, i32],
             "sm_fuse_scenes": [P, i32, P],
             "sm_conf_weights": [P, P, i32, P, P, P, i32, i32, i32, P, P, P, P],
@@ -329,6 +330,19 @@ def sm_conf_train_step(params, feat, target, n: int, lr: float, grad_out, loss_o
                                     _arg(feat, "feat", 4 * SM_CONF_FEATURES * m), _arg(target, "target", 4 * m), int(n),
                                     float(lr), _arg(grad_out, "grad_out", 4 * SM_CONF_PARAMS),
                                     _arg(loss_out, "loss_out", 4), _stream(stream)))
+
+
+def sm_conf_train_step_indexed(params, feat, target, n_obs: int, idx, m: int, lr: float, grad_out, loss_out,
+                               stream=None):
+    """One training step on the minibatch of observations idx[0..m) (int64, device)."""
+    no, mm = max(0, int(n_obs)), max(0, int(m))
+    if idx is not None and not isinstance(idx, int) and str(idx.dtype) != "torch.int64":
+        raise LabelFuseError(SM_ERR_INVALID_ARG, "idx must be int64")
+    _check(lib().sm_conf_train_step_indexed(_arg(params, "params", 4 * SM_CONF_PARAMS),
+                                            _arg(feat, "feat", 4 * SM_CONF_FEATURES * no), _arg(target, "target", 4 * no),
+                                            int(n_obs), _arg(idx, "idx", 8 * mm), int(m), float(lr),
+                                            _arg(grad_out, "grad_out", 4 * SM_CONF_PARAMS), _arg(loss_out, "loss_out", 4),
+                                            _stream(stream)))
 
 
 def sm_host_alloc(nbytes: int) -> int:

@@ -141,6 +141,13 @@ def test_argument_ranges_rejected_on_host(libpath):
     assert L.sm_conf_train_step(P, P, P, 4, float("nan"), P, P, None) == 1
     assert L.sm_conf_train_step(P, P, P, 4, -0.5, P, P, None) == 1
     assert L.sm_conf_train_step(P, None, P, 4, 0.1, P, P, None) == 1
+    ti = L.sm_conf_train_step_indexed
+    assert ti(P, P, P, 10, P, -1, 0.1, P, P, None) == 1                          # m < 0
+    assert ti(P, P, P, -1, P, 4, 0.1, P, P, None) == 1                           # n_obs < 0
+    assert ti(P, P, P, 0, P, 4, 0.1, P, P, None) == 1                            # indices into nothing
+    assert ti(P, P, P, 10, P, 4, float("nan"), P, P, None) == 1                  # lr NaN
+    assert ti(P, P, P, 10, None, 4, 0.1, P, P, None) == 1                        # idx NULL
+    assert ti(P, P, P, 10, P, 4, 0.1, None, P, None) == 1                        # grad NULL
     assert L.sm_host_alloc(0, ctypes.byref(h)) == 1
     assert L.sm_host_free(None) == 0
     comp = ctypes.c_int32(7)

@@ -101,6 +101,38 @@ def test_forward_and_gradient_match_oracle(dev, medium):
     np.testing.assert_allclose(params.cpu().numpy(), p0.cpu().numpy() - 0.5 * grad.cpu().numpy(), rtol=0, atol=1e-7)
 
 
+def test_indexed_step_equals_the_gathered_step(dev, medium):
+    """A minibatch given by indices (repeats included) gives bit for bit the
+    step on the gathered rows, whose gradient the test above checks against
+    the oracle; the oracle's gradient of the gathered rows holds here too; an
+    index outside the observations poisons the step instead of being read."""
+    from paper_2111_11103_gb300 import labelfuse as lf
+    scene, cams, probs = medium
+    feat, rows = gpu_features(scene, cams, probs, dev)
+    X = feat.reshape(-1, 5)[rows.reshape(-1) >= 0][:20000].contiguous()
+    n = X.shape[0]
+    y = (torch.arange(n, device=dev) % 5 < 2).float()
+    g = torch.Generator(device=dev).manual_seed(11)
+    idx = torch.randint(0, n, (3000,), device=dev, generator=g)
+    params = torch.as_tensor(_params(4), device=dev)
+    p_a, p_b = params.clone(), params.clone()
+    grad_a, loss_a = torch.empty(cf.N_PARAMS, device=dev), torch.empty(1, device=dev)
+    grad_b, loss_b = torch.empty_like(grad_a), torch.empty_like(loss_a)
+    Xg, yg = X[idx].contiguous(), y[idx].contiguous()
+    lf.sm_conf_train_step(p_a, Xg, yg, idx.numel(), 0.25, grad_a, loss_a)
+    lf.sm_conf_train_step_indexed(p_b, X, y, n, idx, idx.numel(), 0.25, grad_b, loss_b)
+    torch.cuda.synchronize()
+    assert torch.equal(grad_a, grad_b) and torch.equal(loss_a, loss_b) and torch.equal(p_a, p_b)
+    l_ora, g_ora = cf.loss_and_grad(params.cpu().numpy(), Xg.cpu().numpy(), yg.cpu().numpy())
+    assert abs(float(loss_b) - l_ora) <= 1e-5 * abs(l_ora)
+    np.testing.assert_allclose(grad_b.cpu().numpy(), g_ora, rtol=0, atol=1e-5 * np.abs(g_ora).max())
+    bad = idx.clone()
+    bad[123] = n  # one past the end: not read, the step is poisoned
+    lf.sm_conf_train_step_indexed(params.clone(), X, y, n, bad, bad.numel(), 0.25, grad_b, loss_b)
+    torch.cuda.synchronize()
+    assert torch.isnan(grad_b).all() and torch.isnan(loss_b).all()
+
+
 @pytest.mark.parametrize("rule", ["sum", "logsum", "maxsum", "vote"])
 def test_fusion_with_predicted_weights(ora, dev, tiny, rule):
     from paper_2111_11103_gb300 import labelfuse as lf
