@@ -541,7 +541,9 @@ sm_status sm_render_rows_noalloc(const float *d_vertices, int64_t V, const int32
 
 /* Kernel timing: when enabled, every launch of the kernels below is bracketed
  * by CUDA events on the launching stream (the raster kind brackets its two
- * kernels, cluster cull and raster, together).  sm_profile_read synchronises
+ * kernels, cluster cull and raster, together).  Enabled or not, each such
+ * launch is an NVTX range of the "labelfuse" domain named after its kind
+ * ("project", "raster", ...), which profilers can show or filter on.  sm_profile_read synchronises
  * those events and returns the number of kernel launches and the total device
  * time since the last read (then clears them). */
 typedef enum sm_kernel {

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include <cuda.h>  // driver types of the virtual-memory calls (entry points fetched at run time)
+#include <nvtx3/nvToolsExt.h>  // header-only; inert unless a profiler attaches
 
 #include "lf_internal.cuh"
 
@@ -62,7 +63,25 @@ struct DeviceGuard {
     }
 };
 
-// CUDA-event bracket of one launch when kernel timing is enabled.
+// NVTX domain of the library: every launch scope below is a range named after
+// its kernel kind, so that a timeline (nsys) or a filtered capture (ncu
+// --nvtx) can pick the hot path's steps out; without a profiler attached the
+// calls return at once.
+nvtxDomainHandle_t nvtx_domain()
+{
+    static const nvtxDomainHandle_t d = nvtxDomainCreateA("labelfuse");
+    return d;
+}
+
+const char *kernel_kind_name(int k)
+{
+    static const char *const names[SM_K_COUNT_KINDS] = {"project", "raster", "resolve", "count", "scatter",
+                                                        "normalise", "render", "queue", "conf"};
+    return k >= 0 && k < SM_K_COUNT_KINDS ? names[k] : "kernel";
+}
+
+// CUDA-event bracket of one launch when kernel timing is enabled, and an NVTX
+// range around it always.
 struct ProfScope {
     sm_mesh *m;
     int k;
@@ -71,6 +90,12 @@ struct ProfScope {
     // kernels: how many kernel launches the scope brackets
     ProfScope(sm_mesh *m_, sm_kernel k_, cudaStream_t s_, int kernels = 1) : m(m_), k((int)k_), s(s_)
     {
+        nvtxEventAttributes_t a{};
+        a.version = NVTX_VERSION;
+        a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+        a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+        a.message.ascii = kernel_kind_name(k);
+        nvtxDomainRangePushEx(nvtx_domain(), &a);
         if (!m->prof) return;
         m->ev_kernels[k] += kernels;
         if (m->ev_used[k] == m->ev[k].size()) {
@@ -88,6 +113,7 @@ struct ProfScope {
     ~ProfScope()
     {
         if (ev) cudaEventRecord(ev->b, s);
+        nvtxDomainRangePop(nvtx_domain());
     }
 };
 
