@@ -68,6 +68,9 @@ def parse():
                     help="batched form: this many independent rooms of uneven size (64 for the stated spread), fused "
                          "one by one, side by side on streams, through work-queue launches, and as a CUDA graph")
     ap.add_argument("--ring", type=int, default=16, help="--scenes: resident frames per room")
+    ap.add_argument("--scene-profile", action="store_true",
+                    help="--scenes: one room-after-room step with the library's kernel timing on, per-kernel "
+                         "device time by room resolution and mesh size (no throughput line)")
     ap.add_argument("--learned", action="store_true",
                     help="learned-confidence form: the 4M-triangle apartment, --frames frames (5000 by default), "
                          "4 texel steps, plain against confidence-weighted fusion")
@@ -757,6 +760,40 @@ def run_scenes(args):
             e1.record()
             torch.cuda.synchronize(dev)
         return e0.elapsed_time(e1) / args.steps, clk.summary()
+
+    if args.scene_profile:
+        # kernel device time of one room-after-room step, summed by kind and by
+        # room class (resolution, mesh size above or below 500 k triangles)
+        for _ in range(max(args.warmup, 1)):
+            one_by_one()
+        torch.cuda.synchronize(dev)
+        for r in rooms:
+            for k in lf.SM_KERNEL:
+                lf.sm_profile_read(r["mesh"], k)
+            lf.sm_profile_enable(r["mesh"], True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        one_by_one()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        by_kind, by_class = {}, {}
+        for r in rooms:
+            cls = f"{r['W']}x{r['H']}, {'>' if r['faces'] > 500_000 else '<='}500k faces"
+            c = by_class.setdefault(cls, {"rooms": 0, "frames": 0, "ms": 0.0})
+            c["rooms"] += 1
+            c["frames"] += r["N"]
+            for k in lf.SM_KERNEL:
+                n, ms = lf.sm_profile_read(r["mesh"], k)
+                by_kind[k] = by_kind.get(k, 0.0) + ms
+                c["ms"] += ms
+            lf.sm_profile_enable(r["mesh"], False)
+        for c in by_class.values():
+            c["us_per_frame"] = 1e3 * c["ms"] / max(c["frames"], 1)
+        print(json.dumps({"scene_profile": {"step_ms": e0.elapsed_time(e1), "kernel_ms_by_kind": by_kind,
+                                            "by_room_class": by_class, "frames": frames}}), flush=True)
+        for r in rooms:
+            lf.sm_mesh_free(r["mesh"])
+        return
 
     out = {}
     modes = [("one_by_one", one_by_one)]
