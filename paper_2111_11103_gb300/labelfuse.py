@@ -424,7 +424,8 @@ def device_empty(shape, dtype, device=None, compressible: bool = True):
     """Uninitialised CUDA tensor in memory from sm_device_alloc: compressible
     where the GPU offers it (for row maps and label images, whose runs of equal
     values the memory system stores compressed).  The memory is released with
-    the tensor."""
+    the tensor; releasing a compressible block waits for the device to be idle,
+    so let no such tensor die while a stream is being captured into a graph."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
     if dev.type != "cuda":
