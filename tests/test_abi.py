@@ -197,6 +197,23 @@ def test_binding_checks_buffers_before_the_call(libpath):
         lf._arg(torch.zeros(10, dtype=torch.uint8), "probs", 11, host=True)
 
 
+def test_binding_checks_of_the_newer_calls(libpath):
+    """device_empty wants a CUDA device and a supported element type; the
+    indexed training step wants int64 indices (checked before the call)."""
+    import torch
+    from paper_2111_11103_gb300 import labelfuse as lf
+    with pytest.raises(ValueError, match="CUDA device"):
+        lf.device_empty((4,), torch.int32, "cpu")
+    with pytest.raises(ValueError, match="unsupported dtype"):
+        lf.device_empty((4,), torch.bfloat16, "cuda:0")
+    with pytest.raises(lf.LabelFuseError, match="int64"):
+        lf.sm_conf_train_step_indexed(None, None, None, 8, torch.zeros(4, dtype=torch.int32), 4, 0.1, None, None,
+                                      stream=0)
+    # raw addresses pass through to the library, which checks the rest
+    with pytest.raises(lf.LabelFuseError, match="m < 0"):
+        lf.sm_conf_train_step_indexed(16, 16, 16, 8, 16, -1, 0.1, 16, 16, stream=0)
+
+
 def test_header_is_plain_c_and_a_c_client_links(libpath, tmp_path):
     """include/labelfuse.h compiles as strict C99 and C++17 on its own, and a
     plain C program (no Python, no PyTorch) links against the library and gets
